@@ -1,0 +1,824 @@
+/*
+ * GSCache oracle: a plain, slow, obviously-correct CPU restatement of the hot
+ * path of "GSCache: Real-Time Radiance Caching for Volume Path Tracing using
+ * 3D Gaussian Splatting" (Bauer, Wu, Gadirov, Ma).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header or constant table with the CUDA path; both sides were written
+ * separately from the paper and the readings listed in the design notes.
+ *
+ * Precision: FP64 throughout, except
+ *   - the tracer's FP32 mirror mode (trace_body.inc with REAL = float), which
+ *     exists so that the GPU tracer can be compared bit for bit;
+ *   - the rasterizer's view depth, the sort key of the compositing order and
+ *     the near-plane test: a decision the kernel takes in FP32, so the oracle
+ *     takes it in FP32 too (same operation order, no contraction).
+ *
+ * Contents and the passages they follow:
+ *   philox4x32_10       Salmon et al., SC'11 (counter-based RNG; the paper is
+ *                       silent on its RNG)
+ *   orc_trace           Sec. 3.1 (Eq. 1), 3.2, 3.3 (Algorithm 1), 3.4 (Eq. 2),
+ *                       3.5; trace_body.inc
+ *   orc_transmittance   delta tracking (Sec. 3.2) vs ratio tracking
+ *   orc_project         3D Gaussian splatting projection, Sec. 3.1 / Sec. 3.6
+ *                       (SH degree 0)
+ *   orc_render          front-to-back alpha compositing of all Gaussians per
+ *                       pixel (Sec. 3.1)
+ *   orc_render_backward analytic gradient of orc_render (the "inverse
+ *                       splatting step", Sec. 3.5)
+ *   orc_loss_hdr        Sec. 3.6 "Loss", Eq. after Noise2Noise
+ *   orc_loss_l1ssim     0.8 L1 + 0.2 (1 - SSIM), Wang et al. 2004 (not in the
+ *                       paper; the 1M-Gaussian differentiation workload)
+ *   orc_adamw           Sec. 3.6 "Regularization" (AdamW, Loshchilov & Hutter)
+ *   orc_lr_scale        Eq. 4
+ *
+ * Parity unpinned: the cache-coupled branch of the tracer (Algorithm 1 with
+ * C > 0 and cache images) has no closed form; only the C -> infinity identity
+ * pins it.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define TRACK_MAX_STEPS (1 << 20)
+#define TRACE_MAX_LEVELS 16
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as   */
+/* easy as 1, 2, 3", SC'11).  Ten rounds; round r uses key + r * (W0, W1).   */
+
+static void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c[0];
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c[2];
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+void orc_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    philox4x32_10(c, key[0], key[1]);
+    memcpy(out, c, sizeof c);
+}
+
+/* stream for one path sample: key = seed, counter = (pixel, sample, frame,
+   block); each block yields four words consumed in order */
+typedef struct {
+    uint32_t c0, c1, c2, block, k0, k1;
+    uint32_t buf[4];
+    int avail;
+} rng_t;
+
+static void rng_init(rng_t* r, uint64_t seed, uint32_t pixel, uint32_t sample, uint32_t frame) {
+    r->c0 = pixel; r->c1 = sample; r->c2 = frame; r->block = 0;
+    r->k0 = (uint32_t)seed; r->k1 = (uint32_t)(seed >> 32);
+    r->avail = 0;
+}
+
+static uint32_t rng_next(rng_t* r) {
+    if (r->avail == 0) {
+        uint32_t c[4] = {r->c0, r->c1, r->c2, r->block};
+        r->block += 1;
+        philox4x32_10(c, r->k0, r->k1);
+        memcpy(r->buf, c, sizeof c);
+        r->avail = 4;
+    }
+    uint32_t v = r->buf[4 - r->avail];
+    r->avail -= 1;
+    return v;
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP32 elementary functions of the mirror mode.                             */
+/* ln: x = 2^e m with m in [sqrt(1/2), sqrt(2)], ln m = 2 atanh(s),          */
+/*     s = (m - 1)/(m + 1), atanh by its Taylor series to s^11.              */
+/* sincos(2 pi u): quadrant split, theta in [-pi/4, pi/4], Taylor series of  */
+/*     sin to theta^9 and cos to theta^10, angle addition with pi/4.         */
+
+static float ln_f32(float x) {
+    uint32_t b;
+    memcpy(&b, &x, 4);
+    int e = (int)((b >> 23) & 0xffu) - 127;
+    uint32_t mb = (b & 0x7fffffu) | 0x3f800000u;
+    float m;
+    memcpy(&m, &mb, 4);
+    if (m > 1.41421356f) { m = m * 0.5f; e = e + 1; }
+    float s = (m - 1.0f) / (m + 1.0f);
+    float s2 = s * s;
+    float p = 0.181818182f;
+    p = 0.222222222f + s2 * p;
+    p = 0.285714286f + s2 * p;
+    p = 0.4f + s2 * p;
+    p = 0.666666667f + s2 * p;
+    p = 2.0f + s2 * p;
+    return (float)e * 0.693147181f + s * p;
+}
+
+static void sincos2pi_f32(float u, float* sn_out, float* cs_out) {
+    float v = u * 4.0f;
+    int q = (int)v;
+    float f = v - (float)q;
+    float th = (f - 0.5f) * 1.57079633f;
+    float t2 = th * th;
+    float a = 1.0f - t2 * 0.0138888889f;
+    a = 1.0f - (t2 * 0.0238095238f) * a;
+    a = 1.0f - (t2 * 0.05f) * a;
+    a = 1.0f - (t2 * 0.166666667f) * a;
+    float sn = th * a;
+    float b = 1.0f - t2 * 0.0111111111f;
+    b = 1.0f - (t2 * 0.0178571429f) * b;
+    b = 1.0f - (t2 * 0.0333333333f) * b;
+    b = 1.0f - (t2 * 0.0833333333f) * b;
+    float cs = 1.0f - (t2 * 0.5f) * b;
+    float cp = (cs - sn) * 0.707106781f;
+    float sp = (sn + cs) * 0.707106781f;
+    switch (q) {
+        case 0: *cs_out = cp; *sn_out = sp; break;
+        case 1: *cs_out = -sp; *sn_out = cp; break;
+        case 2: *cs_out = -cp; *sn_out = -sp; break;
+        default: *cs_out = sp; *sn_out = -cp; break;
+    }
+}
+
+void orc_ln_f32(const float* x, float* y, int64_t n) {
+    for (int64_t i = 0; i < n; ++i) y[i] = ln_f32(x[i]);
+}
+
+void orc_sincos2pi_f32(const float* u, float* s, float* c, int64_t n) {
+    for (int64_t i = 0; i < n; ++i) sincos2pi_f32(u[i], &s[i], &c[i]);
+}
+
+static void sincos2pi_f64(double u, double* s, double* c) {
+    *s = sin(6.283185307179586476925 * u);
+    *c = cos(6.283185307179586476925 * u);
+}
+
+/* ------------------------------------------------------------------------ */
+/* tracer, two instantiations                                               */
+
+#define REAL double
+#define SUFFIX _d
+#define LN(x) log(x)
+#define SQRT(x) sqrt(x)
+#define SINCOS2PI(u, s, c) sincos2pi_f64((u), (s), (c))
+#include "trace_body.inc"
+#undef REAL
+#undef SUFFIX
+#undef LN
+#undef SQRT
+#undef SINCOS2PI
+
+#define REAL float
+#define SUFFIX _f
+#define LN(x) ln_f32(x)
+#define SQRT(x) sqrtf(x)
+#define SINCOS2PI(u, s, c) sincos2pi_f32((u), (s), (c))
+#include "trace_body.inc"
+#undef REAL
+#undef SUFFIX
+#undef LN
+#undef SQRT
+#undef SINCOS2PI
+
+/*
+ * Path-traced image and K intermediate path buffers (Sec. 3.5) over a pixel
+ * window.  precision = 32 (FP32 mirror) or 64.  cam = R[9], t[3], pos[3],
+ * fx, fy, cx, cy.  vol_f = {density_max, sigma_max, albedo}.  light = ldir[3],
+ * lrad[3], env[3].  cache: K x 3 x H x W full-frame images or NULL.
+ * lengths (optional): per (pixel, sample) path length.
+ */
+int orc_trace(int precision, const float* grid, int nx, int ny, int nz, const float* vol_f, int tf_n,
+              const float* tf_pos, const float* tf_rgba, const float* light, const float* cam, int W, int H,
+              int spp, int max_bounces, int K, uint64_t seed, uint32_t frame, float C, float eps,
+              const float* cache, int x0, int y0, int w, int h, double* targets, double* image,
+              int32_t* lengths, int nthreads) {
+    if (nx < 2 || ny < 2 || nz < 2 || tf_n < 1 || tf_n > 16 || K < 0 || K > TRACE_MAX_LEVELS || spp < 1)
+        return 1;
+    if (precision == 32) {
+        vol_t_f v;
+        cam_t_f c;
+        vol_setup_f(&v, grid, nx, ny, nz, vol_f[0], vol_f[1], vol_f[2], tf_n, tf_pos, tf_rgba, light, light + 3,
+                    light + 6);
+        cam_setup_f(&c, cam, W, H);
+        trace_window_f(&v, &c, spp, max_bounces, K, seed, frame, C, eps, cache, x0, y0, w, h, targets, image,
+                       lengths, nthreads);
+    } else {
+        vol_t_d v;
+        cam_t_d c;
+        vol_setup_d(&v, grid, nx, ny, nz, vol_f[0], vol_f[1], vol_f[2], tf_n, tf_pos, tf_rgba, light, light + 3,
+                    light + 6);
+        cam_setup_d(&c, cam, W, H);
+        trace_window_d(&v, &c, spp, max_bounces, K, seed, frame, C, eps, cache, x0, y0, w, h, targets, image,
+                       lengths, nthreads);
+    }
+    return 0;
+}
+
+/*
+ * n transmittance estimates along one ray from `origin` in direction `dir`
+ * (FP64): mode 0 = delta tracking (1 if the ray leaves without a real
+ * collision, else 0), mode 1 = ratio tracking.  Estimate k uses the Philox
+ * stream (k, 0, 0).
+ */
+void orc_transmittance(int mode, const float* grid, int nx, int ny, int nz, const float* vol_f, int tf_n,
+                       const float* tf_pos, const float* tf_rgba, const double* origin, const double* dir,
+                       int64_t n, uint64_t seed, double* out, int nthreads) {
+    vol_t_d v;
+    float zero3[3] = {0, 0, 0}, up[3] = {0, 0, 1};
+    vol_setup_d(&v, grid, nx, ny, nz, vol_f[0], vol_f[1], vol_f[2], tf_n, tf_pos, tf_rgba, up, zero3, zero3);
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int64_t k = 0; k < n; ++k) {
+        rng_t r;
+        rng_init(&r, seed, (uint32_t)k, 0u, 0u);
+        if (mode == 0) {
+            double x[3];
+            out[k] = free_flight_d(&v, &r, origin, dir, x) ? 0.0 : 1.0;
+        } else {
+            out[k] = ratio_T_d(&v, &r, origin, dir);
+        }
+    }
+}
+
+/* density and sigma_t at points (FP64), for closed-form checks */
+void orc_sigma_t(const float* grid, int nx, int ny, int nz, const float* vol_f, int tf_n, const float* tf_pos,
+                 const float* tf_rgba, const double* pts, int64_t n, double* out) {
+    vol_t_d v;
+    float zero3[3] = {0, 0, 0}, up[3] = {0, 0, 1};
+    vol_setup_d(&v, grid, nx, ny, nz, vol_f[0], vol_f[1], vol_f[2], tf_n, tf_pos, tf_rgba, up, zero3, zero3);
+    for (int64_t k = 0; k < n; ++k) out[k] = sigma_t_d(&v, pts + 3 * k);
+}
+
+/* ------------------------------------------------------------------------ */
+/* 3D Gaussian splatting rasterizer (FP64).                                  */
+/*                                                                           */
+/* Packed parameters per Gaussian (16 float): mean[0:3], opacity logit[3],  */
+/* log-scale[4:7], pad, quaternion (w,x,y,z)[8:12], RGB[12:15], pad.         */
+/* cam: R[9] (rows: right, down, forward), t[3], pos[3], fx, fy, cx, cy.     */
+/* cfg: alpha_max, alpha_min, T_min, near, dilation.                         */
+
+typedef struct {
+    double mx, my;          /* projected mean, pixel units */
+    double a, b, c;         /* conic: inverse of the 2D covariance */
+    double op;              /* sigmoid(opacity logit) */
+    double col[3];          /* max(rgb, 0) */
+    double lthr;            /* ln(alpha_min / opacity): power below it cannot reach alpha_min */
+    float depth;            /* FP32 view depth (sort key) */
+    int visible;
+} proj_t;
+
+typedef struct {
+    double R[9], t[3], fx, fy, cx, cy;
+    float Rf[9], tf[3];
+} rcam_t;
+
+static void rcam_setup(rcam_t* c, const float* cam) {
+    for (int k = 0; k < 9; ++k) { c->R[k] = cam[k]; c->Rf[k] = cam[k]; }
+    for (int k = 0; k < 3; ++k) { c->t[k] = cam[9 + k]; c->tf[k] = cam[9 + k]; }
+    c->fx = cam[15]; c->fy = cam[16]; c->cx = cam[17]; c->cy = cam[18];
+}
+
+static double sigmoid(double x) { return 1.0 / (1.0 + exp(-x)); }
+
+/* rotation matrix of the unit quaternion (w, x, y, z), row-major */
+static void quat_to_rot(const double q[4], double R[9]) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* FP32 view depth, operation order ((r20 x + r21 y) + r22 z) + t2 */
+static float view_depth_f32(const rcam_t* c, const float* m) {
+    float p0 = c->Rf[6] * m[0];
+    float p1 = c->Rf[7] * m[1];
+    float p2 = c->Rf[8] * m[2];
+    float s = p0 + p1;
+    s = s + p2;
+    return s + c->tf[2];
+}
+
+/* intermediate quantities of one projection, kept for the backward pass */
+typedef struct {
+    double qn[4], qnorm, Rq[9], s[3], M[9], Sig[9], t[3], J[6], Tm[6], A, B, Cc, det;
+} proj_aux_t;
+
+static void project_one(const float* p, const rcam_t* c, const double* cfg, proj_t* out, proj_aux_t* aux) {
+    proj_aux_t local;
+    proj_aux_t* x = aux ? aux : &local;
+    out->visible = 0;
+    out->depth = view_depth_f32(c, p);
+    if (!(out->depth > (float)cfg[3])) return;
+    double q[4] = {p[8], p[9], p[10], p[11]};
+    x->qnorm = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int k = 0; k < 4; ++k) x->qn[k] = q[k] / x->qnorm;
+    quat_to_rot(x->qn, x->Rq);
+    for (int k = 0; k < 3; ++k) x->s[k] = exp((double)p[4 + k]);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) x->M[3 * i + j] = x->Rq[3 * i + j] * x->s[j];
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) {
+            double acc = 0;
+            for (int j = 0; j < 3; ++j) acc += x->M[3 * i + j] * x->M[3 * k + j];
+            x->Sig[3 * i + k] = acc;
+        }
+    for (int m = 0; m < 3; ++m)
+        x->t[m] = c->R[3 * m] * p[0] + c->R[3 * m + 1] * p[1] + c->R[3 * m + 2] * p[2] + c->t[m];
+    double tx = x->t[0], ty = x->t[1], tz = x->t[2];
+    x->J[0] = c->fx / tz; x->J[1] = 0;            x->J[2] = -c->fx * tx / (tz * tz);
+    x->J[3] = 0;          x->J[4] = c->fy / tz;   x->J[5] = -c->fy * ty / (tz * tz);
+    for (int r = 0; r < 2; ++r)
+        for (int k = 0; k < 3; ++k) {
+            double acc = 0;
+            for (int m = 0; m < 3; ++m) acc += x->J[3 * r + m] * c->R[3 * m + k];
+            x->Tm[3 * r + k] = acc;
+        }
+    double S2[4];
+    for (int r = 0; r < 2; ++r)
+        for (int q2 = 0; q2 < 2; ++q2) {
+            double acc = 0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) acc += x->Tm[3 * r + i] * x->Sig[3 * i + j] * x->Tm[3 * q2 + j];
+            S2[2 * r + q2] = acc;
+        }
+    x->A = S2[0] + cfg[4];
+    x->B = S2[1];
+    x->Cc = S2[3] + cfg[4];
+    x->det = x->A * x->Cc - x->B * x->B;
+    if (!(x->det > 0)) return;
+    out->a = x->Cc / x->det;
+    out->b = -x->B / x->det;
+    out->c = x->A / x->det;
+    out->mx = c->fx * tx / tz + c->cx;
+    out->my = c->fy * ty / tz + c->cy;
+    out->op = sigmoid((double)p[3]);
+    out->lthr = log(cfg[1] / out->op);
+    for (int k = 0; k < 3; ++k) out->col[k] = p[12 + k] > 0.0f ? (double)p[12 + k] : 0.0;
+    out->visible = 1;
+}
+
+/* per-Gaussian projection: mx, my, a, b, c, opacity, r, g, b, depth, visible */
+void orc_project(int64_t N, const float* params, const float* cam, const double* cfg, double* out) {
+    rcam_t c;
+    rcam_setup(&c, cam);
+    for (int64_t g = 0; g < N; ++g) {
+        proj_t pr;
+        memset(&pr, 0, sizeof pr);
+        project_one(params + 16 * g, &c, cfg, &pr, NULL);
+        double* o = out + 11 * g;
+        o[0] = pr.mx; o[1] = pr.my; o[2] = pr.a; o[3] = pr.b; o[4] = pr.c; o[5] = pr.op;
+        o[6] = pr.col[0]; o[7] = pr.col[1]; o[8] = pr.col[2]; o[9] = pr.depth; o[10] = pr.visible;
+    }
+}
+
+typedef struct {
+    float depth;
+    int64_t idx;
+} order_t;
+
+static int order_cmp(const void* pa, const void* pb) {
+    const order_t* a = (const order_t*)pa;
+    const order_t* b = (const order_t*)pb;
+    if (a->depth < b->depth) return -1;
+    if (a->depth > b->depth) return 1;
+    return (a->idx > b->idx) - (a->idx < b->idx);
+}
+
+/* project all Gaussians, return the visible ones sorted by (depth, index) */
+static int64_t project_sorted(int64_t N, const float* params, const rcam_t* c, const double* cfg, proj_t* pr,
+                              int64_t* order, int nthreads) {
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int64_t g = 0; g < N; ++g) project_one(params + 16 * g, c, cfg, &pr[g], NULL);
+    order_t* tmp = (order_t*)malloc(sizeof(order_t) * (size_t)(N > 0 ? N : 1));
+    int64_t V = 0;
+    for (int64_t g = 0; g < N; ++g)
+        if (pr[g].visible) { tmp[V].depth = pr[g].depth; tmp[V].idx = g; ++V; }
+    qsort(tmp, (size_t)V, sizeof(order_t), order_cmp);
+    for (int64_t k = 0; k < V; ++k) order[k] = tmp[k].idx;
+    free(tmp);
+    return V;
+}
+
+static int near_rel(double x, double thr, double rel) { return fabs(x - thr) <= rel * fabs(thr); }
+
+#define MARGIN_REL 2e-4
+
+typedef struct {
+    int64_t g;
+    double alpha, T, G, dx, dy;
+    int clamped;
+} term_t;
+
+/*
+ * Walk one pixel front to back over the depth-ordered visible Gaussians.
+ * The plain definition: alpha = min(alpha_max, sigmoid(o) exp(-d^T conic d / 2)),
+ * terms with alpha < alpha_min are dropped, the walk stops before a term
+ * whose T (1 - alpha) < T_min, C = sum c alpha T.  Returns the number of
+ * composited terms; `terms` (optional, capacity cap) receives them.
+ * *marginal is set if a threshold decision lay within MARGIN_REL of its
+ * threshold (the FP32 kernel may decide it the other way).
+ */
+static int64_t walk_pixel(const proj_t* pr, const int64_t* order, int64_t V, const double* cfg, double px,
+                          double py, double C[3], double* T_final, int* marginal, term_t* terms, int64_t cap,
+                          int grad_margins) {
+    double amax = cfg[0], amin = cfg[1], tmin = cfg[2];
+    double T = 1.0;
+    int64_t n = 0;
+    C[0] = C[1] = C[2] = 0.0;
+    *marginal = 0;
+    for (int64_t k = 0; k < V; ++k) {
+        const proj_t* p = &pr[order[k]];
+        double dx = px - p->mx, dy = py - p->my;
+        double power = -0.5 * (p->a * dx * dx + p->c * dy * dy) - p->b * dx * dy;
+        /* cheap reject far below the alpha_min threshold, before exp */
+        if (power < p->lthr - 1e-3) continue;
+        double G = exp(power);
+        double araw = p->op * G;
+        if (near_rel(araw, amin, MARGIN_REL)) *marginal = 1;
+        if (grad_margins && near_rel(araw, amax, MARGIN_REL)) *marginal = 1;
+        double alpha = araw < amax ? araw : amax;
+        if (alpha < amin) continue;
+        double Tn = T * (1.0 - alpha);
+        if (near_rel(Tn, tmin, MARGIN_REL)) *marginal = 1;
+        if (Tn < tmin) break;
+        for (int ch = 0; ch < 3; ++ch) C[ch] += p->col[ch] * alpha * T;
+        if (terms && n < cap) {
+            term_t* t = &terms[n];
+            t->g = order[k]; t->alpha = alpha; t->T = T; t->G = G; t->dx = dx; t->dy = dy;
+            t->clamped = araw >= amax;
+        }
+        ++n;
+        T = Tn;
+    }
+    *T_final = T;
+    return n;
+}
+
+/*
+ * Forward render of the pixel window [x0, x0 + w) x [y0, y0 + h) of a W x H
+ * camera.  Pixel (i, j) is sampled at its centre (i + 0.5, j + 0.5);
+ * background 0.  image: 3 x h x w; marginal, ncontrib: h x w (optional).
+ */
+int orc_render(int64_t N, const float* params, const float* cam, const double* cfg, int x0, int y0, int w, int h,
+               double* image, uint8_t* marginal, int32_t* ncontrib, double* T_final, int nthreads) {
+    rcam_t c;
+    rcam_setup(&c, cam);
+    proj_t* pr = (proj_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(proj_t));
+    int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    if (!pr || !order) { free(pr); free(order); return 2; }
+    int64_t V = project_sorted(N, params, &c, cfg, pr, order, nthreads);
+    long WH = (long)w * h;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+    for (int jj = 0; jj < h; ++jj) {
+        for (int ii = 0; ii < w; ++ii) {
+            double C[3], T;
+            int marg;
+            int64_t n = walk_pixel(pr, order, V, cfg, x0 + ii + 0.5, y0 + jj + 0.5, C, &T, &marg, NULL, 0, 0);
+            long p = (long)jj * w + ii;
+            for (int ch = 0; ch < 3; ++ch) image[ch * WH + p] = C[ch];
+            if (marginal) marginal[p] = (uint8_t)marg;
+            if (ncontrib) ncontrib[p] = (int32_t)n;
+            if (T_final) T_final[p] = T;
+        }
+    }
+    free(pr);
+    free(order);
+    return 0;
+}
+
+/*
+ * Backward of a project step, from 2D gradients to the packed parameter
+ * gradient (chain rule through conic = inverse(J W Sigma W^T J^T + dil I),
+ * Sigma = R(q/|q|) diag(exp(ls))^2 R^T, the pinhole projection of the mean).
+ * g2: dL/d{mx, my, a, b, c, opacity logit, r, g, b}.  grad: 16 floats (+=).
+ */
+static void project_backward_one(const float* p, const rcam_t* c, const double* cfg, const double* g2,
+                                 double* grad) {
+    proj_t pr;
+    proj_aux_t x;
+    project_one(p, c, cfg, &pr, &x);
+    if (!pr.visible) return;
+    double A = x.A, B = x.B, Cc = x.Cc, det2 = x.det * x.det;
+    double ga = g2[2], gb = g2[3], gc = g2[4];
+    /* d conic / d (A, B, Cc) of a = Cc/det, b = -B/det, c = A/det */
+    double dA = (ga * (-Cc * Cc) + gb * (B * Cc) + gc * (-B * B)) / det2;
+    double dB = (ga * (2 * B * Cc) + gb * (-(A * Cc + B * B)) + gc * (2 * A * B)) / det2;
+    double dC = (ga * (-B * B) + gb * (A * B) + gc * (-A * A)) / det2;
+    /* A = Tm0 Sig Tm0^T, B = Tm0 Sig Tm1^T, Cc = Tm1 Sig Tm1^T */
+    const double* Tm0 = x.Tm;
+    const double* Tm1 = x.Tm + 3;
+    double G[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            G[3 * i + j] = dA * Tm0[i] * Tm0[j] + dB * Tm0[i] * Tm1[j] + dC * Tm1[i] * Tm1[j];
+    double ST0[3], ST1[3];
+    for (int k = 0; k < 3; ++k) {
+        ST0[k] = x.Sig[3 * k] * Tm0[0] + x.Sig[3 * k + 1] * Tm0[1] + x.Sig[3 * k + 2] * Tm0[2];
+        ST1[k] = x.Sig[3 * k] * Tm1[0] + x.Sig[3 * k + 1] * Tm1[1] + x.Sig[3 * k + 2] * Tm1[2];
+    }
+    double dTm[6];
+    for (int k = 0; k < 3; ++k) {
+        dTm[k] = 2 * dA * ST0[k] + dB * ST1[k];
+        dTm[3 + k] = dB * ST0[k] + 2 * dC * ST1[k];
+    }
+    /* Tm = J R_w */
+    double dJ[6];
+    for (int r = 0; r < 2; ++r)
+        for (int m = 0; m < 3; ++m) {
+            double acc = 0;
+            for (int k = 0; k < 3; ++k) acc += dTm[3 * r + k] * c->R[3 * m + k];
+            dJ[3 * r + m] = acc;
+        }
+    double tx = x.t[0], ty = x.t[1], tz = x.t[2];
+    double tz2 = tz * tz, tz3 = tz2 * tz;
+    double dt[3] = {0, 0, 0};
+    dt[0] += dJ[2] * (-c->fx / tz2);
+    dt[1] += dJ[5] * (-c->fy / tz2);
+    dt[2] += dJ[0] * (-c->fx / tz2) + dJ[2] * (2 * c->fx * tx / tz3) + dJ[4] * (-c->fy / tz2) +
+             dJ[5] * (2 * c->fy * ty / tz3);
+    /* mean2D = (fx tx / tz + cx, fy ty / tz + cy) */
+    dt[0] += g2[0] * c->fx / tz;
+    dt[2] += g2[0] * (-c->fx * tx / tz2);
+    dt[1] += g2[1] * c->fy / tz;
+    dt[2] += g2[1] * (-c->fy * ty / tz2);
+    /* t = R_w mean + t_w */
+    for (int k = 0; k < 3; ++k) grad[k] += c->R[k] * dt[0] + c->R[3 + k] * dt[1] + c->R[6 + k] * dt[2];
+    /* Sigma = M M^T, M = R_q diag(s): dL/dM = (G + G^T) M */
+    double dM[9];
+    for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) {
+            double acc = 0;
+            for (int j = 0; j < 3; ++j) acc += (G[3 * k + j] + G[3 * j + k]) * x.M[3 * j + l];
+            dM[3 * k + l] = acc;
+        }
+    double dR[9];
+    for (int l = 0; l < 3; ++l) {
+        double ds = 0;
+        for (int k = 0; k < 3; ++k) {
+            ds += dM[3 * k + l] * x.Rq[3 * k + l];
+            dR[3 * k + l] = dM[3 * k + l] * x.s[l];
+        }
+        grad[4 + l] += ds * x.s[l];
+    }
+    /* rotation matrix of the normalised quaternion */
+    double w = x.qn[0], qx = x.qn[1], qy = x.qn[2], qz = x.qn[3];
+    double dq[4];
+    dq[0] = 2 * (-qz * dR[1] + qy * dR[2] + qz * dR[3] - qx * dR[5] - qy * dR[6] + qx * dR[7]);
+    dq[1] = 2 * (qy * dR[1] + qz * dR[2] + qy * dR[3] - w * dR[5] + qz * dR[6] + w * dR[7]) -
+            4 * qx * (dR[4] + dR[8]);
+    dq[2] = 2 * (qx * dR[1] + w * dR[2] + qx * dR[3] + qz * dR[5] - w * dR[6] + qz * dR[7]) -
+            4 * qy * (dR[0] + dR[8]);
+    dq[3] = 2 * (-w * dR[1] + qx * dR[2] + w * dR[3] + qy * dR[5] + qx * dR[6] + qy * dR[7]) -
+            4 * qz * (dR[0] + dR[4]);
+    double dot = w * dq[0] + qx * dq[1] + qy * dq[2] + qz * dq[3];
+    for (int k = 0; k < 4; ++k) grad[8 + k] += (dq[k] - x.qn[k] * dot) / x.qnorm;
+    grad[3] += g2[5];
+    for (int k = 0; k < 3; ++k) grad[12 + k] += g2[6 + k];
+}
+
+/*
+ * Gradient of the window render w.r.t. the packed parameters, given
+ * dL/dimage (3 x h x w).  grads: N x 16 (+=).  g2d (optional): N x 9 2D
+ * gradients dL/d{mx, my, a, b, c, opacity logit, r, g, b} (+=).
+ */
+int orc_render_backward(int64_t N, const float* params, const float* cam, const double* cfg, int x0, int y0, int w,
+                        int h, const double* dL_dimage, double* grads, double* g2d, int nthreads) {
+    rcam_t c;
+    rcam_setup(&c, cam);
+    proj_t* pr = (proj_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(proj_t));
+    int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    double* acc = (double*)calloc((size_t)(N > 0 ? N : 1) * 9, sizeof(double));
+    if (!pr || !order || !acc) { free(pr); free(order); free(acc); return 2; }
+    int64_t V = project_sorted(N, params, &c, cfg, pr, order, nthreads);
+    long WH = (long)w * h;
+#pragma omp parallel num_threads(nthreads)
+    {
+        int64_t cap = 4096;
+        term_t* terms = (term_t*)malloc(sizeof(term_t) * (size_t)cap);
+#pragma omp for schedule(dynamic, 1)
+        for (int jj = 0; jj < h; ++jj) {
+            for (int ii = 0; ii < w; ++ii) {
+                long p = (long)jj * w + ii;
+                double gC[3] = {dL_dimage[p], dL_dimage[WH + p], dL_dimage[2 * WH + p]};
+                if (gC[0] == 0 && gC[1] == 0 && gC[2] == 0) continue;
+                double C[3], T;
+                int marg;
+                int64_t n = walk_pixel(pr, order, V, cfg, x0 + ii + 0.5, y0 + jj + 0.5, C, &T, &marg, terms, cap, 1);
+                if (n > cap) {
+                    cap = n;
+                    terms = (term_t*)realloc(terms, sizeof(term_t) * (size_t)cap);
+                    n = walk_pixel(pr, order, V, cfg, x0 + ii + 0.5, y0 + jj + 0.5, C, &T, &marg, terms, cap, 1);
+                }
+                double S[3] = {0, 0, 0};
+                for (int64_t k = n - 1; k >= 0; --k) {
+                    const term_t* t = &terms[k];
+                    const proj_t* q = &pr[t->g];
+                    const float* pp = params + 16 * t->g;
+                    double* a9 = acc + 9 * t->g;
+                    double dalpha = 0;
+                    for (int ch = 0; ch < 3; ++ch) {
+                        if (pp[12 + ch] > 0.0f) {
+#pragma omp atomic
+                            a9[6 + ch] += t->alpha * t->T * gC[ch];
+                        }
+                        dalpha += gC[ch] * (q->col[ch] * t->T - S[ch] / (1.0 - t->alpha));
+                        S[ch] += q->col[ch] * t->alpha * t->T;
+                    }
+                    if (t->clamped) continue;
+                    double dop = dalpha * t->G * q->op * (1.0 - q->op);
+                    double dpow = dalpha * t->alpha;
+                    double v[5];
+                    v[0] = dpow * (q->a * t->dx + q->b * t->dy);
+                    v[1] = dpow * (q->b * t->dx + q->c * t->dy);
+                    v[2] = dpow * (-0.5 * t->dx * t->dx);
+                    v[3] = dpow * (-t->dx * t->dy);
+                    v[4] = dpow * (-0.5 * t->dy * t->dy);
+                    for (int k5 = 0; k5 < 5; ++k5) {
+#pragma omp atomic
+                        a9[k5] += v[k5];
+                    }
+#pragma omp atomic
+                    a9[5] += dop;
+                }
+            }
+        }
+        free(terms);
+    }
+    if (g2d)
+        for (int64_t g = 0; g < 9 * N; ++g) g2d[g] += acc[g];
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int64_t g = 0; g < N; ++g) {
+        const double* a9 = acc + 9 * g;
+        int any = 0;
+        for (int k = 0; k < 9; ++k) any |= a9[k] != 0;
+        if (any) project_backward_one(params + 16 * g, &c, cfg, a9, grads + 16 * g);
+    }
+    free(pr);
+    free(order);
+    free(acc);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* losses                                                                    */
+
+/*
+ * HDR loss of Sec. 3.6: mean over the k = C h w crop elements of
+ * (x - y)^2 / (y + 0.01)^2 with x the (noisy) target and y the prediction.
+ * full_grad = 0 treats the denominator as a constant (stop-gradient),
+ * 1 differentiates it too.  crop = {x0, y0, w, h} or NULL (whole image);
+ * dL_dpred is zero outside the crop.
+ */
+double orc_loss_hdr(const float* pred, const float* target, int C, int H, int W, const int* crop, int full_grad,
+                    double* dL_dpred) {
+    int x0 = 0, y0 = 0, w = W, h = H;
+    if (crop) { x0 = crop[0]; y0 = crop[1]; w = crop[2]; h = crop[3]; }
+    double k = (double)C * w * h, loss = 0;
+    if (dL_dpred) memset(dL_dpred, 0, sizeof(double) * (size_t)C * H * W);
+    for (int ch = 0; ch < C; ++ch)
+        for (int j = y0; j < y0 + h; ++j)
+            for (int i = x0; i < x0 + w; ++i) {
+                long p = ((long)ch * H + j) * W + i;
+                double y = pred[p], x = target[p], den = y + 0.01;
+                loss += (x - y) * (x - y) / (den * den);
+                if (dL_dpred) {
+                    double g = 2.0 * (y - x) / (den * den);
+                    if (full_grad) g -= 2.0 * (x - y) * (x - y) / (den * den * den);
+                    dL_dpred[p] = g / k;
+                }
+            }
+    return loss / k;
+}
+
+/* 11-tap Gaussian window, sigma 1.5, normalised to sum 1 */
+static void ssim_window(double wnd[11]) {
+    double s = 0;
+    for (int i = 0; i < 11; ++i) { wnd[i] = exp(-((i - 5) * (i - 5)) / (2.0 * 1.5 * 1.5)); s += wnd[i]; }
+    for (int i = 0; i < 11; ++i) wnd[i] /= s;
+}
+
+/* zero-padded 'same' 2D filtering with the separable window (it is symmetric,
+   so correlation and convolution coincide) */
+static void filter2(const double* in, double* out, int h, int w, const double wnd[11]) {
+    double* tmp = (double*)calloc((size_t)h * w, sizeof(double));
+    for (int j = 0; j < h; ++j)
+        for (int i = 0; i < w; ++i) {
+            double acc = 0;
+            for (int k = -5; k <= 5; ++k) {
+                int ii = i + k;
+                if (ii >= 0 && ii < w) acc += wnd[k + 5] * in[(long)j * w + ii];
+            }
+            tmp[(long)j * w + i] = acc;
+        }
+    for (int j = 0; j < h; ++j)
+        for (int i = 0; i < w; ++i) {
+            double acc = 0;
+            for (int k = -5; k <= 5; ++k) {
+                int jj = j + k;
+                if (jj >= 0 && jj < h) acc += wnd[k + 5] * tmp[(long)jj * w + i];
+            }
+            out[(long)j * w + i] = acc;
+        }
+    free(tmp);
+}
+
+/*
+ * 0.8 L1 + 0.2 (1 - SSIM) over the crop (treated as its own zero-padded
+ * image), SSIM of Wang et al. 2004 per channel with an 11x11 Gaussian
+ * window (sigma 1.5), C1 = 0.01^2, C2 = 0.03^2, mean over channels and
+ * pixels.  ssim_map (optional): C x h x w.
+ */
+double orc_loss_l1ssim(const float* pred, const float* target, int C, int H, int W, const int* crop,
+                       double* dL_dpred, double* ssim_map) {
+    int x0 = 0, y0 = 0, w = W, h = H;
+    if (crop) { x0 = crop[0]; y0 = crop[1]; w = crop[2]; h = crop[3]; }
+    const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;
+    double wnd[11];
+    ssim_window(wnd);
+    long n = (long)w * h;
+    double k = (double)C * n;
+    double l1 = 0, ssim_sum = 0;
+    if (dL_dpred) memset(dL_dpred, 0, sizeof(double) * (size_t)C * H * W);
+    double* buf = (double*)malloc(sizeof(double) * (size_t)n * 13);
+    double *x = buf, *y = buf + n, *xx = buf + 2 * n, *yy = buf + 3 * n, *xy = buf + 4 * n;
+    double *mx = buf + 5 * n, *my = buf + 6 * n, *exx = buf + 7 * n, *eyy = buf + 8 * n, *exy = buf + 9 * n;
+    double *gmu = buf + 10 * n, *gxx = buf + 11 * n, *gxy = buf + 12 * n;
+    for (int ch = 0; ch < C; ++ch) {
+        for (int j = 0; j < h; ++j)
+            for (int i = 0; i < w; ++i) {
+                long p = ((long)ch * H + (y0 + j)) * W + (x0 + i), q = (long)j * w + i;
+                x[q] = pred[p]; y[q] = target[p];
+                xx[q] = x[q] * x[q]; yy[q] = y[q] * y[q]; xy[q] = x[q] * y[q];
+                double d = x[q] - y[q];
+                l1 += fabs(d);
+                if (dL_dpred) dL_dpred[p] = 0.8 * (d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0)) / k;
+            }
+        filter2(x, mx, h, w, wnd);
+        filter2(y, my, h, w, wnd);
+        filter2(xx, exx, h, w, wnd);
+        filter2(yy, eyy, h, w, wnd);
+        filter2(xy, exy, h, w, wnd);
+        for (long q = 0; q < n; ++q) {
+            double sxx = exx[q] - mx[q] * mx[q], syy = eyy[q] - my[q] * my[q], sxy = exy[q] - mx[q] * my[q];
+            double A1 = 2 * mx[q] * my[q] + C1, A2 = 2 * sxy + C2;
+            double B1 = mx[q] * mx[q] + my[q] * my[q] + C1, B2 = sxx + syy + C2;
+            double s = (A1 * A2) / (B1 * B2);
+            ssim_sum += s;
+            if (ssim_map) ssim_map[(long)ch * n + q] = s;
+            /* partials of s w.r.t. mu_x, E[x^2], E[xy] (mu_y, E[y^2] are constants) */
+            double dA1 = 2 * my[q], dA2 = -2 * my[q], dB1 = 2 * mx[q], dB2 = -2 * mx[q];
+            gmu[q] = (dA1 * A2 + A1 * dA2) / (B1 * B2) - s * (dB1 * B2 + B1 * dB2) / (B1 * B2);
+            gxx[q] = -s / B2;
+            gxy[q] = 2 * A1 / (B1 * B2);
+        }
+        if (dL_dpred) {
+            /* d mean(s) / d x_q = (w * gmu)(q) + 2 x_q (w * gxx)(q) + y_q (w * gxy)(q), over n */
+            filter2(gmu, mx, h, w, wnd);
+            filter2(gxx, exx, h, w, wnd);
+            filter2(gxy, exy, h, w, wnd);
+            for (int j = 0; j < h; ++j)
+                for (int i = 0; i < w; ++i) {
+                    long p = ((long)ch * H + (y0 + j)) * W + (x0 + i), q = (long)j * w + i;
+                    double ds = mx[q] + 2 * x[q] * exx[q] + y[q] * exy[q];
+                    dL_dpred[p] += -0.2 * ds / k;
+                }
+        }
+    }
+    free(buf);
+    return 0.8 * l1 / k + 0.2 * (1.0 - ssim_sum / k);
+}
+
+/* ------------------------------------------------------------------------ */
+/* AdamW (Sec. 3.6 "Regularization"; Loshchilov & Hutter's decoupled decay)  */
+/* per element e of slot e % 16: lr_e = lr[slot] * lr_scale;                */
+/* m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;                               */
+/* p -= lr_e (m / (1-b1^t) / (sqrt(v / (1-b2^t)) + eps) + wd p); g = 0.      */
+/* Slots with lr 0 are left untouched (no decay).                           */
+
+void orc_adamw(int64_t n, double* p, double* g, double* m, double* v, const double* lr, double lr_scale,
+               double b1, double b2, double eps, double wd, int step) {
+    double bc1 = 1.0 - pow(b1, step), bc2 = 1.0 - pow(b2, step);
+    for (int64_t e = 0; e < n; ++e) {
+        double lre = lr[e % 16] * lr_scale;
+        if (lre != 0.0) {
+            m[e] = b1 * m[e] + (1.0 - b1) * g[e];
+            v[e] = b2 * v[e] + (1.0 - b2) * g[e] * g[e];
+            double mh = m[e] / bc1, vh = v[e] / bc2;
+            p[e] -= lre * (mh / (sqrt(vh) + eps) + wd * p[e]);
+        }
+        g[e] = 0.0;
+    }
+}
+
+/* Eq. 4: eta_t = eta_0 / (1 + ln t), t >= 1 frames of a static viewport */
+double orc_lr_scale(int t) { return 1.0 / (1.0 + log((double)(t < 1 ? 1 : t))); }
+
+/* cache memory of Table 3: 14 FP32 attributes per Gaussian */
+int64_t orc_cache_bytes(int64_t n) { return n * 14 * 4; }

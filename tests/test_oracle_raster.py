@@ -1,0 +1,222 @@
+"""Pins of the oracle rasterizer (Gaussian splatting of one cache level,
+Sec. 3.1) and of its analytic backward (the inverse splatting step, Sec. 3.5).
+
+The forward is pinned by closed forms of special cases (an isotropic Gaussian
+on the optical axis, a rotated anisotropic one, opaque fronts, the near
+plane), by compositing invariants (associativity of front and back groups,
+invariance to input order) and by Table 3's byte counts; the backward by
+central finite differences of the FP64 forward for every parameter kind.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2507_19718_gb300 import synth
+
+CFG = dict(alpha_max=0.99, alpha_min=1 / 255, T_min=1e-4, near=0.2, dilation=0.3)
+
+
+def _one(mean, logscale, quat, logit, rgb):
+    p = np.zeros((1, 16), np.float32)
+    p[0, 0:3] = mean
+    p[0, 3] = logit
+    p[0, 4:7] = logscale
+    p[0, 8:12] = quat
+    p[0, 12:15] = rgb
+    return p
+
+
+def _axis_cam(W=65, H=65, fx=80.0, fy=60.0):
+    cam = synth.axis_camera(W, H, z=-1.0)
+    cam.fx, cam.fy = fx, fy
+    cam.cx, cam.cy = W / 2.0, H / 2.0
+    return cam
+
+
+def test_isotropic_gaussian_on_axis_closed_form(orc):
+    """A sphere-shaped Gaussian of std s at depth z on the optical axis images
+    to a 2D Gaussian with std (f s / z) per axis, widened by the 0.3 px^2
+    dilation; its peak alpha is its opacity sigmoid(o)."""
+    cam = _axis_cam()
+    s, zc, logit = 0.05, 1.5, 0.4
+    tz = zc + 1.0
+    p = _one([0.5, 0.5, zc], [math.log(s)] * 3, [1, 0, 0, 0], logit, [1.0, 0.5, 0.25])
+    img, marg, ncon, _ = orc.render(p, cam, CFG)
+    logit, s, tz = float(p[0, 3]), math.exp(float(p[0, 4])), float(p[0, 2]) + 1.0
+    op = 1 / (1 + math.exp(-logit))
+    vx = (cam.fx * s / tz) ** 2 + 0.3
+    vy = (cam.fy * s / tz) ** 2 + 0.3
+    jj, ii = np.mgrid[0:65, 0:65]
+    dx, dy = ii + 0.5 - 32.5, jj + 0.5 - 32.5
+    alpha = op * np.exp(-0.5 * (dx * dx / vx + dy * dy / vy))
+    alpha = np.where(alpha >= 1 / 255, np.minimum(alpha, 0.99), 0.0)
+    assert img[0, 32, 32] == pytest.approx(op, rel=1e-12)
+    for ch, c in enumerate([1.0, 0.5, 0.25]):
+        np.testing.assert_allclose(img[ch], c * alpha, rtol=1e-10, atol=1e-14)
+    assert ncon.max() == 1
+
+
+def test_off_axis_isotropic_gaussian_closed_form(orc):
+    """Off the axis, an isotropic 3D Gaussian images with covariance
+    s^2 J J^T + 0.3 I, J the pinhole Jacobian at its camera-space mean, and is
+    centred at the perspective projection of its mean."""
+    cam = _axis_cam(W=96, H=80, fx=70.0, fy=90.0)
+    mean = np.array([0.8, 0.35, 1.2])
+    s = 0.06
+    p = _one(mean, [math.log(s)] * 3, [0.3, 0, 0, 0], 1.0, [1, 1, 1])
+    t = p[0, 0:3].astype(np.float64) + cam.t.astype(np.float64)
+    s = math.exp(float(p[0, 4]))
+    img, _, _, _ = orc.render(p, cam, CFG)
+    J = np.array([[cam.fx / t[2], 0, -cam.fx * t[0] / t[2] ** 2], [0, cam.fy / t[2], -cam.fy * t[1] / t[2] ** 2]])
+    cov = s * s * J @ J.T + 0.3 * np.eye(2)
+    mu = np.array([cam.fx * t[0] / t[2] + cam.cx, cam.fy * t[1] / t[2] + cam.cy])
+    jj, ii = np.mgrid[0:80, 0:96]
+    d = np.stack([ii + 0.5 - mu[0], jj + 0.5 - mu[1]], -1)
+    q = np.einsum("...i,ij,...j->...", d, np.linalg.inv(cov), d)
+    alpha = (1 / (1 + math.exp(-1.0))) * np.exp(-0.5 * q)
+    alpha = np.where(alpha >= 1 / 255, np.minimum(alpha, 0.99), 0.0)
+    np.testing.assert_allclose(img[1], alpha, rtol=1e-9, atol=1e-13)
+
+
+def test_rotated_anisotropic_gaussian_axes(orc):
+    """q = (cos th/2, 0, 0, sin th/2) turns the Gaussian's x axis to
+    (cos th, sin th) in the image (x right, y down): along it the std is
+    f s1 / z, across it f s2 / z (plus dilation)."""
+    cam = _axis_cam(W=65, H=65, fx=90.0, fy=90.0)
+    th = math.atan2(3.0, 4.0)
+    s1, s2, zc = 0.09, 0.03, 1.0
+    tz = zc + 1.0
+    p = _one([0.5, 0.5, zc], [math.log(s1), math.log(s2), math.log(0.05)],
+             [math.cos(th / 2), 0, 0, math.sin(th / 2)], 3.0, [1, 1, 1])
+    img, _, _, _ = orc.render(p, cam, CFG)
+    op = min(0.99, 1 / (1 + math.exp(-3.0)))
+    s1, s2 = math.exp(float(p[0, 4])), math.exp(float(p[0, 5]))
+    v1 = (90.0 * s1 / tz) ** 2 + 0.3
+    v2 = (90.0 * s2 / tz) ** 2 + 0.3
+    for k in range(1, 4):
+        # along (0.8, 0.6): pixel offset (4k, 3k), distance 5k
+        a_along = op * math.exp(-0.5 * (5 * k) ** 2 / v1)
+        a_across = op * math.exp(-0.5 * (5 * k) ** 2 / v2)
+        got_along = img[0, 32 + 3 * k, 32 + 4 * k]
+        got_across = img[0, 32 + 4 * k, 32 - 3 * k]
+        assert got_along == pytest.approx(a_along if a_along >= 1 / 255 else 0.0, rel=1e-9, abs=1e-14)
+        assert got_across == pytest.approx(a_across if a_across >= 1 / 255 else 0.0, rel=1e-9, abs=1e-14)
+
+
+def test_opaque_fronts_occlude(orc):
+    """Front-to-back compositing with alpha clamped to alpha_max: the second
+    layer is weighted by (1 - alpha_max); a third layer would drive T below
+    T_min, so the walk stops and nothing behind contributes."""
+    cam = _axis_cam(W=33, H=33, fx=40.0, fy=40.0)
+    cfg = dict(CFG, alpha_max=0.98)
+    cols = [[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1]]
+    p = np.concatenate([_one([0.5, 0.5, z], [math.log(0.3)] * 3, [1, 0, 0, 0], 12.0, c)
+                        for z, c in zip([0.2, 0.4, 0.6, 0.8], cols)])
+    img, _, ncon, tfin = orc.render(p, cam, cfg)
+    np.testing.assert_allclose(img[:, 16, 16], [0.98, 0.98 * 0.02, 0.0], rtol=1e-12)
+    assert ncon[16, 16] == 2
+    assert tfin[16, 16] == pytest.approx(0.02 * 0.02, rel=1e-12)
+    # the order of the inputs does not matter, only their depth
+    img2, _, _, _ = orc.render(p[::-1].copy(), cam, cfg)
+    np.testing.assert_array_equal(img, img2)
+
+
+def test_near_plane_culls(orc):
+    cam = _axis_cam(W=33, H=33, fx=40.0, fy=40.0)
+    # camera at z = -1: depth 0.1 is in front of the camera but before near = 0.2
+    p = _one([0.5, 0.5, -0.9], [math.log(0.2)] * 3, [1, 0, 0, 0], 2.0, [1, 1, 1])
+    img, _, _, _ = orc.render(p, cam, CFG)
+    assert np.all(img == 0)
+    p[0, 2] = -0.7  # depth 0.3
+    img, _, _, _ = orc.render(p, cam, CFG)
+    assert img.max() > 0.5
+
+
+def test_front_back_groups_compose(orc):
+    """C(A u B) = C(A) + T(A) C(B) when every Gaussian of A lies in front of
+    every Gaussian of B (and T stays above T_min); T(A u B) = T(A) T(B)."""
+    cam = synth.orbit_camera(48, 40, 30.0)
+    rng = np.random.default_rng(11)
+    A = synth.gaussians(40, 1, lo=0.35, hi=0.65, logscale_mean=-2.6)
+    B = synth.gaussians(40, 2, lo=0.35, hi=0.65, logscale_mean=-2.6)
+    # push B far behind A along the view direction
+    fwd = cam.R[2].astype(np.float64)
+    B[:, 0:3] = (B[:, 0:3] + 1.5 * fwd).astype(np.float32)
+    A[:, 3] = rng.normal(-2.5, 0.3, 40)
+    B[:, 3] = rng.normal(-2.5, 0.3, 40)
+    ia, ma, _, ta = orc.render(A, cam, CFG)
+    ib, mb, _, tb = orc.render(B, cam, CFG)
+    iab, mab, _, tab = orc.render(np.concatenate([A, B]), cam, CFG)
+    assert tab.min() > 1e-3
+    np.testing.assert_allclose(iab, ia + ta[None] * ib, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(tab, ta * tb, rtol=1e-12)
+    assert ia.max() > 0.02 and ib.max() > 0.01
+
+
+def test_input_order_invariance(orc):
+    cam = synth.orbit_camera(40, 32, 75.0)
+    p = synth.gaussians(200, 5, lo=0.2, hi=0.8, logscale_mean=-2.8)
+    perm = np.random.default_rng(0).permutation(200)
+    i1, _, _, _ = orc.render(p, cam, CFG)
+    i2, _, _, _ = orc.render(p[perm], cam, CFG)
+    np.testing.assert_array_equal(i1, i2)
+    assert i1.max() > 0.1
+
+
+def test_window_matches_full_frame(orc):
+    cam = synth.orbit_camera(40, 32, 10.0)
+    p = synth.gaussians(150, 6, lo=0.2, hi=0.8, logscale_mean=-2.8)
+    full, _, _, _ = orc.render(p, cam, CFG)
+    win, _, _, _ = orc.render(p, cam, CFG, window=(7, 5, 20, 13))
+    np.testing.assert_array_equal(win, full[:, 5:18, 7:27])
+
+
+def test_table3_memory(orc):
+    path = os.path.join(os.path.dirname(__file__), "golden", "table3_memory.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            n, b = map(int, line.split())
+            assert orc.cache_bytes(n) == b
+    assert sum(synth.level_sizes(525000, 3)) == 525000
+    assert synth.level_sizes(525000, 3) == [300000, 150000, 75000]
+
+
+# ----------------------------------------------------------------- backward
+
+def _fd_scene():
+    cam = synth.orbit_camera(36, 30, 40.0, radius=2.0)
+    p = synth.gaussians(18, 21, lo=0.3, hi=0.7, logscale_mean=-2.4, logscale_std=0.3)
+    p[:, 3] = np.random.default_rng(22).normal(-0.5, 0.8, len(p))
+    p[3, 12] = -0.2  # one clamped colour channel: its gradient must be 0
+    return cam, p
+
+
+@pytest.mark.parametrize("slot", [0, 1, 2, 3, 4, 5, 6, 8, 9, 10, 11, 12, 13, 14])
+def test_backward_matches_finite_differences(orc, slot):
+    cam, p = _fd_scene()
+    rng = np.random.default_rng(100 + slot)
+    W = rng.uniform(-1, 1, (3, cam.height, cam.width))
+    grads, _ = orc.render_backward(p, cam, W, CFG)
+    _, _, ncon0, _ = orc.render(p, cam, CFG)
+    h = 1e-4
+    checked = 0
+    gmax = np.abs(grads[:, slot]).max()
+    for g in range(len(p)):
+        pp, pm = p.copy(), p.copy()
+        pp[g, slot] = np.float32(p[g, slot] + h)
+        pm[g, slot] = np.float32(p[g, slot] - h)
+        heff = (np.float64(pp[g, slot]) - np.float64(pm[g, slot])) / 2
+        ip, _, ncp, _ = orc.render(pp, cam, CFG)
+        im, _, ncm, _ = orc.render(pm, cam, CFG)
+        if not (np.array_equal(ncp, ncon0) and np.array_equal(ncm, ncon0)):
+            continue  # the perturbation crossed a threshold: not differentiable here
+        fd = (np.sum(W * ip) - np.sum(W * im)) / (2 * heff)
+        an = grads[g, slot]
+        assert abs(fd - an) <= 2e-4 * max(abs(an), 1e-3 * gmax) + 1e-10, (g, slot, fd, an)
+        checked += 1
+    assert checked >= len(p) // 2
+    if slot == 12:
+        assert grads[3, 12] == 0.0
+    assert gmax > 0
