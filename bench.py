@@ -1,0 +1,405 @@
+#!/usr/bin/env python3
+"""Benchmark of the GSCache hot path on GB300: cache train + render ms/frame
+at 1920x1080 with 1M Gaussians.
+
+One step = one frame of the whole hot path: path-trace the 3 target buffers
+(1 spp, 8 bounces, 256^3 fBm volume, directional + environment light), then
+for each of the 3 cache levels (571,429 + 285,714 + 142,857 Gaussians, the
+paper's N/2^i split) render, HDR loss, backward and AdamW.  `value` is the
+cache train + render time per frame (every stage but the tracer, as the
+paper's ST + OT), `ms_per_step` the whole frame.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per GPU, launched by torchrun); the
+path has no exchange step, so there is no data-path collective.  The
+reference arm times the CPU oracle on a bounded sample of the same frame.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cache train+render ms/frame @1080p,1M Gaussians; served p50/p99 frame latency"
+WIDTH, HEIGHT = 1920, 1080
+TOTAL_GAUSSIANS = 1_000_000
+LEVELS = 3
+SPP, BOUNCES = 1, 8
+ORBIT_DEG_PER_FRAME = 0.5
+TILE, LIST_CAP = (16, 16), 256
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP32 FMA lanes: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def workload_config():
+    from paper_2507_19718_gb300 import synth
+    sizes = synth.level_sizes(TOTAL_GAUSSIANS, LEVELS)
+    return {
+        "workload": "1080p GSCache frame: trace 1spp/8 bounces -> 3 target buffers; 3 cache levels "
+                    "(1M Gaussians) render + HDR loss + backward + AdamW",
+        "width": WIDTH, "height": HEIGHT, "gaussians": TOTAL_GAUSSIANS, "levels": sizes, "spp": SPP,
+        "max_bounces": BOUNCES, "volume": "256^3 fp32: 64 blobs + 4-octave fBm, 8-point TF",
+        "lights": "directional 3.0 + environment 0.3", "tile": list(TILE), "list_capacity": LIST_CAP,
+        "camera": f"orbit r=2.2, fov_y 45 deg, {ORBIT_DEG_PER_FRAME} deg/frame",
+        "l2": "inputs larger than L2 (params+moments 256 MB, pair buffers GBs)", "parallelism": "replicas",
+    }
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ roofline
+
+def phase_algorithmic(phase, c, n_gauss_calls, n_pixels_calls, frames):
+    """(kind, amount per timed region): bytes for HBM-bound phases, FP32 flops
+    for the compositing kernels; the per-unit figures are stated in the
+    design notes."""
+    M = c["pairs_sum"]
+    if phase == "render":
+        return "flop", 10.0 * c["eval_fwd"] + 13.0 * c["composited_fwd"]
+    if phase == "render_bwd":
+        return "flop", 10.0 * c["eval_rewalk"] + 40.0 * c["eval_back"]
+    if phase == "tile_sort":
+        return "byte", 2 * 20.0 * M
+    if phase == "depth_sort":
+        return "byte", 4 * 20.0 * n_gauss_calls
+    if phase == "emit":
+        return "byte", 8.0 * M + 20.0 * n_gauss_calls
+    if phase == "ranges":
+        return "byte", 4.0 * M
+    if phase == "project":
+        return "byte", 132.0 * n_gauss_calls
+    if phase == "scan":
+        return "byte", 20.0 * n_gauss_calls
+    if phase == "project_bwd":
+        return "byte", 244.0 * n_gauss_calls / 2
+    if phase == "adamw":
+        return "byte", 512.0 * n_gauss_calls / 2
+    if phase == "loss":
+        return "byte", 12.0 * n_pixels_calls
+    return None, 0.0
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2507_19718_gb300 import build, gsc, synth
+    from paper_2507_19718_gb300.frame import FrameLoop
+
+    build.build()
+    gsc.lib(build_if_missing=False)
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    cfg = workload_config()
+    scene = synth.scene_frame(256, seed=synth.BASE_SEED + 1)
+    loop = FrameLoop(scene, cfg["levels"], WIDTH, HEIGHT, spp=SPP, max_bounces=BOUNCES,
+                     seed=synth.BASE_SEED + 17 * rank, tile=TILE, list_capacity=LIST_CAP, device=dev)
+    cams = [gsc.camera(synth.orbit_camera(WIDTH, HEIGHT, ORBIT_DEG_PER_FRAME * f))
+            for f in range(args.warmup + 2 * args.steps + 1)]
+    stream = torch.cuda.current_stream()
+
+    # warm-up (also sizes nothing: the pair capacity is fixed)
+    for f in range(args.warmup):
+        loop.frame(cams[f], f)
+    loop.ws.status()
+    loop.ws.counters()
+
+    # ---- device-timed region
+    gsc.profile_read(reset=True)
+    gsc.profile_enable(True)
+    launches0 = gsc.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for f in range(args.warmup, args.warmup + args.steps):
+            loop.frame(cams[f], f)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    launches = gsc.launch_count() - launches0
+    gsc.profile_enable(False)
+    prof = gsc.profile_read(reset=True)
+    counters = loop.ws.counters()
+    loop.ws.status()
+    clocks = clk.summary()
+    total_ms = ev0.elapsed_time(ev1)
+    trace_ms = prof["trace"][0]
+    train_render_ms = total_ms - trace_ms
+    total_max = max_over_ranks(total_ms, world)
+    tr_max = max_over_ranks(train_render_ms, world)
+    K = args.steps
+
+    # ---- end-to-end through the public API with host I/O: per frame the
+    # camera pose goes in (a gsc_camera struct, read by the calls), and the
+    # path-traced display image and the level losses come back to pinned host
+    # memory.
+    host_img = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, pin_memory=True)
+    host_loss = torch.empty((LEVELS,), dtype=torch.float32, pin_memory=True)
+    gsc.profile_read(reset=True)
+    gsc.profile_enable(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_host0 = time.perf_counter()
+    for f in range(args.warmup + K, args.warmup + 2 * K):
+        pose = bytes(cams[f])                     # the caller's pose, host memory
+        c = gsc.Camera.from_buffer_copy(pose)
+        loop.frame(c, f)
+        host_img.copy_(loop.image, non_blocking=True)
+        host_loss.copy_(loop.losses, non_blocking=True)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t_host0) * 1e3
+    gsc.profile_enable(False)
+    trace_e = gsc.profile_read(reset=True)["trace"][0]
+    barrier(world)
+    e2e_max = max_over_ranks(e2e_ms - trace_e, world)
+
+    # ---- roofline of the dominant kernel phase
+    hbm_peak, peak_src = measured_peaks()
+    n_gauss_calls = 2 * TOTAL_GAUSSIANS * K       # every level is binned twice per frame
+    n_pixels_calls = 3 * WIDTH * HEIGHT * LEVELS * K
+    phases = {k: v for k, v in prof.items() if v[2] > 0}
+    dom = max((k for k in phases if k != "trace"), key=lambda k: phases[k][0])
+    kind, amount = phase_algorithmic(dom, counters, n_gauss_calls, n_pixels_calls, K)
+    dom_ms = phases[dom][0]
+    dom_launches = phases[dom][1]
+    per_launch_s = dom_ms / 1e3 / max(dom_launches, 1)
+    if kind == "byte":
+        achieved = amount / max(dom_launches, 1) / per_launch_s / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": None, "peak_source": peak_src}
+    else:
+        achieved = amount / max(dom_launches, 1) / per_launch_s / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(FP32_PEAK_TFLOPS, 1),
+                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    roof["kernel"] = dom
+    roof["launches"] = int(dom_launches)
+    roof["avg_launch_ms"] = round(dom_ms / max(dom_launches, 1), 4)
+    stages = {k: round(v[0] / K, 3) for k, v in phases.items()}
+    counts = {k: round(v / K) for k, v in counters.items()}
+
+    result = {
+        "metric": METRIC, "value": round(tr_max / (K * world), 3), "unit": "ms/frame", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": round(total_max / K, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+        "stages_ms_per_frame": stages, "work_per_frame": counts,
+        "frame_ms_incl_trace": round(total_max / K, 3), "trace_ms_per_frame": round(trace_ms / K, 3),
+        "roofline": roof, "clocks": clocks, "gpu_launches": int(launches),
+        "e2e": {"value": round(e2e_max / (K * world), 3), "unit": "ms/frame",
+                "note": "host-timed frames through the public API, the tracer's device time taken out",
+                "h2d_bytes_per_step": 84, "d2h_bytes_per_step": 3 * WIDTH * HEIGHT * 4 + LEVELS * 4},
+    }
+    return result
+
+
+# ------------------------------------------------------------------ oracle (CPU) arm
+
+def oracle_sample(rank=0):
+    """Time the oracle on a bounded sample of the frame's train + render work
+    and extrapolate to one frame.  Per level: render + backward over a window
+    (per-pixel work) and over a 1x1 window (the per-call projection and depth
+    sort), HDR loss on the window, AdamW over all the level's Gaussians."""
+    import oracle
+    from paper_2507_19718_gb300 import synth
+    oracle.build()
+    sizes = synth.level_sizes(TOTAL_GAUSSIANS, LEVELS)
+    cam = synth.orbit_camera(WIDTH, HEIGHT, 0.0)
+    win = (936, 522, 48, 36)
+    frame_px, win_px = WIDTH * HEIGHT, win[2] * win[3]
+    est_s, used_s = 0.0, 0.0
+    for k, n in enumerate(sizes):
+        p = synth.gaussians(n, synth.BASE_SEED + 1000 + k)
+        t0 = time.perf_counter()
+        oracle.render(p, cam, window=(win[0], win[1], 1, 1))
+        oracle.render_backward(p, cam, np.ones((3, 1, 1)), window=(win[0], win[1], 1, 1))
+        t_fix = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        img, _, _, _ = oracle.render(p, cam, window=win)
+        g = np.random.default_rng(k).uniform(-1, 1, (3, win[3], win[2]))
+        oracle.render_backward(p, cam, g, window=win)
+        tgt = np.random.default_rng(k + 7).uniform(0, 1, img.shape).astype(np.float32)
+        oracle.loss_hdr(img.astype(np.float32), tgt)
+        t_win = time.perf_counter() - t0
+        pp = p.astype(np.float64).reshape(-1)
+        gg = np.random.default_rng(k).normal(0, 1e-3, pp.size)
+        mm, vv = np.zeros_like(pp), np.zeros_like(pp)
+        t0 = time.perf_counter()
+        oracle.adamw(pp, gg, mm, vv, np.tile(np.float64(1e-3), 16), 1.0, 0.9, 0.999, 1e-15, 0.01, 1)
+        t_adam = time.perf_counter() - t0
+        per_px = max(t_win - t_fix, 0.0) / win_px
+        est_s += t_fix + per_px * frame_px + t_adam
+        used_s += t_fix + t_win + t_adam
+    sample = (f"oracle (FP64 C, OpenMP) render+backward+HDR loss on a {win[2]}x{win[3]} window of the "
+              f"1080p frame per level and on a 1x1 window (per-call projection/sort), AdamW on all 1M "
+              f"Gaussians; per-pixel cost extrapolated to {frame_px} px; {used_s:.1f} s of CPU time")
+    return est_s * 1e3, sample
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    vals = []
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        ms, sample = oracle_sample(rank)
+        if i >= args.warmup:
+            vals.append(ms)
+    value = float(np.median(vals))
+    cores = os.cpu_count() or 1
+    return {
+        "metric": METRIC, "impl": "reference", "value": round(value, 1), "unit": "ms/frame", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value, 1), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(),
+        "cpu_baseline": {"value": round(value, 1), "unit": "ms/frame", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 1), "unit": "ms/frame", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        # the oracle arm runs on rank 0's host cores only
+        res = run_reference(args, world, rank)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    res = run_ours(args, world, rank, local)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            ms, sample = oracle_sample()
+            res["cpu_baseline"] = {"value": round(ms, 1), "unit": "ms/frame", "cores": os.cpu_count() or 1,
+                                   "kind": "oracle", "sample": sample}
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

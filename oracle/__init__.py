@@ -69,7 +69,7 @@ def lib():
             L.orc_transmittance.argtypes = [i32, vp, i32, i32, i32, vp, i32, vp, vp, vp, vp, i64, u64, vp, i32]
             L.orc_sigma_t.argtypes = [vp, i32, i32, i32, vp, i32, vp, vp, vp, i64, vp]
             L.orc_project.argtypes = [i64, vp, vp, vp, vp]
-            L.orc_render.argtypes = [i64, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, i32]
+            L.orc_render.argtypes = [i64, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, i32, i32]
             L.orc_render.restype = i32
             L.orc_render_backward.argtypes = [i64, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, i32]
             L.orc_render_backward.restype = i32
@@ -188,8 +188,12 @@ def project(params, cam, cfg=None) -> np.ndarray:
     return out
 
 
-def render(params, cam, cfg=None, window=None, nthreads: int = 0):
-    """Returns image (3, h, w), marginal (h, w) bool, ncontrib (h, w), T_final (h, w)."""
+def render(params, cam, cfg=None, window=None, nthreads: int = 0, grad_margins: bool = False):
+    """Returns image (3, h, w), marginal (h, w) bool, ncontrib (h, w), T_final (h, w).
+
+    marginal flags pixels where a compositing decision lay within 2e-4
+    (relative) of its threshold, so that an FP32 implementation may take it
+    the other way; grad_margins also flags terms near the alpha_max clamp."""
     params = _c(params, np.float32)
     x0, y0, w, h = window if window is not None else (0, 0, cam.width, cam.height)
     image = np.zeros((3, h, w), np.float64)
@@ -197,7 +201,7 @@ def render(params, cam, cfg=None, window=None, nthreads: int = 0):
     ncon = np.zeros((h, w), np.int32)
     tfin = np.zeros((h, w), np.float64)
     rc = lib().orc_render(len(params), _p(params), _p(cam.packed()), _p(_cfg(cfg)), x0, y0, w, h, _p(image),
-                          _p(marg), _p(ncon), _p(tfin), _threads(nthreads))
+                          _p(marg), _p(ncon), _p(tfin), int(grad_margins), _threads(nthreads))
     if rc:
         raise MemoryError("orc_render")
     return image, marg.astype(bool), ncon, tfin

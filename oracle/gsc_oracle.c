@@ -465,9 +465,12 @@ static int64_t walk_pixel(const proj_t* pr, const int64_t* order, int64_t V, con
  * Forward render of the pixel window [x0, x0 + w) x [y0, y0 + h) of a W x H
  * camera.  Pixel (i, j) is sampled at its centre (i + 0.5, j + 0.5);
  * background 0.  image: 3 x h x w; marginal, ncontrib: h x w (optional).
+ * grad_margins != 0 also flags pixels with a term near the alpha_max clamp
+ * (where the gradient, not the image, jumps).
  */
 int orc_render(int64_t N, const float* params, const float* cam, const double* cfg, int x0, int y0, int w, int h,
-               double* image, uint8_t* marginal, int32_t* ncontrib, double* T_final, int nthreads) {
+               double* image, uint8_t* marginal, int32_t* ncontrib, double* T_final, int grad_margins,
+               int nthreads) {
     rcam_t c;
     rcam_setup(&c, cam);
     proj_t* pr = (proj_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(proj_t));
@@ -480,7 +483,8 @@ int orc_render(int64_t N, const float* params, const float* cam, const double* c
         for (int ii = 0; ii < w; ++ii) {
             double C[3], T;
             int marg;
-            int64_t n = walk_pixel(pr, order, V, cfg, x0 + ii + 0.5, y0 + jj + 0.5, C, &T, &marg, NULL, 0, 0);
+            int64_t n = walk_pixel(pr, order, V, cfg, x0 + ii + 0.5, y0 + jj + 0.5, C, &T, &marg, NULL, 0,
+                                   grad_margins);
             long p = (long)jj * w + ii;
             for (int ch = 0; ch < 3; ++ch) image[ch * WH + p] = C[ch];
             if (marginal) marginal[p] = (uint8_t)marg;

@@ -1,0 +1,122 @@
+// Internal declarations of the GB300 GSCache library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gsc.h"
+
+namespace gsc {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// --------------------------------------------------------------- sorting
+constexpr int kSortThreads = 256;
+constexpr int kSortIPT = 8;                              // items per thread
+constexpr int kSortTile = kSortThreads * kSortIPT;      // 2048 items per tile
+constexpr int kMaxSortBlocks = 152 * 8;                 // GB300: 152 SMs x 8 resident blocks
+constexpr int kScanTile = 2048;
+
+// --------------------------------------------------------------- raster
+// Projected record of one Gaussian, three float4 (48 B):
+//   r0 = (mean2D.x, mean2D.y, qa, qb)   r1 = (qc, opacity, lthr2, 0)   r2 = (r, g, b, 0)
+// with p2 = qa dx^2 + qb dx dy + qc dy^2 = log2(exp(-d^T conic d / 2)), i.e.
+// qa = -a log2(e) / 2, qb = -b log2(e), qc = -c log2(e) / 2, and
+// lthr2 = log2(alpha_min / opacity): a pair is composited iff p2 >= lthr2.
+struct CamDev {
+    float R[9], t[3], pos[3], fx, fy, cx, cy;
+    int W, H;
+};
+
+struct RasterDev {
+    float alpha_max, alpha_min, T_min, near_plane, dilation;
+    int tile_w, tile_h, tiles_x, tiles_y, cap;
+};
+
+// instrumentation (api.cu): event-timed phases and the launch counter
+enum Phase : int {
+    kPhProject, kPhDepthSort, kPhScan, kPhEmit, kPhTileSort, kPhRanges, kPhRender, kPhRenderBwd, kPhProjectBwd,
+    kPhLoss, kPhAdam, kPhTrace, kNumPhases
+};
+void count_launch(int n);
+struct PhaseScope {
+    PhaseScope(int phase, cudaStream_t s, int launches);
+    ~PhaseScope();
+    int phase;
+    cudaStream_t stream;
+    int slot;
+};
+
+// status words in the workspace
+enum : int { kStatusCode = 0, kStatusWords = 4 };
+// counters in the workspace
+enum : int { kCntPairs = 0, kCntPairsMax = 1, kCounterWords = 8 };
+// 64-bit work statistics in the workspace
+enum : int { kStEvalFwd = 0, kStCompFwd = 1, kStEvalRewalk = 2, kStEvalBack = 3, kStPairsSum = 4, kStBinnings = 5,
+             kStatWords = 8 };
+
+}  // namespace gsc
+
+// The workspace handle.  Every device pointer points into the caller's buffer.
+struct gsc_workspace {
+    char* base;
+    size_t bytes;
+    int64_t max_gaussians, max_pairs, max_tiles;
+    int32_t max_w, max_h;
+    int sort_blocks;  // grid of the pair sort
+    int32_t* status;
+    uint32_t* counters;
+    unsigned long long* stats;
+    float4* rec;       // 3 x NG
+    uint32_t *key0, *key1, *idx0, *idx1;
+    uint2* rect;       // packed tile rectangle per Gaussian
+    uint32_t* cnt;     // tiles touched per Gaussian
+    uint32_t* off;     // exclusive prefix of cnt in depth order
+    uint32_t* scan_sums;
+    uint32_t *pkey0, *pkey1, *pval0, *pval1;
+    uint32_t* hist;    // kMaxSortBlocks x 256 + 256
+    uint2* ranges;     // [start, end) per tile
+    float4* g2d;       // 3 x NG: 2D gradients
+    float* red;        // reduction scratch for losses
+    size_t red_floats;
+};
+
+struct gsc_scene {
+    gsc_scene_desc desc;
+    float sbar;  // majorant
+};
+
+namespace gsc {
+
+// sort.cu
+void scan_gathered(const uint32_t* cnt, const uint32_t* idx, uint32_t n, uint32_t* out, uint32_t* sums,
+                   uint32_t* counters, int32_t* status, uint32_t capacity, unsigned long long* stats, cudaStream_t s);
+// Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
+// The count is n_host, or *n_dev if n_dev != NULL (clamped to n_host).
+// Returns 0 if the sorted data ends in (k0, v0), 1 if in (k1, v1).
+int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* n_dev,
+                     uint32_t n_host, int bits, int blocks, uint32_t* hist, cudaStream_t s);
+int sort_blocks_for(uint64_t n);
+
+// raster.cu
+cudaError_t bin_gaussians(const float* params, int64_t N, const CamDev& cam, const RasterDev& rc,
+                          gsc_workspace* ws, const uint32_t** sorted_vals, cudaStream_t s);
+cudaError_t launch_render(const CamDev& cam, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
+                          float* image, cudaStream_t s);
+cudaError_t launch_render_backward(const float* params, int64_t N, const CamDev& cam, const RasterDev& rc,
+                                   gsc_workspace* ws, const uint32_t* vals, const float* dL_dimage, float* grads,
+                                   cudaStream_t s);
+
+// trace.cu
+cudaError_t launch_trace(const gsc_scene* sc, const CamDev& cam, const gsc_trace_params& p, const float* cache,
+                         float* targets, float* image, cudaStream_t s);
+
+// optim.cu
+cudaError_t launch_loss(int kind, const float* pred, const float* target, int C, int H, int W, int x0, int y0,
+                        int w, int h, float* dL_dpred, float* loss_out, float* red, size_t red_floats,
+                        cudaStream_t s);
+cudaError_t launch_adamw(float* params, float* grads, float* m, float* v, int64_t N, const gsc_adam_params& a,
+                         cudaStream_t s);
+
+}  // namespace gsc

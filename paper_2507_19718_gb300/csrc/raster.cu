@@ -1,0 +1,650 @@
+// Tile-based Gaussian splatting of one cache level and its gradient
+// (Sec. 3.1 / 3.5 of GSCache, which renders each level with the 3D Gaussian
+// splatting rasterizer at SH degree 0, Sec. 3.6).
+//
+// Forward:  k_project  -> depth radix sort -> scan of tile counts -> k_emit
+//           -> stable radix sort of the pairs by tile -> k_ranges -> k_render
+// Backward: the same binning (no per-pixel state is kept from the forward),
+//           k_render_bwd (forward re-walk for the final T and the last
+//           composited entry, then back to front), k_project_bwd.
+//
+// The compositing decisions (alpha >= alpha_min, T (1 - alpha) < T_min) are
+// computed by one inline function with explicitly rounded operations, so the
+// forward and the backward take them identically.  A Gaussian is binned into
+// every tile its alpha >= alpha_min support can reach (radius from the
+// largest eigenvalue of its 2D covariance), which makes every pixel's
+// ordered list independent of the tile shape: images are bit-identical for
+// any tile size.
+#include <math.h>
+
+#include "gsc_internal.cuh"
+
+namespace gsc {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// FP32 view depth with a fixed operation order ((r20 x + r21 y) + r22 z) + t2;
+// it is the sort key and the near-plane test.
+__device__ __forceinline__ float view_depth(const CamDev& c, float x, float y, float z) {
+    float s = __fadd_rn(__fmul_rn(c.R[6], x), __fmul_rn(c.R[7], y));
+    s = __fadd_rn(s, __fmul_rn(c.R[8], z));
+    return __fadd_rn(s, c.t[2]);
+}
+
+// log2 of the Gaussian falloff at pixel-centre offset (dx, dy), fixed rounding
+__device__ __forceinline__ float falloff_log2(float4 r0, float qc, float dx, float dy) {
+    float p = __fmul_rn(__fmul_rn(r0.z, dx), dx);
+    p = __fmaf_rn(__fmul_rn(r0.w, dx), dy, p);
+    p = __fmaf_rn(__fmul_rn(qc, dy), dy, p);
+    return p;
+}
+
+struct Proj {
+    float qn[4], qinv;
+    float Rq[9], s[3], M[9];
+    float Sig[9];
+    float t[3];
+    float Tm[6];
+    float A, B, C;
+    float a, b, c;  // conic
+};
+
+// Projection of one Gaussian (EWA splatting, pinhole Jacobian at the camera
+// space mean, dilation added to the 2D covariance).  False if culled.
+__device__ __forceinline__ bool project_core(float4 p0, float4 p1, float4 p2, const CamDev& cam,
+                                             const RasterDev& rc, Proj& x) {
+    float depth = view_depth(cam, p0.x, p0.y, p0.z);
+    if (!(depth > rc.near_plane)) return false;
+    float qn2 = p2.x * p2.x + p2.y * p2.y + p2.z * p2.z + p2.w * p2.w;
+    if (!(qn2 > 0.f)) return false;
+    float qlen = sqrtf(qn2);
+    x.qinv = 1.f / qlen;
+    float w = p2.x * x.qinv, qx = p2.y * x.qinv, qy = p2.z * x.qinv, qz = p2.w * x.qinv;
+    x.qn[0] = w; x.qn[1] = qx; x.qn[2] = qy; x.qn[3] = qz;
+    x.Rq[0] = 1.f - 2.f * (qy * qy + qz * qz);
+    x.Rq[1] = 2.f * (qx * qy - w * qz);
+    x.Rq[2] = 2.f * (qx * qz + w * qy);
+    x.Rq[3] = 2.f * (qx * qy + w * qz);
+    x.Rq[4] = 1.f - 2.f * (qx * qx + qz * qz);
+    x.Rq[5] = 2.f * (qy * qz - w * qx);
+    x.Rq[6] = 2.f * (qx * qz - w * qy);
+    x.Rq[7] = 2.f * (qy * qz + w * qx);
+    x.Rq[8] = 1.f - 2.f * (qx * qx + qy * qy);
+    x.s[0] = expf(p1.x); x.s[1] = expf(p1.y); x.s[2] = expf(p1.z);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) x.M[3 * i + j] = x.Rq[3 * i + j] * x.s[j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = i; k < 3; ++k) {
+            float v = x.M[3 * i] * x.M[3 * k] + x.M[3 * i + 1] * x.M[3 * k + 1] + x.M[3 * i + 2] * x.M[3 * k + 2];
+            x.Sig[3 * i + k] = v;
+            x.Sig[3 * k + i] = v;
+        }
+    const float* R = cam.R;
+    x.t[0] = R[0] * p0.x + R[1] * p0.y + R[2] * p0.z + cam.t[0];
+    x.t[1] = R[3] * p0.x + R[4] * p0.y + R[5] * p0.z + cam.t[1];
+    x.t[2] = depth;
+    float iz = 1.f / depth;
+    float J00 = cam.fx * iz, J02 = -cam.fx * x.t[0] * iz * iz;
+    float J11 = cam.fy * iz, J12 = -cam.fy * x.t[1] * iz * iz;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        x.Tm[k] = J00 * R[k] + J02 * R[6 + k];
+        x.Tm[3 + k] = J11 * R[3 + k] + J12 * R[6 + k];
+    }
+    float u0[3], u1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        u0[k] = x.Sig[3 * k] * x.Tm[0] + x.Sig[3 * k + 1] * x.Tm[1] + x.Sig[3 * k + 2] * x.Tm[2];
+        u1[k] = x.Sig[3 * k] * x.Tm[3] + x.Sig[3 * k + 1] * x.Tm[4] + x.Sig[3 * k + 2] * x.Tm[5];
+    }
+    x.A = x.Tm[0] * u0[0] + x.Tm[1] * u0[1] + x.Tm[2] * u0[2] + rc.dilation;
+    x.B = x.Tm[3] * u0[0] + x.Tm[4] * u0[1] + x.Tm[5] * u0[2];
+    x.C = x.Tm[3] * u1[0] + x.Tm[4] * u1[1] + x.Tm[5] * u1[2] + rc.dilation;
+    // FP32 products are exact in FP64: the determinant carries one rounding
+    double det = (double)x.A * (double)x.C - (double)x.B * (double)x.B;
+    if (!(det > 0.0)) return false;
+    x.a = (float)((double)x.C / det);
+    x.b = (float)(-(double)x.B / det);
+    x.c = (float)((double)x.A / det);
+    return true;
+}
+
+__global__ void __launch_bounds__(256) k_project(const float4* __restrict__ params, uint32_t N, CamDev cam,
+                                                 RasterDev rc, float4* __restrict__ rec, uint32_t* __restrict__ key,
+                                                 uint32_t* __restrict__ idx, uint2* __restrict__ rect,
+                                                 uint32_t* __restrict__ cnt) {
+    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= N) return;
+    float4 p0 = params[4 * (size_t)g], p1 = params[4 * (size_t)g + 1];
+    float4 p2 = params[4 * (size_t)g + 2], p3 = params[4 * (size_t)g + 3];
+    idx[g] = g;
+    key[g] = 0xffffffffu;
+    cnt[g] = 0;
+    Proj x;
+    if (!project_core(p0, p1, p2, cam, rc, x)) return;
+    float op = 1.f / (1.f + expf(-p0.w));
+    if (!(op >= rc.alpha_min)) return;  // no pixel can reach alpha_min
+    float lthr2 = log2f(rc.alpha_min / op);
+    float mx = cam.fx * x.t[0] / x.t[2] + cam.cx;
+    float my = cam.fy * x.t[1] / x.t[2] + cam.cy;
+    float half = 0.5f * (x.A + x.C), dd = 0.5f * (x.A - x.C);
+    float lmax = half + sqrtf(dd * dd + x.B * x.B);
+    // alpha >= alpha_min  =>  d^T conic d <= 2 ln(op / alpha_min)  =>  |d|^2 <= that * lmax
+    float r = sqrtf(-2.f * lthr2 * kLn2 * lmax) * 1.001f + 0.02f;
+    if (!isfinite(mx) || !isfinite(my) || !isfinite(r)) return;
+    float xl = ceilf(fmaxf(mx - r - 0.5f, -1.f)), xh = floorf(fminf(mx + r - 0.5f, (float)cam.W));
+    float yl = ceilf(fmaxf(my - r - 0.5f, -1.f)), yh = floorf(fminf(my + r - 0.5f, (float)cam.H));
+    int ilo = max(0, (int)xl), ihi = min(cam.W - 1, (int)xh);
+    int jlo = max(0, (int)yl), jhi = min(cam.H - 1, (int)yh);
+    if (ilo > ihi || jlo > jhi) return;
+    uint32_t tx0 = ilo / rc.tile_w, tx1 = ihi / rc.tile_w + 1;
+    uint32_t ty0 = jlo / rc.tile_h, ty1 = jhi / rc.tile_h + 1;
+    rect[g] = make_uint2(tx0 | (tx1 << 16), ty0 | (ty1 << 16));
+    cnt[g] = (tx1 - tx0) * (ty1 - ty0);
+    key[g] = __float_as_uint(x.t[2]);
+    float h = -0.5f * kLog2e;
+    rec[3 * (size_t)g] = make_float4(mx, my, h * x.a, -kLog2e * x.b);
+    rec[3 * (size_t)g + 1] = make_float4(h * x.c, op, lthr2, 0.f);
+    rec[3 * (size_t)g + 2] = make_float4(fmaxf(p3.x, 0.f), fmaxf(p3.y, 0.f), fmaxf(p3.z, 0.f), 0.f);
+}
+
+// one warp writes the pairs of 32 consecutive depth-ordered Gaussians, one
+// Gaussian at a time, so that every store instruction is contiguous
+__global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ off,
+                                              const uint32_t* __restrict__ cnt, const uint2* __restrict__ rect,
+                                              uint32_t N, int tiles_x, const uint32_t* __restrict__ counters,
+                                              uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval) {
+    uint32_t total = counters[kCntPairs];
+    uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    uint32_t i = wid * 32 + lane;
+    if (wid * 32 >= N) return;
+    uint32_t g = 0, c = 0, o = 0;
+    uint2 rc = make_uint2(0, 0);
+    if (i < N) {
+        g = sidx[i];
+        c = cnt[g];
+        o = off[i];
+        if (c) rc = rect[g];
+    }
+    for (int j = 0; j < 32; ++j) {
+        uint32_t cj = __shfl_sync(kFull, c, j);
+        uint32_t oj = __shfl_sync(kFull, o, j);
+        uint32_t gj = __shfl_sync(kFull, g, j);
+        uint32_t rx = __shfl_sync(kFull, rc.x, j);
+        uint32_t ry = __shfl_sync(kFull, rc.y, j);
+        if (cj == 0 || (uint64_t)oj + cj > total) continue;
+        uint32_t tx0 = rx & 0xffffu, wx = (rx >> 16) - tx0, ty0 = ry & 0xffffu;
+        for (uint32_t k = lane; k < cj; k += 32) {
+            uint32_t ky = k / wx, kx = k - ky * wx;
+            pkey[oj + k] = (ty0 + ky) * (uint32_t)tiles_x + tx0 + kx;
+            pval[oj + k] = gj;
+        }
+    }
+}
+
+__global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ counters,
+                         uint2* __restrict__ ranges) {
+    uint32_t n = counters[kCntPairs];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t k = keys[i];
+        if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
+        if (i == n - 1 || keys[i + 1] != k) ranges[k].y = i + 1;
+    }
+}
+
+// one 64-bit atomic per warp
+__device__ __forceinline__ void warp_count(unsigned long long* dst, uint32_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, (unsigned long long)v);
+}
+
+// ------------------------------------------------------------------ forward
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW* TH) k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+                                                   const float4* __restrict__ rec, CamDev cam, RasterDev rc,
+                                                   float* __restrict__ image, unsigned long long* __restrict__ stats) {
+    extern __shared__ float4 smem[];
+    const int cap = rc.cap;
+    float4* s0 = smem;
+    float4* s1 = smem + cap;
+    float4* s2 = smem + 2 * cap;
+    constexpr int NT = TW * TH;
+    int tile = blockIdx.x;
+    int tx = tile % rc.tiles_x, ty = tile / rc.tiles_x;
+    int px = tx * TW + (threadIdx.x % TW), py = ty * TH + (threadIdx.x / TW);
+    bool inside = px < cam.W && py < cam.H;
+    float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    uint2 rg = ranges[tile];
+    float T = 1.f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
+    uint32_t n_eval = 0, n_comp = 0;
+    bool done = !inside;
+    for (uint32_t base = rg.x; base < rg.y; base += cap) {
+        if (__syncthreads_count(done) == NT) break;
+        int n = (int)min((uint32_t)cap, rg.y - base);
+        for (int k = threadIdx.x; k < n; k += NT) {
+            uint32_t g = vals[base + k];
+            s0[k] = rec[3 * (size_t)g];
+            s1[k] = rec[3 * (size_t)g + 1];
+            s2[k] = rec[3 * (size_t)g + 2];
+        }
+        __syncthreads();
+        if (!done) {
+            for (int k = 0; k < n; ++k) {
+                float4 r0 = s0[k];
+                float4 r1 = s1[k];
+                float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy, r0.y);
+                float p = falloff_log2(r0, r1.x, dx, dy);
+                ++n_eval;
+                if (p < r1.z) continue;
+                float alpha = fminf(rc.alpha_max, __fmul_rn(r1.y, ex2_approx(p)));
+                float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+                if (Tn < rc.T_min) {
+                    done = true;
+                    break;
+                }
+                ++n_comp;
+                float4 c = s2[k];
+                float wgt = alpha * T;
+                Cr = fmaf(c.x, wgt, Cr);
+                Cg = fmaf(c.y, wgt, Cg);
+                Cb = fmaf(c.z, wgt, Cb);
+                T = Tn;
+            }
+        }
+        __syncthreads();
+    }
+    warp_count(&stats[kStEvalFwd], n_eval);
+    warp_count(&stats[kStCompFwd], n_comp);
+    if (inside) {
+        size_t HW = (size_t)cam.W * cam.H, p = (size_t)py * cam.W + px;
+        image[p] = Cr;
+        image[HW + p] = Cg;
+        image[2 * HW + p] = Cb;
+    }
+}
+
+// ------------------------------------------------------------------ backward
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW* TH) k_render_bwd(const uint2* __restrict__ ranges,
+                                                       const uint32_t* __restrict__ vals,
+                                                       const float4* __restrict__ rec, CamDev cam, RasterDev rc,
+                                                       const float* __restrict__ dL_dimg, float4* __restrict__ g2d,
+                                                       unsigned long long* __restrict__ stats) {
+    extern __shared__ float4 smem[];
+    const int cap = rc.cap;
+    float4* s0 = smem;
+    float4* s1 = smem + cap;
+    float4* s2 = smem + 2 * cap;
+    uint32_t* sid = reinterpret_cast<uint32_t*>(smem + 3 * cap);
+    __shared__ uint32_t s_end;
+    constexpr int NT = TW * TH;
+    int tile = blockIdx.x;
+    int tx = tile % rc.tiles_x, ty = tile / rc.tiles_x;
+    int px = tx * TW + (threadIdx.x % TW), py = ty * TH + (threadIdx.x / TW);
+    bool inside = px < cam.W && py < cam.H;
+    float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    size_t HW = (size_t)cam.W * cam.H, pix = (size_t)py * cam.W + px;
+    float gr = 0.f, gg = 0.f, gb = 0.f;
+    if (inside) {
+        gr = dL_dimg[pix];
+        gg = dL_dimg[HW + pix];
+        gb = dL_dimg[2 * HW + pix];
+    }
+    bool active = inside && (gr != 0.f || gg != 0.f || gb != 0.f);
+    uint2 rg = ranges[tile];
+
+    // phase 1: forward re-walk, the same decisions as k_render
+    float T = 1.f;
+    uint32_t last = rg.x;
+    uint32_t n_eval1 = 0, n_eval2 = 0;
+    bool done = !active;
+    for (uint32_t base = rg.x; base < rg.y; base += cap) {
+        if (__syncthreads_count(done) == NT) break;
+        int n = (int)min((uint32_t)cap, rg.y - base);
+        for (int k = threadIdx.x; k < n; k += NT) {
+            uint32_t g = vals[base + k];
+            s0[k] = rec[3 * (size_t)g];
+            s1[k] = rec[3 * (size_t)g + 1];
+        }
+        __syncthreads();
+        if (!done) {
+            for (int k = 0; k < n; ++k) {
+                float4 r0 = s0[k];
+                float4 r1 = s1[k];
+                float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy, r0.y);
+                float p = falloff_log2(r0, r1.x, dx, dy);
+                ++n_eval1;
+                if (p < r1.z) continue;
+                float alpha = fminf(rc.alpha_max, __fmul_rn(r1.y, ex2_approx(p)));
+                float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+                if (Tn < rc.T_min) {
+                    done = true;
+                    break;
+                }
+                T = Tn;
+                last = base + k + 1;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) s_end = rg.x;
+    __syncthreads();
+    if (active) atomicMax(&s_end, last);
+    __syncthreads();
+    uint32_t end = s_end;
+    // per-warp bound: entries past every lane's last need no work
+    uint32_t wlast = active ? last : rg.x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(kFull, wlast, o));
+
+    // phase 2: back to front
+    float Sr = 0.f, Sg = 0.f, Sb = 0.f;
+    int lane = threadIdx.x & 31;
+    for (uint32_t hi = end; hi > rg.x;) {
+        uint32_t lo = hi - rg.x > (uint32_t)cap ? hi - cap : rg.x;
+        int n = (int)(hi - lo);
+        __syncthreads();
+        for (int k = threadIdx.x; k < n; k += NT) {
+            uint32_t g = vals[lo + k];
+            sid[k] = g;
+            s0[k] = rec[3 * (size_t)g];
+            s1[k] = rec[3 * (size_t)g + 1];
+            s2[k] = rec[3 * (size_t)g + 2];
+        }
+        __syncthreads();
+        for (int k = n - 1; k >= 0; --k) {
+            uint32_t j = lo + k;
+            if (j >= wlast) continue;  // warp-uniform
+            float4 r0 = s0[k];
+            float4 r1 = s1[k];
+            bool act = active && j < last;
+            float dmx = 0.f, dmy = 0.f, dqa = 0.f, dqb = 0.f, dqc = 0.f, dlo = 0.f, dcr = 0.f, dcg = 0.f, dcb = 0.f;
+            if (act) {
+                float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy, r0.y);
+                float p = falloff_log2(r0, r1.x, dx, dy);
+                ++n_eval2;
+                if (p >= r1.z) {
+                    float e = ex2_approx(p);
+                    float araw = __fmul_rn(r1.y, e);
+                    float alpha = fminf(rc.alpha_max, araw);
+                    float inv = 1.f / (1.f - alpha);
+                    T = T * inv;  // transmittance in front of this entry
+                    float4 c = s2[k];
+                    float wgt = alpha * T;
+                    dcr = wgt * gr;
+                    dcg = wgt * gg;
+                    dcb = wgt * gb;
+                    float dal = gr * (c.x * T - Sr * inv) + gg * (c.y * T - Sg * inv) + gb * (c.z * T - Sb * inv);
+                    Sr = fmaf(c.x, wgt, Sr);
+                    Sg = fmaf(c.y, wgt, Sg);
+                    Sb = fmaf(c.z, wgt, Sb);
+                    if (araw < rc.alpha_max) {
+                        dlo = dal * e * r1.y * (1.f - r1.y);
+                        float dp = dal * alpha * kLn2;
+                        dqa = dp * dx * dx;
+                        dqb = dp * dx * dy;
+                        dqc = dp * dy * dy;
+                        dmx = -dp * (2.f * r0.z * dx + r0.w * dy);
+                        dmy = -dp * (r0.w * dx + 2.f * r1.x * dy);
+                    }
+                } else {
+                    act = false;
+                }
+            }
+            if (__any_sync(kFull, act)) {
+                dmx = warp_sum(dmx);
+                dmy = warp_sum(dmy);
+                dqa = warp_sum(dqa);
+                dqb = warp_sum(dqb);
+                dqc = warp_sum(dqc);
+                dlo = warp_sum(dlo);
+                dcr = warp_sum(dcr);
+                dcg = warp_sum(dcg);
+                dcb = warp_sum(dcb);
+                if (lane == 0) {
+                    uint32_t g = sid[k];
+                    atomicAdd(&g2d[3 * (size_t)g], make_float4(dmx, dmy, dqa, dqb));
+                    atomicAdd(&g2d[3 * (size_t)g + 1], make_float4(dqc, dlo, 0.f, 0.f));
+                    atomicAdd(&g2d[3 * (size_t)g + 2], make_float4(dcr, dcg, dcb, 0.f));
+                }
+            }
+        }
+        hi = lo;
+    }
+    warp_count(&stats[kStEvalRewalk], n_eval1);
+    warp_count(&stats[kStEvalBack], n_eval2);
+}
+
+// 2D gradients -> packed parameter gradients (+=)
+__global__ void __launch_bounds__(128) k_project_bwd(const float4* __restrict__ params, uint32_t N, CamDev cam,
+                                                     RasterDev rc, const uint32_t* __restrict__ cnt,
+                                                     const float4* __restrict__ g2d, float4* __restrict__ grads) {
+    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= N || cnt[g] == 0) return;
+    float4 a0 = g2d[3 * (size_t)g], a1 = g2d[3 * (size_t)g + 1], a2 = g2d[3 * (size_t)g + 2];
+    if (a0.x == 0.f && a0.y == 0.f && a0.z == 0.f && a0.w == 0.f && a1.x == 0.f && a1.y == 0.f && a2.x == 0.f &&
+        a2.y == 0.f && a2.z == 0.f)
+        return;
+    float4 p0 = params[4 * (size_t)g], p1 = params[4 * (size_t)g + 1];
+    float4 p2 = params[4 * (size_t)g + 2], p3 = params[4 * (size_t)g + 3];
+    Proj x;
+    if (!project_core(p0, p1, p2, cam, rc, x)) return;
+    const float* R = cam.R;
+    // conic entries from the scaled ones used by the rasterizer
+    float ga = a0.z * (-0.5f * kLog2e), gb = a0.w * (-kLog2e), gc = a1.x * (-0.5f * kLog2e);
+    // dL/dSigma2D = -Q G Q with Q = conic, G = [[ga, gb/2], [gb/2, gc]]
+    float a = x.a, b = x.b, c = x.c;
+    float dA = -(ga * a * a + gb * a * b + gc * b * b);
+    float dC = -(ga * b * b + gb * b * c + gc * c * c);
+    float dB = -(2.f * ga * a * b + gb * (a * c + b * b) + 2.f * gc * b * c);
+    const float* T0 = x.Tm;
+    const float* T1 = x.Tm + 3;
+    float st0[3], st1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        st0[k] = x.Sig[3 * k] * T0[0] + x.Sig[3 * k + 1] * T0[1] + x.Sig[3 * k + 2] * T0[2];
+        st1[k] = x.Sig[3 * k] * T1[0] + x.Sig[3 * k + 1] * T1[1] + x.Sig[3 * k + 2] * T1[2];
+    }
+    float dT0[3], dT1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dT0[k] = 2.f * dA * st0[k] + dB * st1[k];
+        dT1[k] = dB * st0[k] + 2.f * dC * st1[k];
+    }
+    // Tm = J R: only J00, J02, J11, J12 are non-zero
+    float dJ00 = dT0[0] * R[0] + dT0[1] * R[1] + dT0[2] * R[2];
+    float dJ02 = dT0[0] * R[6] + dT0[1] * R[7] + dT0[2] * R[8];
+    float dJ11 = dT1[0] * R[3] + dT1[1] * R[4] + dT1[2] * R[5];
+    float dJ12 = dT1[0] * R[6] + dT1[1] * R[7] + dT1[2] * R[8];
+    float tx = x.t[0], ty = x.t[1], tz = x.t[2];
+    float iz = 1.f / tz, iz2 = iz * iz, iz3 = iz2 * iz;
+    float dtx = dJ02 * (-cam.fx * iz2) + a0.x * cam.fx * iz;
+    float dty = dJ12 * (-cam.fy * iz2) + a0.y * cam.fy * iz;
+    float dtz = dJ00 * (-cam.fx * iz2) + dJ02 * (2.f * cam.fx * tx * iz3) + dJ11 * (-cam.fy * iz2) +
+                dJ12 * (2.f * cam.fy * ty * iz3) - a0.x * cam.fx * tx * iz2 - a0.y * cam.fy * ty * iz2;
+    float4 o0 = grads[4 * (size_t)g], o1 = grads[4 * (size_t)g + 1];
+    float4 o2 = grads[4 * (size_t)g + 2], o3 = grads[4 * (size_t)g + 3];
+    o0.x += R[0] * dtx + R[3] * dty + R[6] * dtz;
+    o0.y += R[1] * dtx + R[4] * dty + R[7] * dtz;
+    o0.z += R[2] * dtx + R[5] * dty + R[8] * dtz;
+    o0.w += a1.y;
+    // Sigma = M M^T: dL/dM = (G + G^T) M with G = dA T0 T0^T + dB T0 T1^T + dC T1 T1^T
+    float Gs[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            Gs[3 * i + j] = 2.f * dA * T0[i] * T0[j] + dB * (T0[i] * T1[j] + T1[i] * T0[j]) + 2.f * dC * T1[i] * T1[j];
+    float dR[9];
+    float dls[3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        float ds = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float dM = Gs[3 * k] * x.M[l] + Gs[3 * k + 1] * x.M[3 + l] + Gs[3 * k + 2] * x.M[6 + l];
+            ds += dM * x.Rq[3 * k + l];
+            dR[3 * k + l] = dM * x.s[l];
+        }
+        dls[l] = ds * x.s[l];
+    }
+    o1.x += dls[0];
+    o1.y += dls[1];
+    o1.z += dls[2];
+    float w = x.qn[0], qx = x.qn[1], qy = x.qn[2], qz = x.qn[3];
+    float dw = 2.f * (-qz * dR[1] + qy * dR[2] + qz * dR[3] - qx * dR[5] - qy * dR[6] + qx * dR[7]);
+    float dx = 2.f * (qy * dR[1] + qz * dR[2] + qy * dR[3] - w * dR[5] + qz * dR[6] + w * dR[7]) -
+               4.f * qx * (dR[4] + dR[8]);
+    float dy = 2.f * (qx * dR[1] + w * dR[2] + qx * dR[3] + qz * dR[5] - w * dR[6] + qz * dR[7]) -
+               4.f * qy * (dR[0] + dR[8]);
+    float dz = 2.f * (-w * dR[1] + qx * dR[2] + w * dR[3] + qy * dR[5] + qx * dR[6] + qy * dR[7]) -
+               4.f * qz * (dR[0] + dR[4]);
+    float dot = w * dw + qx * dx + qy * dy + qz * dz;
+    o2.x += (dw - w * dot) * x.qinv;
+    o2.y += (dx - qx * dot) * x.qinv;
+    o2.z += (dy - qy * dot) * x.qinv;
+    o2.w += (dz - qz * dot) * x.qinv;
+    if (p3.x > 0.f) o3.x += a2.x;
+    if (p3.y > 0.f) o3.y += a2.y;
+    if (p3.z > 0.f) o3.z += a2.z;
+    grads[4 * (size_t)g] = o0;
+    grads[4 * (size_t)g + 1] = o1;
+    grads[4 * (size_t)g + 2] = o2;
+    grads[4 * (size_t)g + 3] = o3;
+}
+
+// ------------------------------------------------------------------ host
+
+static int bits_for(uint32_t n) {
+    int b = 1;
+    while (b < 32 && (1u << b) < n) ++b;
+    return b;
+}
+
+cudaError_t bin_gaussians(const float* params, int64_t N, const CamDev& cam, const RasterDev& rc,
+                          gsc_workspace* ws, const uint32_t** sorted_vals, cudaStream_t s) {
+    uint32_t n = (uint32_t)N;
+    uint32_t nblk = (n + 255) / 256;
+    if (nblk == 0) nblk = 1;
+    {
+        PhaseScope ph(kPhProject, s, 1);
+        k_project<<<nblk, 256, 0, s>>>(reinterpret_cast<const float4*>(params), n, cam, rc, ws->rec, ws->key0,
+                                       ws->idx0, ws->rect, ws->cnt);
+    }
+    int w;
+    {
+        PhaseScope ph(kPhDepthSort, s, 3 * 4);
+        w = radix_sort_pairs(ws->key0, ws->idx0, ws->key1, ws->idx1, nullptr, n, 32, sort_blocks_for(n), ws->hist, s);
+    }
+    const uint32_t* sidx = w ? ws->idx1 : ws->idx0;
+    {
+        PhaseScope ph(kPhScan, s, 3);
+        scan_gathered(ws->cnt, sidx, n, ws->off, ws->scan_sums, ws->counters, ws->status, (uint32_t)ws->max_pairs,
+                      ws->stats, s);
+    }
+    uint32_t eblk = (n + 255) / 256;
+    if (eblk == 0) eblk = 1;
+    {
+        PhaseScope ph(kPhEmit, s, 1);
+        k_emit<<<eblk, 256, 0, s>>>(sidx, ws->off, ws->cnt, ws->rect, n, rc.tiles_x, ws->counters, ws->pkey0,
+                                    ws->pval0);
+    }
+    uint32_t tiles = (uint32_t)rc.tiles_x * rc.tiles_y;
+    int bits = bits_for(tiles);
+    int p;
+    {
+        PhaseScope ph(kPhTileSort, s, 3 * ((bits + 7) / 8));
+        p = radix_sort_pairs(ws->pkey0, ws->pval0, ws->pkey1, ws->pval1, ws->counters + kCntPairs,
+                             (uint32_t)ws->max_pairs, bits, ws->sort_blocks, ws->hist, s);
+    }
+    const uint32_t* keys = p ? ws->pkey1 : ws->pkey0;
+    *sorted_vals = p ? ws->pval1 : ws->pval0;
+    {
+        PhaseScope ph(kPhRanges, s, 1);
+        cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * tiles, s);
+        k_ranges<<<152 * 8, 256, 0, s>>>(keys, ws->counters, ws->ranges);
+    }
+    return cudaGetLastError();
+}
+
+template <int TW, int TH>
+static cudaError_t render_t(const CamDev& cam, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
+                            float* image, cudaStream_t s) {
+    size_t smem = sizeof(float4) * 3 * rc.cap;
+    auto kern = k_render<TW, TH>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<rc.tiles_x * rc.tiles_y, TW * TH, smem, s>>>(ws->ranges, vals, ws->rec, cam, rc, image, ws->stats);
+    return cudaGetLastError();
+}
+
+template <int TW, int TH>
+static cudaError_t render_bwd_t(const CamDev& cam, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
+                                const float* dL, cudaStream_t s) {
+    size_t smem = (sizeof(float4) * 3 + sizeof(uint32_t)) * rc.cap;
+    auto kern = k_render_bwd<TW, TH>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<rc.tiles_x * rc.tiles_y, TW * TH, smem, s>>>(ws->ranges, vals, ws->rec, cam, rc, dL, ws->g2d,
+                                                         ws->stats);
+    return cudaGetLastError();
+}
+
+#define GSC_TILE_DISPATCH(FN, ...)                                                   \
+    if (rc.tile_w == 16 && rc.tile_h == 16) return FN<16, 16>(__VA_ARGS__);          \
+    if (rc.tile_w == 8 && rc.tile_h == 8) return FN<8, 8>(__VA_ARGS__);              \
+    if (rc.tile_w == 32 && rc.tile_h == 8) return FN<32, 8>(__VA_ARGS__);            \
+    if (rc.tile_w == 16 && rc.tile_h == 8) return FN<16, 8>(__VA_ARGS__);            \
+    if (rc.tile_w == 8 && rc.tile_h == 16) return FN<8, 16>(__VA_ARGS__);            \
+    if (rc.tile_w == 8 && rc.tile_h == 32) return FN<8, 32>(__VA_ARGS__);            \
+    if (rc.tile_w == 32 && rc.tile_h == 4) return FN<32, 4>(__VA_ARGS__);            \
+    return cudaErrorInvalidValue;
+
+cudaError_t launch_render(const CamDev& cam, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
+                          float* image, cudaStream_t s) {
+    PhaseScope ph(kPhRender, s, 1);
+    GSC_TILE_DISPATCH(render_t, cam, rc, ws, vals, image, s)
+}
+
+cudaError_t launch_render_backward(const float* params, int64_t N, const CamDev& cam, const RasterDev& rc,
+                                   gsc_workspace* ws, const uint32_t* vals, const float* dL_dimage, float* grads,
+                                   cudaStream_t s) {
+    cudaError_t e;
+    {
+        PhaseScope ph(kPhRenderBwd, s, 1);
+        cudaMemsetAsync(ws->g2d, 0, sizeof(float4) * 3 * (size_t)N, s);
+        auto launch = [&]() -> cudaError_t { GSC_TILE_DISPATCH(render_bwd_t, cam, rc, ws, vals, dL_dimage, s) };
+        e = launch();
+    }
+    if (e != cudaSuccess) return e;
+    uint32_t n = (uint32_t)N;
+    uint32_t nblk = (n + 127) / 128;
+    if (nblk == 0) nblk = 1;
+    {
+        PhaseScope ph(kPhProjectBwd, s, 1);
+        k_project_bwd<<<nblk, 128, 0, s>>>(reinterpret_cast<const float4*>(params), n, cam, rc, ws->cnt, ws->g2d,
+                                           reinterpret_cast<float4*>(grads));
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gsc

@@ -1,0 +1,283 @@
+// Device-wide exclusive scan and stable LSD radix sort used by the tile
+// binning of the rasterizer: a depth sort of the Gaussians followed by a
+// stable sort of the emitted (tile, Gaussian) pairs by tile id, which
+// together order every tile's list by (view depth, Gaussian index).
+//
+// Radix sort: 8-bit digits, three kernels per pass over a fixed grid of
+// `blocks` CTAs, each owning a contiguous range of the input:
+//   hist    per-CTA digit counts (warp-aggregated shared-memory atomics),
+//           stored digit-major so that one exclusive scan yields the stable
+//           scatter base of every (digit, CTA);
+//   scan    one CTA per digit scans its `blocks` counts;
+//   scatter each CTA ranks its keys in 2048-key tiles (warp match + per-warp
+//           digit counters), then writes keys and values to their slots.
+// The element count may live on the device (the pair count is only known
+// after the binning scan), so no host round trip is needed.
+#include "gsc_internal.cuh"
+
+namespace gsc {
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t read_count(const uint32_t* n_dev, uint32_t n_host) {
+    if (!n_dev) return n_host;
+    uint32_t n = *n_dev;
+    return n < n_host ? n : n_host;
+}
+
+// contiguous range of CTA b: multiples of the tile so that only the last CTA
+// with work has a partial tile
+__device__ __forceinline__ void block_range(uint32_t n, int blocks, int b, uint32_t& lo, uint32_t& hi) {
+    uint64_t per = ((uint64_t)n + blocks - 1) / blocks;
+    per = (per + kSortTile - 1) / kSortTile * kSortTile;
+    uint64_t l = per * (uint64_t)b, h = l + per;
+    lo = (uint32_t)(l < n ? l : n);
+    hi = (uint32_t)(h < n ? h : n);
+}
+
+// exclusive scan over a 256-thread block; returns the total in *total
+__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_t* smem8, uint32_t* total) {
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem8[warp] = x;
+    __syncthreads();
+    uint32_t wsum = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        uint32_t s = smem8[w];
+        if (w < warp) wsum += s;
+        tot += s;
+    }
+    __syncthreads();
+    *total = tot;
+    return wsum + x - v;
+}
+
+// ------------------------------------------------------------------ radix
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys,
+                                                             const uint32_t* n_dev, uint32_t n_host, int shift,
+                                                             uint32_t* __restrict__ hist, int blocks) {
+    __shared__ uint32_t h[8][256];
+    uint32_t n = read_count(n_dev, n_host);
+    uint32_t lo, hi;
+    block_range(n, blocks, blockIdx.x, lo, hi);
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) (&h[0][0])[i] = 0;
+    __syncthreads();
+    // warp-uniform trip count so that __match_any_sync sees full warps
+    for (uint32_t base = lo; base < hi; base += kSortThreads) {
+        uint32_t i = base + threadIdx.x;
+        bool valid = i < hi;
+        int d = valid ? (int)((keys[i] >> shift) & 255u) : 256;
+        unsigned peers = __match_any_sync(kFull, d);
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[warp][d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += kSortThreads) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) s += h[w][d];
+        hist[(size_t)d * blocks + blockIdx.x] = s;
+    }
+}
+
+// one CTA per digit: exclusive scan of its per-CTA counts, digit total to totals[d]
+__global__ void __launch_bounds__(kSortThreads) k_radix_scan(uint32_t* __restrict__ hist, int blocks,
+                                                             uint32_t* __restrict__ totals) {
+    __shared__ uint32_t sm[8];
+    int d = blockIdx.x;
+    uint32_t run = 0;
+    for (int b0 = 0; b0 < blocks; b0 += kSortThreads) {
+        int b = b0 + threadIdx.x;
+        uint32_t v = b < blocks ? hist[(size_t)d * blocks + b] : 0;
+        uint32_t tot;
+        uint32_t ex = block_exclusive_scan_256(v, sm, &tot);
+        if (b < blocks) hist[(size_t)d * blocks + b] = run + ex;
+        run += tot;
+    }
+    if (threadIdx.x == 0) totals[d] = run;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
+                                                                const uint32_t* __restrict__ vin,
+                                                                uint32_t* __restrict__ kout,
+                                                                uint32_t* __restrict__ vout, const uint32_t* n_dev,
+                                                                uint32_t n_host, int shift,
+                                                                const uint32_t* __restrict__ hist,
+                                                                const uint32_t* __restrict__ totals, int blocks) {
+    __shared__ uint32_t wh[8][256];
+    __shared__ uint32_t dbase[256];
+    __shared__ uint32_t sm[8];
+    uint32_t n = read_count(n_dev, n_host);
+    uint32_t lo, hi;
+    block_range(n, blocks, blockIdx.x, lo, hi);
+    if (lo >= hi) return;  // uniform per CTA
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    {
+        // start of digit d = sum of all smaller digits' totals, plus this CTA's offset within d
+        uint32_t tot;
+        uint32_t ex = block_exclusive_scan_256(totals[threadIdx.x], sm, &tot);
+        dbase[threadIdx.x] = ex + hist[(size_t)threadIdx.x * blocks + blockIdx.x];
+    }
+    unsigned lt = lanemask_lt();
+    for (uint32_t tile = lo; tile < hi; tile += kSortTile) {
+        for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) (&wh[0][0])[i] = 0;
+        __syncthreads();
+        uint32_t kk[kSortIPT], vv[kSortIPT], rank[kSortIPT];
+        int dd[kSortIPT];
+#pragma unroll
+        for (int j = 0; j < kSortIPT; ++j) {
+            uint32_t i = tile + warp * (kWarp * kSortIPT) + j * kWarp + lane;
+            bool valid = i < hi;
+            kk[j] = valid ? kin[i] : 0u;
+            vv[j] = valid ? vin[i] : 0u;
+            int d = valid ? (int)((kk[j] >> shift) & 255u) : 256;
+            unsigned peers = __match_any_sync(kFull, d);
+            uint32_t base = valid ? wh[warp][d] : 0u;
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) wh[warp][d] = base + (uint32_t)__popc(peers);
+            __syncwarp();
+            rank[j] = base + (uint32_t)__popc(peers & lt);
+            dd[j] = d;
+        }
+        __syncthreads();
+        {
+            int d = threadIdx.x;
+            uint32_t run = dbase[d];
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                uint32_t c = wh[w][d];
+                wh[w][d] = run;
+                run += c;
+            }
+            dbase[d] = run;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kSortIPT; ++j) {
+            if (dd[j] < 256) {
+                uint32_t pos = wh[warp][dd[j]] + rank[j];
+                kout[pos] = kk[j];
+                vout[pos] = vv[j];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+int sort_blocks_for(uint64_t n) {
+    uint64_t b = (n + kSortTile - 1) / kSortTile;
+    if (b < 1) b = 1;
+    if (b > (uint64_t)kMaxSortBlocks) b = kMaxSortBlocks;
+    return (int)b;
+}
+
+int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* n_dev,
+                     uint32_t n_host, int bits, int blocks, uint32_t* hist, cudaStream_t s) {
+    uint32_t* totals = hist + (size_t)kMaxSortBlocks * 256;
+    int cur = 0;
+    for (int shift = 0; shift < bits; shift += 8) {
+        uint32_t* ki = cur ? k1 : k0;
+        uint32_t* vi = cur ? v1 : v0;
+        uint32_t* ko = cur ? k0 : k1;
+        uint32_t* vo = cur ? v0 : v1;
+        k_radix_hist<<<blocks, kSortThreads, 0, s>>>(ki, n_dev, n_host, shift, hist, blocks);
+        k_radix_scan<<<256, kSortThreads, 0, s>>>(hist, blocks, totals);
+        k_radix_scatter<<<blocks, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_dev, n_host, shift, hist, totals, blocks);
+        cur ^= 1;
+    }
+    return cur;
+}
+
+// ------------------------------------------------------------------ scan
+
+// per 2048-item tile sum of cnt[idx[i]]
+__global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t* __restrict__ cnt,
+                                                     const uint32_t* __restrict__ idx, uint32_t n,
+                                                     uint32_t* __restrict__ sums) {
+    __shared__ uint32_t sm[8];
+    uint32_t base = blockIdx.x * kScanTile;
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        uint32_t i = base + j * 256 + threadIdx.x;
+        if (i < n) acc += cnt[idx[i]];
+    }
+    uint32_t tot;
+    block_exclusive_scan_256(acc, sm, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// single CTA: exclusive scan of the tile sums; grand total -> counters, with
+// the capacity check of the pair buffers
+__global__ void __launch_bounds__(256) k_scan_sums(uint32_t* __restrict__ sums, uint32_t nb,
+                                                   uint32_t* __restrict__ counters, int32_t* __restrict__ status,
+                                                   uint32_t capacity, unsigned long long* __restrict__ stats) {
+    __shared__ uint32_t sm[8];
+    uint64_t run = 0;
+    for (uint32_t b0 = 0; b0 < nb; b0 += 256) {
+        uint32_t b = b0 + threadIdx.x;
+        uint32_t v = b < nb ? sums[b] : 0;
+        uint32_t tot;
+        uint32_t ex = block_exclusive_scan_256(v, sm, &tot);
+        if (b < nb) sums[b] = (uint32_t)run + ex;
+        run += tot;
+    }
+    if (threadIdx.x == 0) {
+        uint32_t total = run > 0xffffffffull ? 0xffffffffu : (uint32_t)run;
+        atomicMax(&counters[kCntPairsMax], total);
+        stats[kStPairsSum] += run > capacity ? 0ull : run;
+        stats[kStBinnings] += 1ull;
+        if (run > capacity) {
+            status[kStatusCode] = GSC_ERR_CAPACITY;
+            counters[kCntPairs] = 0;  // every later stage of this render does nothing
+        } else {
+            counters[kCntPairs] = total;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scan_apply(const uint32_t* __restrict__ cnt,
+                                                    const uint32_t* __restrict__ idx, uint32_t n,
+                                                    const uint32_t* __restrict__ sums, uint32_t* __restrict__ out) {
+    __shared__ uint32_t sm[8];
+    uint32_t base = blockIdx.x * kScanTile;
+    uint32_t v[8];
+    uint32_t acc = 0;
+    // blocked arrangement: thread t owns items base + 8t .. base + 8t + 7
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        uint32_t i = base + threadIdx.x * 8 + j;
+        v[j] = i < n ? cnt[idx[i]] : 0u;
+        acc += v[j];
+    }
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan_256(acc, sm, &tot) + sums[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        uint32_t i = base + threadIdx.x * 8 + j;
+        if (i < n) out[i] = run;
+        run += v[j];
+    }
+}
+
+void scan_gathered(const uint32_t* cnt, const uint32_t* idx, uint32_t n, uint32_t* out, uint32_t* sums,
+                   uint32_t* counters, int32_t* status, uint32_t capacity, unsigned long long* stats, cudaStream_t s) {
+    uint32_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb == 0) nb = 1;
+    k_scan_reduce<<<nb, 256, 0, s>>>(cnt, idx, n, sums);
+    k_scan_sums<<<1, 256, 0, s>>>(sums, nb, counters, status, capacity, stats);
+    k_scan_apply<<<nb, 256, 0, s>>>(cnt, idx, n, sums, out);
+}
+
+}  // namespace gsc

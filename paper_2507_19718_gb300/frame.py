@@ -1,0 +1,100 @@
+"""One GSCache frame on the GPU (Sec. 3.1, Fig. 4): the path tracer produces
+the K intermediate path buffers, then every cache level is rendered,
+compared with its buffer by the HDR loss, differentiated and stepped by AdamW
+with the viewport-adaptive learning rate of Eq. 4.
+
+Every step is a call of the C ABI (``gsc``); this module only sequences the
+calls and owns the device tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import gsc, synth
+
+
+class CacheLevel:
+    """Parameters, gradients and Adam moments of one cache level (N x 16 FP32)."""
+
+    def __init__(self, params: np.ndarray, device="cuda"):
+        self.params = torch.from_numpy(np.ascontiguousarray(params, np.float32)).to(device)
+        self.grads = torch.zeros_like(self.params)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+
+    @property
+    def n(self) -> int:
+        return self.params.shape[0]
+
+
+class FrameLoop:
+    """Path-trace targets, then train and render a multi-level cache, per frame."""
+
+    def __init__(self, scene: synth.Scene, level_sizes, width: int, height: int, spp: int = 1,
+                 max_bounces: int = 8, seed: int = synth.BASE_SEED, tile=(16, 16), list_capacity: int = 256,
+                 max_pairs: int | None = None, weight_decay: float = 0.01, lr=None, device: str = "cuda",
+                 gaussian_seed: int | None = None, C_term: float = 0.0):
+        self.width, self.height = width, height
+        self.spp, self.max_bounces, self.seed = spp, max_bounces, seed
+        self.K = len(level_sizes)
+        self.C_term = C_term
+        self.scene = gsc.Scene.from_synth(scene, device)
+        gs = seed + 1000 if gaussian_seed is None else gaussian_seed
+        self.levels = [CacheLevel(synth.gaussians(n, gs + k), device) for k, n in enumerate(level_sizes)]
+        nmax = max(level_sizes)
+        if max_pairs is None:
+            # about 130 tiles per Gaussian at 1080p with 16x16 tiles (support
+            # radius ~90 px); scale with the pixel count and tile area
+            per = 200.0 * (width * height) / (1920 * 1080) * 256.0 / (tile[0] * tile[1])
+            max_pairs = int(min((1 << 31) - 1, max(1 << 16, nmax * max(per, 4.0))))
+        self.ws = gsc.Workspace(nmax, max_pairs, width, height, device)
+        self.cfg = gsc.raster_cfg(tile=tile, list_capacity=list_capacity)
+        self.lr = np.asarray(gsc.PAPER_LR if lr is None else lr, np.float32)
+        self.weight_decay = weight_decay
+        f32 = dict(dtype=torch.float32, device=device)
+        self.targets = torch.zeros((self.K, 3, height, width), **f32)
+        self.image = torch.zeros((3, height, width), **f32)
+        self.renders = torch.zeros((self.K, 3, height, width), **f32)
+        self.dL = torch.zeros((self.K, 3, height, width), **f32)
+        self.losses = torch.zeros((self.K,), **f32)
+        self.adam_step = 0
+        self.static_frames = 0
+        self._last_pose = None
+
+    def _schedule(self, c: gsc.Camera) -> float:
+        """Eq. 4: frames the viewport has been unchanged (pose compared bit for bit)."""
+        pose = bytes(c)
+        self.static_frames = self.static_frames + 1 if pose == self._last_pose else 1
+        self._last_pose = pose
+        return gsc.lr_scale(self.static_frames)
+
+    def trace(self, c: gsc.Camera, frame: int, stream=None):
+        cache = self.renders if self.C_term > 0 else None
+        gsc.trace(self.scene, c, self.spp, self.max_bounces, self.K, self.seed, frame, C_term=self.C_term,
+                  cache=cache, targets=self.targets, image=self.image, stream=stream)
+
+    def render_levels(self, c: gsc.Camera, stream=None):
+        for k, L in enumerate(self.levels):
+            gsc.cache_render(L.params, c, self.cfg, self.ws, image=self.renders[k], stream=stream)
+
+    def train_levels(self, c: gsc.Camera, lr_scale: float, stream=None):
+        self.adam_step += 1
+        adam = gsc.adam_params(self.lr, weight_decay=self.weight_decay, lr_scale=lr_scale, step=self.adam_step)
+        for k, L in enumerate(self.levels):
+            gsc.loss(gsc.LOSS_HDR, self.renders[k], self.targets[k], self.ws, dL_dpred=self.dL[k],
+                     loss_out=self.losses[k], stream=stream)
+            gsc.cache_backward(L.params, c, self.cfg, self.ws, self.dL[k], L.grads, stream=stream)
+            gsc.cache_step(L.params, L.grads, L.m, L.v, adam, stream=stream)
+
+    def frame(self, cam, frame: int, stream=None):
+        """One frame: render the cache (its images feed the tracer when C > 0),
+        trace the targets, then train every level on its buffer."""
+        c = cam if isinstance(cam, gsc.Camera) else gsc.camera(cam)
+        lr_scale = self._schedule(c)
+        self.render_levels(c, stream)
+        self.trace(c, frame, stream)
+        self.train_levels(c, lr_scale, stream)
+        return self.losses

@@ -99,21 +99,19 @@ def _hash_lattice(ix, iy, iz, seed):
 
 
 def _value_noise(res: int, freq: float, seed: int) -> np.ndarray:
+    """Value noise: hashed lattice values at integer points of x * freq,
+    smoothstep-interpolated along each axis (separably, axis by axis)."""
     x = np.linspace(0.0, 1.0, res) * freq
     i0 = np.floor(x).astype(np.int64)
     f = x - i0
-    f = f * f * (3 - 2 * f)  # smoothstep fade
-    out = np.zeros((res, res, res), np.float64)
-    for dz in (0, 1):
-        wz = f if dz else 1 - f
-        for dy in (0, 1):
-            wy = f if dy else 1 - f
-            for dx in (0, 1):
-                wx = f if dx else 1 - f
-                v = _hash_lattice((i0 + dx)[None, None, :], (i0 + dy)[None, :, None],
-                                  (i0 + dz)[:, None, None], seed)
-                out += v * wz[:, None, None] * wy[None, :, None] * wx[None, None, :]
-    return out
+    f = f * f * (3 - 2 * f)
+    n = int(i0.max()) + 2
+    lat = np.arange(n)
+    L = _hash_lattice(lat[None, None, :], lat[None, :, None], lat[:, None, None], seed)  # [z][y][x]
+    L = L[:, :, i0] * (1 - f)[None, None, :] + L[:, :, i0 + 1] * f[None, None, :]
+    L = L[:, i0, :] * (1 - f)[None, :, None] + L[:, i0 + 1, :] * f[None, :, None]
+    L = L[i0, :, :] * (1 - f)[:, None, None] + L[i0 + 1, :, :] * f[:, None, None]
+    return L
 
 
 def fbm_volume(res: int, n_blobs: int, seed: int, peak: float = 20.0, octaves: int = 4,

@@ -17,3 +17,16 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """The CUDA library, built in-tree; a GPU test fails (never skips) when
+    the GPU or the library is unavailable."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for -m gpu tests")
+    from paper_2507_19718_gb300 import build, gsc
+    build.build()
+    gsc.lib(build_if_missing=False)
+    return gsc

@@ -1,0 +1,100 @@
+"""The C-ABI library builds, loads without a GPU, exports every function that
+include/gsc.h declares, and rejects bad arguments on the host before any CUDA
+call.  No compute call is made here."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gsc.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gsc_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2507_19718_gb300 import build, gsc
+    build.build()
+    return gsc.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    from paper_2507_19718_gb300 import gsc
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(gsc.SIGNATURES) == names
+
+
+def test_version_and_lr_schedule(L, orc):
+    assert L.gsc_abi_version() == 1
+    for t in [0, 1, 2, 3, 10, 100, 12345]:
+        assert L.gsc_lr_scale(t) == pytest.approx(orc.lr_scale(max(t, 1)), rel=1e-7)
+
+
+def test_workspace_size_grows_with_limits(L):
+    from paper_2507_19718_gb300 import gsc
+    def size(*a):
+        n = C.c_size_t()
+        assert L.gsc_workspace_size(*a, None, C.byref(n)) == 0
+        return n.value
+    a = size(1024, 100000, 128, 128)
+    b = size(2048, 100000, 128, 128)
+    c = size(1024, 200000, 128, 128)
+    d = size(1024, 100000, 1920, 1080)
+    assert 0 < a < b and a < c and a < d and a % 256 == 0
+    # 4 arrays of 4-byte (key, value) per pair
+    assert c - a >= 100000 * 16 - 4 * 256
+    n = C.c_size_t()
+    assert L.gsc_workspace_size(-1, 10, 8, 8, None, C.byref(n)) == gsc.GSC_ERR_INVALID_ARG
+
+
+def test_host_side_validation(L):
+    from paper_2507_19718_gb300 import gsc
+    # scene: grid too small
+    d = gsc.SceneDesc()
+    d.nx, d.ny, d.nz = 1, 8, 8
+    d.density = 0x1000
+    d.density_max, d.sigma_max, d.albedo, d.tf_count = 20.0, 20.0, 0.8, 2
+    d.tf_pos[:2] = [0.0, 1.0]
+    h = C.c_void_p()
+    assert L.gsc_scene_create(C.byref(d), C.byref(h)) == gsc.GSC_ERR_INVALID_ARG
+    buf = C.create_string_buffer(256)
+    L.gsc_last_error(buf, 256)
+    assert b"grid" in buf.value
+    # a valid descriptor creates a host-only handle (nothing is enqueued)
+    d.nx = 8
+    assert L.gsc_scene_create(C.byref(d), C.byref(h)) == 0
+    pos = (C.c_float * 2)(0.5, 0.2)
+    rgba = (C.c_float * 8)(*([0.5] * 8))
+    assert L.gsc_scene_set_tf(h, 2, pos, rgba) == gsc.GSC_ERR_INVALID_ARG  # not ascending
+    assert L.gsc_scene_destroy(h) == 0
+    # workspace: unaligned buffer / too small
+    w = C.c_void_p()
+    assert L.gsc_workspace_create(C.c_void_p(0x1001), 1 << 30, 16, 16, 8, 8, None, C.byref(w)) == \
+        gsc.GSC_ERR_INVALID_ARG
+    assert L.gsc_workspace_create(C.c_void_p(0x1000), 16, 16, 16, 8, 8, None, C.byref(w)) == gsc.GSC_ERR_OOM
+    # render: bad tile shape, then NULL workspace
+    cam = gsc.Camera()
+    cam.fx = cam.fy = 100.0
+    cam.width = cam.height = 32
+    cfg = gsc.raster_cfg(tile=(12, 12))
+    assert L.gsc_cache_render(None, 0, C.byref(cam), C.byref(cfg), None, None, None) == gsc.GSC_ERR_INVALID_ARG
+    cfg = gsc.raster_cfg(tile=(16, 16), list_capacity=100)
+    assert L.gsc_cache_render(None, 0, C.byref(cam), C.byref(cfg), None, None, None) == gsc.GSC_ERR_INVALID_ARG
+    cfg = gsc.raster_cfg()
+    assert L.gsc_cache_render(None, 0, C.byref(cam), C.byref(cfg), None, None, None) == gsc.GSC_ERR_INVALID_ARG
+    # optimiser: bad hyper-parameters
+    a = gsc.adam_params([0.01] * 16, step=0)
+    assert L.gsc_cache_step(C.c_void_p(256), C.c_void_p(256), C.c_void_p(256), C.c_void_p(256), 4, C.byref(a),
+                            None) == gsc.GSC_ERR_INVALID_ARG
+    # loss: kind not available / crop outside
+    assert L.gsc_loss(7, C.c_void_p(256), C.c_void_p(256), 3, 8, 8, None, None, C.c_void_p(256), C.c_void_p(256),
+                      None) == gsc.GSC_ERR_INVALID_ARG

@@ -1,0 +1,191 @@
+"""GPU parity of the Gaussian-splatting render and its gradient (Sec. 3.1,
+Sec. 3.5) against the FP64 oracle, through the C ABI.
+
+Forward: within 1e-4 absolute per channel on every pixel whose compositing
+decisions are not within 2e-4 of a threshold (the oracle flags those; they
+must be rare).  Tile size and staging capacity do not change a single bit.
+Backward: dL/dimage random, zeroed on flagged pixels, gradients within
+|d| <= 1e-3 max(|g|, 1e-3 max_group |g|) per parameter group.
+"""
+import numpy as np
+import pytest
+
+from paper_2507_19718_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+GROUPS = {"mean": [0, 1, 2], "opacity": [3], "logscale": [4, 5, 6], "rotation": [8, 9, 10, 11],
+          "color": [12, 13, 14]}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ws(gsc, n, pairs, w, h):
+    return gsc.Workspace(n, pairs, w, h)
+
+
+def _render(gsc, p_np, cam, cfg, ws):
+    torch = _torch()
+    p = torch.from_numpy(p_np).cuda()
+    img = gsc.cache_render(p, cam, cfg, ws)
+    ws.status()
+    return img.cpu().numpy().astype(np.float64)
+
+
+def _scene0(n=1024, w=128, h=128, angle=30.0, seed=synth.BASE_SEED + 2):
+    return synth.gaussians(n, seed), synth.orbit_camera(w, h, angle)
+
+
+def _compare_forward(gpu_img, orc_img, marg, tol=1e-4):
+    assert marg.mean() < 0.02, marg.mean()
+    ok = ~marg
+    err = np.abs(gpu_img - orc_img)[:, ok]
+    assert err.max() <= tol, (err.max(), np.unravel_index(np.argmax(np.abs(gpu_img - orc_img)), gpu_img.shape))
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
+def test_render_matches_oracle_config0(gpu, orc, tile):
+    p, cam = _scene0()
+    ws = _ws(gpu, len(p), 1 << 21, cam.width, cam.height)
+    img = _render(gpu, p, cam, gpu.raster_cfg(tile=tile), ws)
+    ref, marg, ncon, _ = orc.render(p, cam)
+    assert ncon.max() > 20 and ref.max() > 0.3
+    _compare_forward(img, ref, marg)
+
+
+def test_tile_and_capacity_do_not_change_bits(gpu, orc):
+    p, cam = _scene0(angle=75.0)
+    ws = _ws(gpu, len(p), 1 << 22, cam.width, cam.height)
+    base = _render(gpu, p, cam, gpu.raster_cfg(tile=(16, 16), list_capacity=256), ws)
+    for tile, cap in [((8, 8), 64), ((32, 8), 2048), ((16, 8), 32), ((8, 16), 512), ((8, 32), 128),
+                      ((32, 4), 96)]:
+        other = _render(gpu, p, cam, gpu.raster_cfg(tile=tile, list_capacity=cap), ws)
+        np.testing.assert_array_equal(other, base, err_msg=str((tile, cap)))
+
+
+def test_ragged_image_and_degenerate_gaussians(gpu, orc):
+    # image size not a multiple of the tile; Gaussians behind the camera, off
+    # screen, transparent, with a zero quaternion, and one covering the frame
+    p, cam = _scene0(n=300, w=100, h=75, angle=200.0, seed=9)
+    fwd = cam.R[2].astype(np.float64)
+    p[0, 0:3] = (cam.pos - 0.5 * fwd).astype(np.float32)   # behind the camera
+    p[1, 0:3] = (cam.pos + 0.1 * fwd).astype(np.float32)   # before the near plane
+    p[2, 0:3] = (cam.pos + 2.0 * fwd + 5.0 * cam.R[0]).astype(np.float32)  # off screen
+    p[3, 3] = -9.0                                          # opacity below alpha_min
+    p[4, 8:12] = 0.0                                        # degenerate rotation
+    p[5, 0:3] = (cam.pos + 1.2 * fwd).astype(np.float32)
+    p[5, 4:7] = -0.3                                        # huge: covers the frame
+    p[5, 3] = -2.0
+    ws = _ws(gpu, len(p), 1 << 20, cam.width, cam.height)
+    for tile in [(16, 16), (8, 8), (32, 8)]:
+        img = _render(gpu, p, cam, gpu.raster_cfg(tile=tile), ws)
+        ref, marg, _, _ = orc.render(p, cam)
+        _compare_forward(img, ref, marg)
+    assert ref[:, 0, 0].sum() > 0  # the big Gaussian reaches the corner
+
+
+def test_empty_and_single(gpu, orc):
+    torch = _torch()
+    p, cam = _scene0(n=1, w=40, h=24, seed=4)
+    p[0, 0:3] = [0.5, 0.5, 0.5]
+    p[0, 4:7] = -2.0
+    ws = _ws(gpu, 4, 1 << 12, cam.width, cam.height)
+    img = _render(gpu, p, cam, gpu.raster_cfg(), ws)
+    ref, marg, _, _ = orc.render(p, cam)
+    _compare_forward(img, ref, marg)
+    out = torch.full((3, cam.height, cam.width), 7.0, device="cuda")
+    gpu.cache_render(torch.zeros((0, 16), device="cuda"), cam, gpu.raster_cfg(), ws, image=out)
+    assert float(out.abs().max()) == 0.0
+
+
+def test_pair_capacity_overflow_is_reported(gpu):
+    torch = _torch()
+    p, cam = _scene0()
+    ws = _ws(gpu, len(p), 1000, cam.width, cam.height)
+    img = gpu.cache_render(torch.from_numpy(p).cuda(), cam, gpu.raster_cfg(), ws)
+    with pytest.raises(gpu.GscError) as e:
+        ws.status()
+    assert e.value.status == gpu.GSC_ERR_CAPACITY
+    assert float(img.abs().max()) == 0.0  # nothing was composited, nothing overran
+    need = _ws(gpu, len(p), 1 << 21, cam.width, cam.height)
+    gpu.cache_render(torch.from_numpy(p).cuda(), cam, gpu.raster_cfg(), need)
+    n = need.status()
+    assert 1000 < n < (1 << 21)
+
+
+def _grad_compare(g_gpu, g_ref, tol=1e-3):
+    for name, slots in GROUPS.items():
+        a, b = g_gpu[:, slots], g_ref[:, slots]
+        floor = 1e-3 * np.abs(b).max()
+        bad = np.abs(a - b) > tol * np.maximum(np.abs(b), floor)
+        assert not bad.any(), (name, np.argwhere(bad)[:5], a[bad][:5], b[bad][:5])
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
+def test_backward_matches_oracle_config0(gpu, orc, tile):
+    torch = _torch()
+    p, cam = _scene0(w=96, h=80)
+    _, marg, _, _ = orc.render(p, cam, grad_margins=True)
+    dL = np.random.default_rng(5).uniform(-1, 1, (3, cam.height, cam.width))
+    dL[:, marg] = 0.0
+    dL = dL.astype(np.float32)
+    ref, _ = orc.render_backward(p, cam, dL.astype(np.float64))
+    ws = _ws(gpu, len(p), 1 << 21, cam.width, cam.height)
+    g = gpu.cache_backward(torch.from_numpy(p).cuda(), cam, gpu.raster_cfg(tile=tile), ws,
+                           torch.from_numpy(dL).cuda())
+    ws.status()
+    g = g.cpu().numpy().astype(np.float64)
+    assert np.all(g[:, [7, 15]] == 0)
+    assert np.abs(ref).max() > 0
+    _grad_compare(g, ref)
+
+
+def test_backward_accumulates_and_autograd_matches(gpu, orc):
+    torch = _torch()
+    p, cam = _scene0(n=400, w=64, h=48, seed=12)
+    ws = _ws(gpu, len(p), 1 << 20, cam.width, cam.height)
+    cfg = gpu.raster_cfg()
+    params = torch.from_numpy(p).cuda().requires_grad_(True)
+    w = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, (3, 48, 64)).astype(np.float32)).cuda()
+    img = gpu.render(params, cam, cfg, ws)
+    (img * w).sum().backward()
+    direct = gpu.cache_backward(params.detach(), cam, cfg, ws, w)
+    np.testing.assert_allclose(params.grad.cpu().numpy(), direct.cpu().numpy(), rtol=1e-5, atol=1e-7)
+    twice = gpu.cache_backward(params.detach(), cam, cfg, ws, w, grads=direct.clone())
+    np.testing.assert_allclose(twice.cpu().numpy(), 2 * direct.cpu().numpy(), rtol=1e-5, atol=1e-7)
+
+
+def test_full_size_1080p_1M_sampled(gpu, orc):
+    """At the benchmark's size (1920x1080, 1M Gaussians, 16x16 tiles):
+    sampled windows of the image against the oracle, and the gradient of a
+    loss living on a 32x32 crop against the oracle's crop gradient."""
+    torch = _torch()
+    n = 1_000_000
+    p = synth.gaussians(n, synth.BASE_SEED + 3)
+    cam = synth.orbit_camera(1920, 1080, 20.0)
+    ws = _ws(gpu, n, 400_000_000, 1920, 1080)
+    cfg = gpu.raster_cfg()
+    params = torch.from_numpy(p).cuda()
+    img = gpu.cache_render(params, cam, cfg, ws)
+    need = ws.status()
+    assert need > 10_000_000
+    img = img.cpu().numpy()
+    for (x0, y0) in [(940, 520), (700, 300), (1300, 800), (0, 0)]:
+        ref, marg, _, _ = orc.render(p, cam, window=(x0, y0, 8, 8))
+        _compare_forward(img[:, y0:y0 + 8, x0:x0 + 8].astype(np.float64), ref, marg)
+    crop = (944, 524, 32, 32)
+    _, marg, _, _ = orc.render(p, cam, window=crop, grad_margins=True)
+    dl = np.random.default_rng(2).uniform(-1, 1, (3, 32, 32))
+    dl[:, marg] = 0
+    full = np.zeros((3, 1080, 1920), np.float32)
+    full[:, 524:556, 944:976] = dl
+    ref, _ = orc.render_backward(p, cam, dl, window=crop)
+    g = gpu.cache_backward(params, cam, cfg, ws, torch.from_numpy(full).cuda())
+    ws.status()
+    g = g.cpu().numpy().astype(np.float64)
+    touched = np.abs(ref).sum(1) > 0
+    assert touched.sum() > 100
+    _grad_compare(g, ref)
