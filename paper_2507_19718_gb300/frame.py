@@ -46,9 +46,10 @@ class FrameLoop:
         self.levels = [CacheLevel(synth.gaussians(n, gs + k), device) for k, n in enumerate(level_sizes)]
         nmax = max(level_sizes)
         if max_pairs is None:
-            # about 130 tiles per Gaussian at 1080p with 16x16 tiles (support
-            # radius ~90 px); scale with the pixel count and tile area
-            per = 200.0 * (width * height) / (1920 * 1080) * 256.0 / (tile[0] * tile[1])
+            # log-normal scales (N(-3, 0.5)) make the large Gaussians dominate:
+            # about 370 tiles per Gaussian at 1080p with 16x16 tiles; keep
+            # headroom and scale with the pixel count and tile area
+            per = 640.0 * (width * height) / (1920 * 1080) * 256.0 / (tile[0] * tile[1])
             max_pairs = int(min((1 << 31) - 1, max(1 << 16, nmax * max(per, 4.0))))
         self.ws = gsc.Workspace(nmax, max_pairs, width, height, device)
         self.cfg = gsc.raster_cfg(tile=tile, list_capacity=list_capacity)

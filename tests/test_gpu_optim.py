@@ -22,7 +22,8 @@ def test_hdr_loss_matches_oracle(gpu, orc, kind, crop):
     val, grad = gpu.loss(kind, _t(pred), _t(tgt), ws, crop=crop)
     ref, rgrad = orc.loss_hdr(pred, tgt, crop=crop, full_grad=bool(kind))
     assert float(val) == pytest.approx(ref, rel=2e-6)
-    np.testing.assert_allclose(grad.cpu().numpy(), rgrad, rtol=2e-6, atol=1e-12)
+    # FP32 error of the largest term; the full-gradient variant cancels two terms
+    np.testing.assert_allclose(grad.cpu().numpy(), rgrad, rtol=2e-6, atol=1e-6 * np.abs(rgrad).max())
 
 
 def test_adamw_matches_oracle(gpu, orc):
@@ -38,10 +39,23 @@ def test_adamw_matches_oracle(gpu, orc):
     P, G, M, V = _t(p), _t(g), _t(m), _t(v)
     gpu.cache_step(P, G, M, V, a)
     rp, rg, rm, rv = (x.astype(np.float64).reshape(-1) for x in (p, g, m, v))
-    orc.adamw(rp, rg, rm, rv, lr.astype(np.float64), 0.6, 0.9, 0.999, 1e-15, 0.01, 5)
-    np.testing.assert_allclose(P.cpu().numpy().reshape(-1), rp, rtol=1e-6, atol=1e-7)
-    np.testing.assert_allclose(M.cpu().numpy().reshape(-1), rm, rtol=1e-5, atol=1e-10)
-    np.testing.assert_allclose(V.cpu().numpy().reshape(-1), rv, rtol=1e-5, atol=1e-12)
+    # the kernel receives FP32 hyper-parameters; the oracle gets the same values
+    f = lambda x: float(np.float32(x))  # noqa: E731
+    orc.adamw(rp, rg, rm, rv, lr.astype(np.float64), f(0.6), f(0.9), f(0.999), f(1e-15), f(0.01), 5)
+    # FP32 rounding of the update (a few ulp of |dp|) and of the final sum (of |p|)
+    got = P.cpu().numpy().reshape(-1).astype(np.float64)
+    dp = np.abs(rp - p.reshape(-1).astype(np.float64))
+    bound = 1e-6 * np.abs(rp) + 8e-6 * dp + 1e-9
+    assert np.all(np.abs(got - rp) <= bound), np.max(np.abs(got - rp) / bound)
+    # moments: a few FP32 ulps of the two summed terms (they may cancel)
+    g64, m64, v64 = (x.reshape(-1).astype(np.float64) for x in (g, m, v))
+    live = np.tile(lr > 0, n)
+    bm = 4e-7 * (np.abs(m64) + 0.1 * np.abs(g64)) + 1e-30
+    bv = 4e-7 * (v64 + 0.001 * g64 * g64) + 1e-30
+    gm, gv = M.cpu().numpy().reshape(-1), V.cpu().numpy().reshape(-1)
+    assert np.all(np.abs(gm - rm)[live] <= bm[live])
+    assert np.all(np.abs(gv - rv)[live] <= bv[live])
+    np.testing.assert_array_equal(gm[~live], m.reshape(-1)[~live])
     assert float(G.abs().max()) == 0.0
     frozen = np.tile(lr == 0, n)
     np.testing.assert_array_equal(P.cpu().numpy().reshape(-1)[frozen], p.reshape(-1)[frozen])

@@ -39,8 +39,10 @@ def _scene0(n=1024, w=128, h=128, angle=30.0, seed=synth.BASE_SEED + 2):
     return synth.gaussians(n, seed), synth.orbit_camera(w, h, angle)
 
 
-def _compare_forward(gpu_img, orc_img, marg, tol=1e-4):
-    assert marg.mean() < 0.02, marg.mean()
+def _compare_forward(gpu_img, orc_img, marg, tol=1e-4, max_marginal=0.02):
+    # at 1M Gaussians a pixel tests thousands of alphas, so more of them have
+    # one decision within the margin; the comparison set must stay large
+    assert marg.mean() < max_marginal, marg.mean()
     ok = ~marg
     err = np.abs(gpu_img - orc_img)[:, ok]
     assert err.max() <= tol, (err.max(), np.unravel_index(np.argmax(np.abs(gpu_img - orc_img)), gpu_img.shape))
@@ -174,8 +176,8 @@ def test_full_size_1080p_1M_sampled(gpu, orc):
     assert need > 10_000_000
     img = img.cpu().numpy()
     for (x0, y0) in [(940, 520), (700, 300), (1300, 800), (0, 0)]:
-        ref, marg, _, _ = orc.render(p, cam, window=(x0, y0, 8, 8))
-        _compare_forward(img[:, y0:y0 + 8, x0:x0 + 8].astype(np.float64), ref, marg)
+        ref, marg, _, _ = orc.render(p, cam, window=(x0, y0, 16, 16))
+        _compare_forward(img[:, y0:y0 + 16, x0:x0 + 16].astype(np.float64), ref, marg, max_marginal=0.15)
     crop = (944, 524, 32, 32)
     _, marg, _, _ = orc.render(p, cam, window=crop, grad_margins=True)
     dl = np.random.default_rng(2).uniform(-1, 1, (3, 32, 32))
