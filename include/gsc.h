@@ -242,6 +242,26 @@ gsc_status gsc_cache_backward(const float* params, int64_t N, const gsc_camera* 
 gsc_status gsc_loss(int32_t kind, const float* pred, const float* target, int32_t C, int32_t H, int32_t W,
                     const int32_t* crop, float* dL_dpred, float* loss_out, gsc_workspace* ws, gsc_stream_t stream);
 
+/* gsc_loss without a workspace, for callers that cannot allocate device
+ * memory or hand the library a buffer at the point of the call: a plug-in
+ * running inside a host application that owns every device allocation, a
+ * real-time frame loop that forbids allocation after start-up, or code that
+ * only has the two images.  The paper has no counterpart; this is a library
+ * convenience.  Same loss kinds, crop, outputs and results as gsc_loss
+ * (GSC_LOSS_L1_SSIM is not available here).
+ *
+ * Scratch: the per-CTA partial sums live in a fixed array inside the library
+ * (32,768 floats, 128 KiB, held by every device that loads the library until
+ * the process exits), so C * w * h may be at most 8,388,608 elements (e.g.
+ * 3 x 1920 x 1080 fits); larger crops return GSC_ERR_CAPACITY.  The first
+ * call on each device looks up the array's device address (with that device
+ * current), so make that first call before capturing a stream into a graph.
+ * Every call uses the same array: calls that can run at the same time on the
+ * GPU (different streams without ordering) race and give wrong losses.
+ * Nothing in the array needs clearing between calls.  Allocates nothing. */
+gsc_status gsc_loss_noalloc(int32_t kind, const float* pred, const float* target, int32_t C, int32_t H, int32_t W,
+                            const int32_t* crop, float* dL_dpred, float* loss_out, gsc_stream_t stream);
+
 /* AdamW with decoupled weight decay (Sec. 3.6 "Regularization"); per-slot
  * learning rates (the paper's per-attribute LRs, Sec. 4.1) scaled by
  * lr_scale (Eq. 4, see gsc_lr_scale).  step is 1-based (bias correction).

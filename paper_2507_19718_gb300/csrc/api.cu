@@ -87,6 +87,18 @@ gsc_status fail(gsc_status st, const char* fmt, ...) {
     return st;
 }
 
+}  // namespace
+
+gsc_status gsc::set_error(gsc_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+namespace {
+
 gsc_status cuda_fail(cudaError_t e, const char* where) {
     return fail(GSC_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }

@@ -34,6 +34,9 @@ struct RasterDev {
     int tile_w, tile_h, tiles_x, tiles_y, cap;
 };
 
+// sets the calling thread's last error message (api.cu) and returns st
+gsc_status set_error(gsc_status st, const char* fmt, ...);
+
 // instrumentation (api.cu): event-timed phases and the launch counter
 enum Phase : int {
     kPhProject, kPhDepthSort, kPhScan, kPhEmit, kPhTileSort, kPhRanges, kPhRender, kPhRenderBwd, kPhProjectBwd,

@@ -89,6 +89,80 @@ cudaError_t launch_loss(int kind, const float* pred, const float* target, int C,
     return cudaErrorInvalidValue;
 }
 
+// ------------------------------------------------------------------ loss without a workspace
+//
+// gsc_loss_noalloc: the same two kernels as gsc_loss, launched with one CTA
+// per 256 elements, whose partial sums go to the file-scope array below
+// instead of a workspace.  The array is the library's own: every device that
+// loads the library holds it (128 KiB) until the process exits.  Host code
+// may not pass the symbol itself to a kernel (on the host it is only a
+// stand-in); its device address is looked up once per device.
+
+constexpr int kNoAllocSlots = 32768;  // partial sums = CTAs of 256 elements
+static __device__ __align__(256) float g_noalloc_partials[kNoAllocSlots];
+
+}  // namespace gsc
+
+#include <mutex>
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" gsc_status gsc_loss_noalloc(int32_t kind, const float* pred, const float* target, int32_t C, int32_t H,
+                                       int32_t W, const int32_t* crop, float* dL_dpred, float* loss_out,
+                                       gsc_stream_t stream) {
+    using namespace gsc;
+    if (!pred || !target || !loss_out) return set_error(GSC_ERR_INVALID_ARG, "gsc_loss_noalloc: NULL argument");
+    if (kind != GSC_LOSS_HDR && kind != GSC_LOSS_HDR_FULLGRAD)
+        return set_error(GSC_ERR_INVALID_ARG, "gsc_loss_noalloc: loss kind %d not available", kind);
+    if (C < 1 || H < 1 || W < 1) return set_error(GSC_ERR_INVALID_ARG, "gsc_loss_noalloc: empty image");
+    int x0 = 0, y0 = 0, w = W, h = H;
+    if (crop) {
+        x0 = crop[0]; y0 = crop[1]; w = crop[2]; h = crop[3];
+        if (x0 < 0 || y0 < 0 || w < 1 || h < 1 || x0 + w > W || y0 + h > H)
+            return set_error(GSC_ERR_INVALID_ARG, "gsc_loss_noalloc: crop outside the image");
+    }
+    size_t n = (size_t)C * w * h;
+    size_t blocks = (n + kRedThreads - 1) / kRedThreads;
+    if (blocks > (size_t)kNoAllocSlots)
+        return set_error(GSC_ERR_CAPACITY,
+                         "gsc_loss_noalloc: %zu elements exceed the fixed scratch (at most %d elements)", n,
+                         kNoAllocSlots * kRedThreads);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return set_error(GSC_ERR_CUDA, "gsc_loss_noalloc: no current device");
+    float* partials = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+            if (e != cudaSuccess || !p)
+                return set_error(GSC_ERR_CUDA, "gsc_loss_noalloc: scratch address lookup failed: %s",
+                                 cudaGetErrorString(e));
+            g_noalloc_ptr[dev] = (float*)p;
+        }
+        partials = g_noalloc_ptr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dL_dpred && (x0 != 0 || y0 != 0 || w != W || h != H))
+        if (cudaMemsetAsync(dL_dpred, 0, sizeof(float) * (size_t)C * H * W, s) != cudaSuccess)
+            return set_error(GSC_ERR_CUDA, "gsc_loss_noalloc: clearing dL_dpred failed");
+    float invk = (float)(1.0 / (double)n);
+    PhaseScope ph(kPhLoss, s, 2);
+    k_loss_hdr<<<(unsigned)blocks, kRedThreads, 0, s>>>(pred, target, C, H, W, x0, y0, w, h,
+                                                        kind == GSC_LOSS_HDR_FULLGRAD, invk, dL_dpred, partials);
+    k_reduce_final<<<1, 1024, 0, s>>>(partials, (int)blocks, 1.0 / (double)n, loss_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(GSC_ERR_CUDA, "gsc_loss_noalloc launch: %s", cudaGetErrorString(e));
+    return GSC_OK;
+}
+
+namespace gsc {
+
 // ------------------------------------------------------------------ AdamW
 
 struct AdamDev {

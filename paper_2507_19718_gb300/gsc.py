@@ -81,6 +81,7 @@ SIGNATURES = {
     "gsc_cache_render": (_i32, [_vp, _i64, C.POINTER(Camera), C.POINTER(RasterCfg), _vp, _vp, _vp]),
     "gsc_cache_backward": (_i32, [_vp, _i64, C.POINTER(Camera), C.POINTER(RasterCfg), _vp, _vp, _vp, _vp]),
     "gsc_loss": (_i32, [_i32, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "gsc_loss_noalloc": (_i32, [_i32, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp]),
     "gsc_cache_step": (_i32, [_vp, _vp, _vp, _vp, _i64, C.POINTER(AdamParams), _vp]),
     "gsc_lr_scale": (_f32, [_i32]),
     "gsc_profile_enable": (_i32, [_i32]),
@@ -337,6 +338,24 @@ def loss(kind: int, pred: torch.Tensor, target: torch.Tensor, ws: Workspace, cro
         cr = (C.c_int32 * 4)(*[int(x) for x in crop])
     _check(lib().gsc_loss(kind, _ptr(pred), _ptr(target), Cc, H, W, cr, _ptr(dL_dpred) if want_grad else None,
                           _ptr(loss_out), ws.handle, _stream(stream)))
+    return loss_out, dL_dpred
+
+
+def loss_noalloc(kind: int, pred: torch.Tensor, target: torch.Tensor, crop=None,
+                 dL_dpred: torch.Tensor | None = None, loss_out: torch.Tensor | None = None,
+                 want_grad: bool = True, stream=None):
+    """gsc_loss_noalloc: the loss without a workspace (the library's own
+    fixed scratch; at most 8,388,608 elements)."""
+    _need(pred, "pred")
+    _need(target, "target", pred.numel())
+    Cc, H, W = pred.shape
+    if want_grad and dL_dpred is None:
+        dL_dpred = torch.empty_like(pred)
+    if loss_out is None:
+        loss_out = torch.empty((), dtype=torch.float32, device=pred.device)
+    cr = (C.c_int32 * 4)(*[int(x) for x in crop]) if crop is not None else None
+    _check(lib().gsc_loss_noalloc(kind, _ptr(pred), _ptr(target), Cc, H, W, cr,
+                                  _ptr(dL_dpred) if want_grad else None, _ptr(loss_out), _stream(stream)))
     return loss_out, dL_dpred
 
 
