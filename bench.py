@@ -37,7 +37,7 @@ TOTAL_GAUSSIANS = 1_000_000
 LEVELS = 3
 SPP, BOUNCES = 1, 8
 ORBIT_DEG_PER_FRAME = 0.5
-TILE, LIST_CAP = (16, 16), 256
+TILE, LIST_CAP, BIN = (16, 16), 256, 64
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # FP32 FMA lanes: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (maximum SM clock)
@@ -52,7 +52,7 @@ def workload_config():
                     "(1M Gaussians) render + HDR loss + backward + AdamW",
         "width": WIDTH, "height": HEIGHT, "gaussians": TOTAL_GAUSSIANS, "levels": sizes, "spp": SPP,
         "max_bounces": BOUNCES, "volume": "256^3 fp32: 64 blobs + 4-octave fBm, 8-point TF",
-        "lights": "directional 3.0 + environment 0.3", "tile": list(TILE), "list_capacity": LIST_CAP,
+        "lights": "directional 3.0 + environment 0.3", "tile": list(TILE), "list_capacity": LIST_CAP, "bin": BIN,
         "camera": f"orbit r=2.2, fov_y 45 deg, {ORBIT_DEG_PER_FRAME} deg/frame",
         "l2": "inputs larger than L2 (params+moments 256 MB, pair buffers GBs)", "parallelism": "replicas",
     }
@@ -169,7 +169,7 @@ def phase_algorithmic(phase, c, n_gauss_calls, n_pixels_calls, frames):
     if phase == "render_bwd":
         return "flop", 10.0 * c["eval_rewalk"] + 40.0 * c["eval_back"]
     if phase == "tile_sort":
-        return "byte", 2 * 20.0 * M
+        return "byte", 2 * 20.0 * M   # pairs are (bin, Gaussian); 2 passes of 8-bit digits
     if phase == "depth_sort":
         return "byte", 4 * 20.0 * n_gauss_calls
     if phase == "emit":
@@ -203,7 +203,8 @@ def run_ours(args, world, rank, local):
     cfg = workload_config()
     scene = synth.scene_frame(256, seed=synth.BASE_SEED + 1)
     loop = FrameLoop(scene, cfg["levels"], WIDTH, HEIGHT, spp=SPP, max_bounces=BOUNCES,
-                     seed=synth.BASE_SEED + 17 * rank, tile=TILE, list_capacity=LIST_CAP, device=dev)
+                     seed=synth.BASE_SEED + 17 * rank, tile=TILE, list_capacity=LIST_CAP, device=dev,
+                     bin_size=BIN)
     cams = [gsc.camera(synth.orbit_camera(WIDTH, HEIGHT, ORBIT_DEG_PER_FRAME * f))
             for f in range(args.warmup + 2 * args.steps + 1)]
     stream = torch.cuda.current_stream()
@@ -317,7 +318,7 @@ def oracle_sample(rank=0):
     oracle.build()
     sizes = synth.level_sizes(TOTAL_GAUSSIANS, LEVELS)
     cam = synth.orbit_camera(WIDTH, HEIGHT, 0.0)
-    win = (880, 495, 160, 90)
+    win = (720, 405, 480, 270)
     frame_px, win_px = WIDTH * HEIGHT, win[2] * win[3]
     est_s, used_s = 0.0, 0.0
     for k, n in enumerate(sizes):

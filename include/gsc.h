@@ -75,17 +75,22 @@ typedef struct gsc_camera {
     int32_t width, height;
 } gsc_camera;
 
-/* Rasterizer configuration.  Tiles must satisfy tile_w * tile_h in
- * {64, 128, 256} with tile_w, tile_h in {8, 16, 32} (e.g. 8x8, 16x16, 32x8).
- * list_capacity: Gaussian entries staged in shared memory per batch
- * (64..2048, multiple of 32).  alpha_max (0.99), alpha_min (1/255), T_min
- * (1e-4), near_plane (0.2) and dilation (0.3 px^2) are the compositing
+/* Rasterizer configuration.  Tiles (one CTA each, one thread per pixel):
+ * 16x16, 8x8, 32x8, 16x8, 8x16, 8x32 or 32x4.  Gaussians are binned into
+ * coarse square bins of bin_size pixels (a multiple of tile_w and tile_h,
+ * 32..512; 0 = 64); every tile walks its bin's depth-ordered list and keeps
+ * the Gaussians whose support reaches the tile.  list_capacity: entries
+ * staged in shared memory per batch (32..2048, multiple of 32; raised to the
+ * tile's thread count if smaller).  alpha_max (0.99), alpha_min (1/255),
+ * T_min (1e-4), near_plane (0.2) and dilation (0.3 px^2) are the compositing
  * constants of 3D Gaussian splatting, which the paper uses unchanged
- * (Sec. 3.1). */
+ * (Sec. 3.1).  Tile shape, bin size and capacity change performance only,
+ * never a bit of the result. */
 typedef struct gsc_raster_cfg {
     int32_t tile_w, tile_h;
     int32_t list_capacity;
     float alpha_max, alpha_min, T_min, near_plane, dilation;
+    int32_t bin_size;
 } gsc_raster_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -205,9 +210,10 @@ gsc_status gsc_workspace_counters(gsc_workspace* ws, gsc_stream_t stream, int64_
 
 /* Render the N Gaussians of one cache level into image (3 x H x W, written):
  * project each Gaussian (EWA covariance J W Sigma W^T J^T + dilation), bin it
- * into every screen tile its alpha >= alpha_min support can touch, sort the
- * (tile, Gaussian) pairs by (tile, view depth, index), and composite front to
- * back per pixel with early transmittance cut-off:
+ * into every coarse bin its alpha >= alpha_min support can touch, sort the
+ * (bin, Gaussian) pairs by (bin, view depth, index), let every tile keep the
+ * entries of its bin that reach it, and composite front to back per pixel
+ * with early transmittance cut-off:
  *   alpha = min(alpha_max, sigmoid(o) exp(-d^T conic d / 2)), terms with
  *   alpha < alpha_min skipped, stop before a term whose T (1 - alpha) < T_min,
  *   C = sum max(c, 0) alpha T, background 0.

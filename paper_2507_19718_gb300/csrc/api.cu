@@ -124,6 +124,10 @@ gsc_status check_cfg(const gsc_raster_cfg* c) {
         return fail(GSC_ERR_INVALID_ARG, "unsupported tile %dx%d", c->tile_w, c->tile_h);
     if (c->list_capacity < 32 || c->list_capacity > 2048 || c->list_capacity % 32)
         return fail(GSC_ERR_INVALID_ARG, "list_capacity %d not a multiple of 32 in [32, 2048]", c->list_capacity);
+    if (c->bin_size != 0 && (c->bin_size < 32 || c->bin_size > 512 || c->bin_size % c->tile_w ||
+                             c->bin_size % c->tile_h))
+        return fail(GSC_ERR_INVALID_ARG, "bin_size %d must be 0 or a multiple of the tile in [32, 512]",
+                    c->bin_size);
     if (!(c->alpha_max > 0.f && c->alpha_max < 1.f) || !(c->alpha_min > 0.f && c->alpha_min < c->alpha_max) ||
         !(c->T_min > 0.f && c->T_min < 1.f) || !(c->near_plane > 0.f) || !(c->dilation >= 0.f))
         return fail(GSC_ERR_INVALID_ARG, "compositing constants out of range");
@@ -155,7 +159,13 @@ RasterDev raster_dev(const gsc_raster_cfg* c, const gsc_camera* cam) {
     r.tile_w = c->tile_w; r.tile_h = c->tile_h;
     r.tiles_x = (cam->width + c->tile_w - 1) / c->tile_w;
     r.tiles_y = (cam->height + c->tile_h - 1) / c->tile_h;
-    r.cap = c->list_capacity;
+    int nt = c->tile_w * c->tile_h;
+    r.cap = c->list_capacity < nt ? nt : c->list_capacity;
+    r.bin = c->bin_size ? c->bin_size : 64;
+    r.bins_x = (cam->width + r.bin - 1) / r.bin;
+    r.bins_y = (cam->height + r.bin - 1) / r.bin;
+    r.spt_x = r.bin / c->tile_w;
+    r.spt_y = r.bin / c->tile_h;
     return r;
 }
 

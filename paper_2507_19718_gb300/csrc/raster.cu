@@ -2,8 +2,9 @@
 // (Sec. 3.1 / 3.5 of GSCache, which renders each level with the 3D Gaussian
 // splatting rasterizer at SH degree 0, Sec. 3.6).
 //
-// Forward:  k_project  -> depth radix sort -> scan of tile counts -> k_emit
-//           -> stable radix sort of the pairs by tile -> k_ranges -> k_render
+// Forward:  k_project  -> depth radix sort -> scan of bin counts -> k_emit
+//           -> stable radix sort of the (bin, Gaussian) pairs by bin
+//           -> k_ranges -> k_render (each tile filters its bin's list)
 // Backward: the same binning (no per-pixel state is kept from the forward),
 //           k_render_bwd (forward re-walk for the final T and the last
 //           composited entry, then back to front), k_project_bwd.
@@ -151,7 +152,9 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ para
     uint32_t tx0 = ilo / rc.tile_w, tx1 = ihi / rc.tile_w + 1;
     uint32_t ty0 = jlo / rc.tile_h, ty1 = jhi / rc.tile_h + 1;
     rect[g] = make_uint2(tx0 | (tx1 << 16), ty0 | (ty1 << 16));
-    cnt[g] = (tx1 - tx0) * (ty1 - ty0);
+    uint32_t bx0 = ilo / rc.bin, bx1 = ihi / rc.bin + 1;
+    uint32_t by0 = jlo / rc.bin, by1 = jhi / rc.bin + 1;
+    cnt[g] = (bx1 - bx0) * (by1 - by0);
     key[g] = __float_as_uint(x.t[2]);
     float h = -0.5f * kLog2e;
     rec[3 * (size_t)g] = make_float4(mx, my, h * x.a, -kLog2e * x.b);
@@ -159,11 +162,12 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ para
     rec[3 * (size_t)g + 2] = make_float4(fmaxf(p3.x, 0.f), fmaxf(p3.y, 0.f), fmaxf(p3.z, 0.f), 0.f);
 }
 
-// one warp writes the pairs of 32 consecutive depth-ordered Gaussians, one
-// Gaussian at a time, so that every store instruction is contiguous
+// one warp writes the (bin, Gaussian) pairs of 32 consecutive depth-ordered
+// Gaussians, one Gaussian at a time, so that every store instruction is
+// contiguous; the bin rectangle follows from the tile rectangle
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ off,
                                               const uint32_t* __restrict__ cnt, const uint2* __restrict__ rect,
-                                              uint32_t N, int tiles_x, const uint32_t* __restrict__ counters,
+                                              uint32_t N, RasterDev rc, const uint32_t* __restrict__ counters,
                                               uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval) {
     uint32_t total = counters[kCntPairs];
     uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -171,24 +175,26 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ sidx,
     uint32_t i = wid * 32 + lane;
     if (wid * 32 >= N) return;
     uint32_t g = 0, c = 0, o = 0;
-    uint2 rc = make_uint2(0, 0);
+    uint2 rr = make_uint2(0, 0);
     if (i < N) {
         g = sidx[i];
         c = cnt[g];
         o = off[i];
-        if (c) rc = rect[g];
+        if (c) rr = rect[g];
     }
     for (int j = 0; j < 32; ++j) {
         uint32_t cj = __shfl_sync(kFull, c, j);
         uint32_t oj = __shfl_sync(kFull, o, j);
         uint32_t gj = __shfl_sync(kFull, g, j);
-        uint32_t rx = __shfl_sync(kFull, rc.x, j);
-        uint32_t ry = __shfl_sync(kFull, rc.y, j);
+        uint32_t rx = __shfl_sync(kFull, rr.x, j);
+        uint32_t ry = __shfl_sync(kFull, rr.y, j);
         if (cj == 0 || (uint64_t)oj + cj > total) continue;
-        uint32_t tx0 = rx & 0xffffu, wx = (rx >> 16) - tx0, ty0 = ry & 0xffffu;
+        uint32_t bx0 = (rx & 0xffffu) / rc.spt_x, bx1 = ((rx >> 16) - 1) / rc.spt_x + 1;
+        uint32_t by0 = (ry & 0xffffu) / rc.spt_y;
+        uint32_t wx = bx1 - bx0;
         for (uint32_t k = lane; k < cj; k += 32) {
             uint32_t ky = k / wx, kx = k - ky * wx;
-            pkey[oj + k] = (ty0 + ky) * (uint32_t)tiles_x + tx0 + kx;
+            pkey[oj + k] = (by0 + ky) * (uint32_t)rc.bins_x + bx0 + kx;
             pval[oj + k] = gj;
         }
     }
@@ -204,7 +210,39 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* __re
     }
 }
 
-// one 64-bit atomic per warp
+
+__device__ __forceinline__ unsigned lanemask_lt32() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Block-wide stream compaction: rank of this thread among the threads whose
+// flag is set (in thread order) and their total.  Two barriers.
+template <int NT>
+__device__ __forceinline__ int block_rank(bool flag, int* s_warp, int& total) {
+    unsigned b = __ballot_sync(kFull, flag);
+    int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) s_warp[w] = __popc(b);
+    __syncthreads();
+    int off = 0, tot = 0;
+#pragma unroll
+    for (int k = 0; k < NT / 32; ++k) {
+        int c = s_warp[k];
+        off += k < w ? c : 0;
+        tot += c;
+    }
+    __syncthreads();
+    total = tot;
+    return off + __popc(b & lanemask_lt32());
+}
+
+__device__ __forceinline__ bool tile_in(uint2 r, int tx, int ty) {
+    return tx >= (int)(r.x & 0xffffu) && tx < (int)(r.x >> 16) && ty >= (int)(r.y & 0xffffu) &&
+           ty < (int)(r.y >> 16);
+}
+
+// one warp of the block counts its pixels' evaluated pairs with one atomic
 __device__ __forceinline__ void warp_count(unsigned long long* dst, uint32_t v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
@@ -212,38 +250,59 @@ __device__ __forceinline__ void warp_count(unsigned long long* dst, uint32_t v) 
 }
 
 // ------------------------------------------------------------------ forward
-
+//
+// One CTA per tile, one thread per pixel.  The tile walks the depth-ordered
+// list of its bin in rounds: the CTA tests NT candidates at a time against
+// the tile (tile rectangle of the Gaussian), compacts the hits in list order
+// into shared memory (their 48-B records) until `cap` are staged, then every
+// pixel composites the staged entries.  The CTA stops when all its pixels
+// have reached T_min.
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW* TH) k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
-                                                   const float4* __restrict__ rec, CamDev cam, RasterDev rc,
-                                                   float* __restrict__ image, unsigned long long* __restrict__ stats) {
+                                                   const uint2* __restrict__ rect, const float4* __restrict__ rec,
+                                                   CamDev cam, RasterDev rc, float* __restrict__ image,
+                                                   unsigned long long* __restrict__ stats) {
+    constexpr int NT = TW * TH;
     extern __shared__ float4 smem[];
+    __shared__ int s_warp[NT / 32];
     const int cap = rc.cap;
     float4* s0 = smem;
     float4* s1 = smem + cap;
     float4* s2 = smem + 2 * cap;
-    constexpr int NT = TW * TH;
     int tile = blockIdx.x;
     int tx = tile % rc.tiles_x, ty = tile / rc.tiles_x;
     int px = tx * TW + (threadIdx.x % TW), py = ty * TH + (threadIdx.x / TW);
     bool inside = px < cam.W && py < cam.H;
     float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
-    uint2 rg = ranges[tile];
+    uint2 rg = ranges[(ty / rc.spt_y) * rc.bins_x + tx / rc.spt_x];
     float T = 1.f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
     uint32_t n_eval = 0, n_comp = 0;
     bool done = !inside;
-    for (uint32_t base = rg.x; base < rg.y; base += cap) {
-        if (__syncthreads_count(done) == NT) break;
-        int n = (int)min((uint32_t)cap, rg.y - base);
-        for (int k = threadIdx.x; k < n; k += NT) {
-            uint32_t g = vals[base + k];
-            s0[k] = rec[3 * (size_t)g];
-            s1[k] = rec[3 * (size_t)g + 1];
-            s2[k] = rec[3 * (size_t)g + 2];
+    uint32_t pos = rg.x;
+    for (;;) {
+        if (__syncthreads_count(done) == NT || pos >= rg.y) break;
+        int staged = 0;
+        while (pos < rg.y && staged + NT <= cap) {
+            uint32_t c = pos + threadIdx.x;
+            uint32_t g = 0;
+            bool hit = false;
+            if (c < rg.y) {
+                g = vals[c];
+                hit = tile_in(rect[g], tx, ty);
+            }
+            int tot;
+            int r = block_rank<NT>(hit, s_warp, tot);
+            if (hit) {
+                s0[staged + r] = rec[3 * (size_t)g];
+                s1[staged + r] = rec[3 * (size_t)g + 1];
+                s2[staged + r] = rec[3 * (size_t)g + 2];
+            }
+            staged += tot;
+            pos += NT;
         }
         __syncthreads();
         if (!done) {
-            for (int k = 0; k < n; ++k) {
+            for (int k = 0; k < staged; ++k) {
                 float4 r0 = s0[k];
                 float4 r1 = s1[k];
                 float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy, r0.y);
@@ -265,7 +324,6 @@ __global__ void __launch_bounds__(TW* TH) k_render(const uint2* __restrict__ ran
                 T = Tn;
             }
         }
-        __syncthreads();
     }
     warp_count(&stats[kStEvalFwd], n_eval);
     warp_count(&stats[kStCompFwd], n_comp);
@@ -285,20 +343,29 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Phase 1 re-walks the bin list front to back with the forward's decisions
+// to find each pixel's final T and the list position after its last
+// composited entry.  Phase 2 walks the list back to front from the tile's
+// largest such position, staging hits top-down so that they are processed
+// in reverse list order; per entry the nine 2D gradient terms are summed
+// over the warp and added with three float4 atomics.
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW* TH) k_render_bwd(const uint2* __restrict__ ranges,
                                                        const uint32_t* __restrict__ vals,
+                                                       const uint2* __restrict__ rect,
                                                        const float4* __restrict__ rec, CamDev cam, RasterDev rc,
                                                        const float* __restrict__ dL_dimg, float4* __restrict__ g2d,
                                                        unsigned long long* __restrict__ stats) {
+    constexpr int NT = TW * TH;
     extern __shared__ float4 smem[];
+    __shared__ int s_warp[NT / 32];
+    __shared__ uint32_t s_end;
     const int cap = rc.cap;
     float4* s0 = smem;
     float4* s1 = smem + cap;
     float4* s2 = smem + 2 * cap;
     uint32_t* sid = reinterpret_cast<uint32_t*>(smem + 3 * cap);
-    __shared__ uint32_t s_end;
-    constexpr int NT = TW * TH;
+    uint32_t* spos = sid + cap;
     int tile = blockIdx.x;
     int tx = tile % rc.tiles_x, ty = tile / rc.tiles_x;
     int px = tx * TW + (threadIdx.x % TW), py = ty * TH + (threadIdx.x / TW);
@@ -312,24 +379,38 @@ __global__ void __launch_bounds__(TW* TH) k_render_bwd(const uint2* __restrict__
         gb = dL_dimg[2 * HW + pix];
     }
     bool active = inside && (gr != 0.f || gg != 0.f || gb != 0.f);
-    uint2 rg = ranges[tile];
+    uint2 rg = ranges[(ty / rc.spt_y) * rc.bins_x + tx / rc.spt_x];
 
-    // phase 1: forward re-walk, the same decisions as k_render
+    // phase 1
     float T = 1.f;
     uint32_t last = rg.x;
     uint32_t n_eval1 = 0, n_eval2 = 0;
     bool done = !active;
-    for (uint32_t base = rg.x; base < rg.y; base += cap) {
-        if (__syncthreads_count(done) == NT) break;
-        int n = (int)min((uint32_t)cap, rg.y - base);
-        for (int k = threadIdx.x; k < n; k += NT) {
-            uint32_t g = vals[base + k];
-            s0[k] = rec[3 * (size_t)g];
-            s1[k] = rec[3 * (size_t)g + 1];
+    uint32_t pos = rg.x;
+    for (;;) {
+        if (__syncthreads_count(done) == NT || pos >= rg.y) break;
+        int staged = 0;
+        while (pos < rg.y && staged + NT <= cap) {
+            uint32_t c = pos + threadIdx.x;
+            uint32_t g = 0;
+            bool hit = false;
+            if (c < rg.y) {
+                g = vals[c];
+                hit = tile_in(rect[g], tx, ty);
+            }
+            int tot;
+            int r = block_rank<NT>(hit, s_warp, tot);
+            if (hit) {
+                s0[staged + r] = rec[3 * (size_t)g];
+                s1[staged + r] = rec[3 * (size_t)g + 1];
+                spos[staged + r] = c;
+            }
+            staged += tot;
+            pos += NT;
         }
         __syncthreads();
         if (!done) {
-            for (int k = 0; k < n; ++k) {
+            for (int k = 0; k < staged; ++k) {
                 float4 r0 = s0[k];
                 float4 r1 = s1[k];
                 float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy, r0.y);
@@ -343,38 +424,51 @@ __global__ void __launch_bounds__(TW* TH) k_render_bwd(const uint2* __restrict__
                     break;
                 }
                 T = Tn;
-                last = base + k + 1;
+                last = spos[k] + 1;
             }
         }
-        __syncthreads();
     }
     if (threadIdx.x == 0) s_end = rg.x;
     __syncthreads();
     if (active) atomicMax(&s_end, last);
     __syncthreads();
     uint32_t end = s_end;
-    // per-warp bound: entries past every lane's last need no work
     uint32_t wlast = active ? last : rg.x;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(kFull, wlast, o));
 
-    // phase 2: back to front
+    // phase 2
     float Sr = 0.f, Sg = 0.f, Sb = 0.f;
     int lane = threadIdx.x & 31;
-    for (uint32_t hi = end; hi > rg.x;) {
-        uint32_t lo = hi - rg.x > (uint32_t)cap ? hi - cap : rg.x;
-        int n = (int)(hi - lo);
+    pos = end;
+    while (pos > rg.x) {
+        int staged = 0;
         __syncthreads();
-        for (int k = threadIdx.x; k < n; k += NT) {
-            uint32_t g = vals[lo + k];
-            sid[k] = g;
-            s0[k] = rec[3 * (size_t)g];
-            s1[k] = rec[3 * (size_t)g + 1];
-            s2[k] = rec[3 * (size_t)g + 2];
+        while (pos > rg.x && staged + NT <= cap) {
+            uint32_t lo = pos - rg.x > (uint32_t)NT ? pos - NT : rg.x;
+            uint32_t c = lo + threadIdx.x;
+            uint32_t g = 0;
+            bool hit = false;
+            if (c < pos) {
+                g = vals[c];
+                hit = tile_in(rect[g], tx, ty);
+            }
+            int tot;
+            int r = block_rank<NT>(hit, s_warp, tot);
+            if (hit) {
+                int sl = cap - staged - tot + r;
+                s0[sl] = rec[3 * (size_t)g];
+                s1[sl] = rec[3 * (size_t)g + 1];
+                s2[sl] = rec[3 * (size_t)g + 2];
+                sid[sl] = g;
+                spos[sl] = c;
+            }
+            staged += tot;
+            pos = lo;
         }
         __syncthreads();
-        for (int k = n - 1; k >= 0; --k) {
-            uint32_t j = lo + k;
+        for (int k = cap - 1; k >= cap - staged; --k) {
+            uint32_t j = spos[k];
             if (j >= wlast) continue;  // warp-uniform
             float4 r0 = s0[k];
             float4 r1 = s1[k];
@@ -430,7 +524,6 @@ __global__ void __launch_bounds__(TW* TH) k_render_bwd(const uint2* __restrict__
                 }
             }
         }
-        hi = lo;
     }
     warp_count(&stats[kStEvalRewalk], n_eval1);
     warp_count(&stats[kStEvalBack], n_eval2);
@@ -567,10 +660,9 @@ cudaError_t bin_gaussians(const float* params, int64_t N, const CamDev& cam, con
     if (eblk == 0) eblk = 1;
     {
         PhaseScope ph(kPhEmit, s, 1);
-        k_emit<<<eblk, 256, 0, s>>>(sidx, ws->off, ws->cnt, ws->rect, n, rc.tiles_x, ws->counters, ws->pkey0,
-                                    ws->pval0);
+        k_emit<<<eblk, 256, 0, s>>>(sidx, ws->off, ws->cnt, ws->rect, n, rc, ws->counters, ws->pkey0, ws->pval0);
     }
-    uint32_t tiles = (uint32_t)rc.tiles_x * rc.tiles_y;
+    uint32_t tiles = (uint32_t)rc.bins_x * rc.bins_y;
     int bits = bits_for(tiles);
     int p;
     {
@@ -588,23 +680,38 @@ cudaError_t bin_gaussians(const float* params, int64_t N, const CamDev& cam, con
     return cudaGetLastError();
 }
 
+// Raise a kernel's dynamic shared-memory limit when a launch needs more than
+// the default (which also has to hold the kernel's static shared memory).
+template <typename K>
+static cudaError_t ensure_smem(K kern, size_t bytes, int* cached) {
+    if ((int)bytes <= *cached) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) *cached = (int)bytes;
+    return e;
+}
+
 template <int TW, int TH>
 static cudaError_t render_t(const CamDev& cam, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
                             float* image, cudaStream_t s) {
     size_t smem = sizeof(float4) * 3 * rc.cap;
     auto kern = k_render<TW, TH>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<rc.tiles_x * rc.tiles_y, TW * TH, smem, s>>>(ws->ranges, vals, ws->rec, cam, rc, image, ws->stats);
+    static int cached = 32 * 1024;
+    cudaError_t e = ensure_smem(kern, smem, &cached);
+    if (e != cudaSuccess) return e;
+    kern<<<rc.tiles_x * rc.tiles_y, TW * TH, smem, s>>>(ws->ranges, vals, ws->rect, ws->rec, cam, rc, image,
+                                                         ws->stats);
     return cudaGetLastError();
 }
 
 template <int TW, int TH>
 static cudaError_t render_bwd_t(const CamDev& cam, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
                                 const float* dL, cudaStream_t s) {
-    size_t smem = (sizeof(float4) * 3 + sizeof(uint32_t)) * rc.cap;
+    size_t smem = (sizeof(float4) * 3 + 2 * sizeof(uint32_t)) * rc.cap;
     auto kern = k_render_bwd<TW, TH>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<rc.tiles_x * rc.tiles_y, TW * TH, smem, s>>>(ws->ranges, vals, ws->rec, cam, rc, dL, ws->g2d,
+    static int cached = 32 * 1024;
+    cudaError_t e = ensure_smem(kern, smem, &cached);
+    if (e != cudaSuccess) return e;
+    kern<<<rc.tiles_x * rc.tiles_y, TW * TH, smem, s>>>(ws->ranges, vals, ws->rect, ws->rec, cam, rc, dL, ws->g2d,
                                                          ws->stats);
     return cudaGetLastError();
 }

@@ -36,7 +36,7 @@ class FrameLoop:
     def __init__(self, scene: synth.Scene, level_sizes, width: int, height: int, spp: int = 1,
                  max_bounces: int = 8, seed: int = synth.BASE_SEED, tile=(16, 16), list_capacity: int = 256,
                  max_pairs: int | None = None, weight_decay: float = 0.01, lr=None, device: str = "cuda",
-                 gaussian_seed: int | None = None, C_term: float = 0.0):
+                 gaussian_seed: int | None = None, C_term: float = 0.0, bin_size: int = 0):
         self.width, self.height = width, height
         self.spp, self.max_bounces, self.seed = spp, max_bounces, seed
         self.K = len(level_sizes)
@@ -47,12 +47,13 @@ class FrameLoop:
         nmax = max(level_sizes)
         if max_pairs is None:
             # log-normal scales (N(-3, 0.5)) make the large Gaussians dominate:
-            # about 370 tiles per Gaussian at 1080p with 16x16 tiles; keep
-            # headroom and scale with the pixel count and tile area
-            per = 640.0 * (width * height) / (1920 * 1080) * 256.0 / (tile[0] * tile[1])
+            # at 1080p a Gaussian's support spans ~300 px, i.e. ~33 bins of
+            # 64 px; keep headroom and scale with the pixel count and bin area
+            b = bin_size or 64
+            per = 96.0 * (width * height) / (1920 * 1080) * (64.0 / b) ** 2
             max_pairs = int(min((1 << 31) - 1, max(1 << 16, nmax * max(per, 4.0))))
         self.ws = gsc.Workspace(nmax, max_pairs, width, height, device)
-        self.cfg = gsc.raster_cfg(tile=tile, list_capacity=list_capacity)
+        self.cfg = gsc.raster_cfg(tile=tile, list_capacity=list_capacity, bin_size=bin_size)
         self.lr = np.asarray(gsc.PAPER_LR if lr is None else lr, np.float32)
         self.weight_decay = weight_decay
         f32 = dict(dtype=torch.float32, device=device)

@@ -62,10 +62,10 @@ def test_tile_and_capacity_do_not_change_bits(gpu, orc):
     p, cam = _scene0(angle=75.0)
     ws = _ws(gpu, len(p), 1 << 22, cam.width, cam.height)
     base = _render(gpu, p, cam, gpu.raster_cfg(tile=(16, 16), list_capacity=256), ws)
-    for tile, cap in [((8, 8), 64), ((32, 8), 2048), ((16, 8), 32), ((8, 16), 512), ((8, 32), 128),
-                      ((32, 4), 96)]:
-        other = _render(gpu, p, cam, gpu.raster_cfg(tile=tile, list_capacity=cap), ws)
-        np.testing.assert_array_equal(other, base, err_msg=str((tile, cap)))
+    for tile, cap, b in [((8, 8), 64, 32), ((32, 8), 2048, 64), ((16, 8), 32, 128), ((8, 16), 512, 256),
+                         ((8, 32), 128, 64), ((32, 4), 96, 32), ((16, 16), 1024, 512), ((16, 16), 256, 48)]:
+        other = _render(gpu, p, cam, gpu.raster_cfg(tile=tile, list_capacity=cap, bin_size=b), ws)
+        np.testing.assert_array_equal(other, base, err_msg=str((tile, cap, b)))
 
 
 def test_ragged_image_and_degenerate_gaussians(gpu, orc):
