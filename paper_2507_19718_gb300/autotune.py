@@ -1,0 +1,79 @@
+"""Autotuner of the rasterizer launch configuration.
+
+The tile shape, the coarse bin size and the shared-memory staging capacity
+never change a result bit (every pixel composites the same ordered list);
+they only change speed.  ``autotune`` times the render and its backward for
+each candidate through the C ABI (CUDA events on the launching stream) on the
+caller's actual levels and camera, and returns the fastest configuration.
+"""
+from __future__ import annotations
+
+import itertools
+from dataclasses import dataclass
+
+import torch
+
+from . import gsc
+
+TILES = ((16, 16), (8, 8), (32, 8), (16, 8), (8, 16))
+BINS = (32, 64, 128)
+CAPS = (256, 512, 1024)
+
+
+@dataclass
+class Trial:
+    tile: tuple
+    bin_size: int
+    list_capacity: int
+    ms: float
+
+    def cfg(self, **kw) -> gsc.RasterCfg:
+        return gsc.raster_cfg(tile=self.tile, list_capacity=self.list_capacity, bin_size=self.bin_size, **kw)
+
+
+def candidates(tiles=TILES, bins=BINS, caps=CAPS):
+    for t, b, c in itertools.product(tiles, bins, caps):
+        if b % t[0] or b % t[1] or c < t[0] * t[1]:
+            continue
+        yield t, b, c
+
+
+def time_config(levels, cam, ws: gsc.Workspace, tile, bin_size, cap, backward=True, reps=2, stream=None):
+    """Mean ms of rendering (and differentiating) every level once."""
+    c = cam if isinstance(cam, gsc.Camera) else gsc.camera(cam)
+    cfg = gsc.raster_cfg(tile=tile, list_capacity=cap, bin_size=bin_size)
+    dev = levels[0].device
+    img = torch.empty((3, c.height, c.width), dtype=torch.float32, device=dev)
+    dl = torch.full((3, c.height, c.width), 1e-3, dtype=torch.float32, device=dev)
+    grads = [torch.zeros_like(p) for p in levels]
+    s = torch.cuda.current_stream() if stream is None else stream
+
+    def once():
+        for p, g in zip(levels, grads):
+            gsc.cache_render(p, c, cfg, ws, image=img, stream=s)
+            if backward:
+                gsc.cache_backward(p, c, cfg, ws, dl, g, stream=s)
+
+    once()  # warm-up
+    ws.status(s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        once()
+    e1.record(s)
+    e1.synchronize()
+    ws.status(s)
+    return e0.elapsed_time(e1) / reps
+
+
+def autotune(levels, cam, ws: gsc.Workspace, backward=True, cands=None, reps=2, verbose=False):
+    """Fastest (tile, bin, capacity) for rendering (and differentiating) the
+    given levels from `cam`.  Returns (best Trial, all trials)."""
+    trials = []
+    for tile, b, cap in (cands if cands is not None else candidates()):
+        ms = time_config(levels, cam, ws, tile, b, cap, backward=backward, reps=reps)
+        trials.append(Trial(tile, b, cap, ms))
+        if verbose:
+            print(f"tile {tile[0]}x{tile[1]} bin {b} cap {cap}: {ms:.3f} ms", flush=True)
+    best = min(trials, key=lambda t: t.ms)
+    return best, trials

@@ -242,6 +242,39 @@ __device__ __forceinline__ bool tile_in(uint2 r, int tx, int ty) {
            ty < (int)(r.y >> 16);
 }
 
+// Largest log2-falloff p = qa dx^2 + qb dx dy + qc dy^2 (negative definite)
+// of a Gaussian over the rectangle [x0, x1] x [y0, y1] of pixel centres:
+// 0 if its mean lies inside, else the best of the four edges, each a 1-D
+// concave quadratic maximised at its clamped stationary point.
+__device__ __forceinline__ float edge_max(float qa, float qb, float qc, float fixed, float lo, float hi) {
+    // p(fixed, t) = qa fixed^2 + qb fixed t + qc t^2, maximum over t in [lo, hi]
+    float t = -qb * fixed / (2.f * qc);
+    t = fminf(fmaxf(t, lo), hi);
+    return qa * fixed * fixed + qb * fixed * t + qc * t * t;
+}
+
+__device__ __forceinline__ float rect_max_falloff(float4 r0, float qc, float x0, float x1, float y0, float y1) {
+    float ax = x0 - r0.x, bx = x1 - r0.x, ay = y0 - r0.y, by = y1 - r0.y;
+    if (ax <= 0.f && bx >= 0.f && ay <= 0.f && by >= 0.f) return 0.f;
+    float m = edge_max(r0.z, r0.w, qc, ax, ay, by);
+    m = fmaxf(m, edge_max(r0.z, r0.w, qc, bx, ay, by));
+    m = fmaxf(m, edge_max(qc, r0.w, r0.z, ay, ax, bx));
+    m = fmaxf(m, edge_max(qc, r0.w, r0.z, by, ax, bx));
+    return m;
+}
+
+// A bin entry is kept for a tile if its tile rectangle covers the tile and
+// its falloff can reach its alpha_min threshold at some pixel centre of the
+// tile.  The margin (in log2 units) keeps the test conservative against the
+// rounding of the per-pixel evaluation, so no composited pair is dropped.
+constexpr float kCullMargin = 4e-3f;
+__device__ __forceinline__ bool tile_hit(uint2 rect, float4 r0, float4 r1, int tx, int ty, int TW, int TH) {
+    if (!tile_in(rect, tx, ty)) return false;
+    float x0 = (float)(tx * TW) + 0.5f, y0 = (float)(ty * TH) + 0.5f;
+    float m = rect_max_falloff(r0, r1.x, x0, x0 + (float)(TW - 1), y0, y0 + (float)(TH - 1));
+    return m >= r1.z - kCullMargin * (1.f + fabsf(r1.z));
+}
+
 // one warp of the block counts its pixels' evaluated pairs with one atomic
 __device__ __forceinline__ void warp_count(unsigned long long* dst, uint32_t v) {
 #pragma unroll
@@ -286,15 +319,21 @@ __global__ void __launch_bounds__(TW* TH) k_render(const uint2* __restrict__ ran
             uint32_t c = pos + threadIdx.x;
             uint32_t g = 0;
             bool hit = false;
+            float4 a0, a1;
             if (c < rg.y) {
                 g = vals[c];
-                hit = tile_in(rect[g], tx, ty);
+                uint2 rr = rect[g];
+                if (tile_in(rr, tx, ty)) {
+                    a0 = rec[3 * (size_t)g];
+                    a1 = rec[3 * (size_t)g + 1];
+                    hit = tile_hit(rr, a0, a1, tx, ty, TW, TH);
+                }
             }
             int tot;
             int r = block_rank<NT>(hit, s_warp, tot);
             if (hit) {
-                s0[staged + r] = rec[3 * (size_t)g];
-                s1[staged + r] = rec[3 * (size_t)g + 1];
+                s0[staged + r] = a0;
+                s1[staged + r] = a1;
                 s2[staged + r] = rec[3 * (size_t)g + 2];
             }
             staged += tot;
@@ -341,6 +380,33 @@ __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
+}
+
+// Warp reduce-scatter of eight values: at each butterfly step a lane keeps
+// half of its values and adds the partner's copy of that half, so 4 + 2 + 1
+// shuffles leave lane l with the sum over its 8-lane group of value
+// (l >> 2) & 7, and two more finish the sum over all 32 lanes (9 shuffles
+// instead of 8 x 5).
+__device__ __forceinline__ float warp_reduce_scatter8(const float (&a)[8], int lane) {
+    float b[4], c[2];
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float send = h4 ? a[k] : a[k + 4];
+        float keep = h4 ? a[k + 4] : a[k];
+        b[k] = keep + __shfl_xor_sync(kFull, send, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        float send = h3 ? b[k] : b[k + 2];
+        float keep = h3 ? b[k + 2] : b[k];
+        c[k] = keep + __shfl_xor_sync(kFull, send, 8);
+    }
+    float send = h2 ? c[0] : c[1];
+    float d = (h2 ? c[1] : c[0]) + __shfl_xor_sync(kFull, send, 4);
+    d += __shfl_xor_sync(kFull, d, 2);
+    d += __shfl_xor_sync(kFull, d, 1);
+    return d;
 }
 
 // Phase 1 re-walks the bin list front to back with the forward's decisions
@@ -394,15 +460,21 @@ __global__ void __launch_bounds__(TW* TH) k_render_bwd(const uint2* __restrict__
             uint32_t c = pos + threadIdx.x;
             uint32_t g = 0;
             bool hit = false;
+            float4 a0, a1;
             if (c < rg.y) {
                 g = vals[c];
-                hit = tile_in(rect[g], tx, ty);
+                uint2 rr = rect[g];
+                if (tile_in(rr, tx, ty)) {
+                    a0 = rec[3 * (size_t)g];
+                    a1 = rec[3 * (size_t)g + 1];
+                    hit = tile_hit(rr, a0, a1, tx, ty, TW, TH);
+                }
             }
             int tot;
             int r = block_rank<NT>(hit, s_warp, tot);
             if (hit) {
-                s0[staged + r] = rec[3 * (size_t)g];
-                s1[staged + r] = rec[3 * (size_t)g + 1];
+                s0[staged + r] = a0;
+                s1[staged + r] = a1;
                 spos[staged + r] = c;
             }
             staged += tot;
@@ -449,16 +521,22 @@ __global__ void __launch_bounds__(TW* TH) k_render_bwd(const uint2* __restrict__
             uint32_t c = lo + threadIdx.x;
             uint32_t g = 0;
             bool hit = false;
+            float4 a0, a1;
             if (c < pos) {
                 g = vals[c];
-                hit = tile_in(rect[g], tx, ty);
+                uint2 rr = rect[g];
+                if (tile_in(rr, tx, ty)) {
+                    a0 = rec[3 * (size_t)g];
+                    a1 = rec[3 * (size_t)g + 1];
+                    hit = tile_hit(rr, a0, a1, tx, ty, TW, TH);
+                }
             }
             int tot;
             int r = block_rank<NT>(hit, s_warp, tot);
             if (hit) {
                 int sl = cap - staged - tot + r;
-                s0[sl] = rec[3 * (size_t)g];
-                s1[sl] = rec[3 * (size_t)g + 1];
+                s0[sl] = a0;
+                s1[sl] = a1;
                 s2[sl] = rec[3 * (size_t)g + 2];
                 sid[sl] = g;
                 spos[sl] = c;
@@ -507,21 +585,16 @@ __global__ void __launch_bounds__(TW* TH) k_render_bwd(const uint2* __restrict__
                 }
             }
             if (__any_sync(kFull, act)) {
-                dmx = warp_sum(dmx);
-                dmy = warp_sum(dmy);
-                dqa = warp_sum(dqa);
-                dqb = warp_sum(dqb);
-                dqc = warp_sum(dqc);
-                dlo = warp_sum(dlo);
-                dcr = warp_sum(dcr);
-                dcg = warp_sum(dcg);
-                dcb = warp_sum(dcb);
-                if (lane == 0) {
-                    uint32_t g = sid[k];
-                    atomicAdd(&g2d[3 * (size_t)g], make_float4(dmx, dmy, dqa, dqb));
-                    atomicAdd(&g2d[3 * (size_t)g + 1], make_float4(dqc, dlo, 0.f, 0.f));
-                    atomicAdd(&g2d[3 * (size_t)g + 2], make_float4(dcr, dcg, dcb, 0.f));
+                // values 0..7 -> floats 0..5, 8, 9 of the 12-float 2D gradient record
+                const float v8[8] = {dmx, dmy, dqa, dqb, dqc, dlo, dcr, dcg};
+                float tot = warp_reduce_scatter8(v8, lane);
+                float blue = warp_sum(dcb);
+                float* gg2 = reinterpret_cast<float*>(g2d + 3 * (size_t)sid[k]);
+                if ((lane & 3) == 0) {
+                    int v = lane >> 2;
+                    atomicAdd(gg2 + (v < 6 ? v : v + 2), tot);
                 }
+                if (lane == 1) atomicAdd(gg2 + 10, blue);
             }
         }
     }
