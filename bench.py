@@ -38,7 +38,7 @@ LEVELS = 3
 SPP, BOUNCES = 1, 8
 ORBIT_DEG_PER_FRAME = 0.5
 # candidates of the start-up autotuner (tile shape x bin size x staging capacity)
-TUNE_TILES, TUNE_BINS, TUNE_CAPS = ((16, 16), (32, 8), (16, 8)), (64, 128), (256, 512)
+TUNE_TILES, TUNE_BINS, TUNE_CAPS, TUNE_PPT = ((16, 16), (32, 8), (16, 8)), (64, 128), (256, 512), (1, 2)
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # FP32 FMA lanes: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (maximum SM clock)
@@ -48,13 +48,13 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 def workload_config(tuned=None):
     from paper_2507_19718_gb300 import synth
     sizes = synth.level_sizes(TOTAL_GAUSSIANS, LEVELS)
-    tile, cap, b = (tuned.tile, tuned.list_capacity, tuned.bin_size) if tuned else ((16, 16), 512, 128)
+    tile, cap, b, q = (tuned.tile, tuned.list_capacity, tuned.bin_size, tuned.ppt) if tuned else ((16, 16), 512, 128, 1)
     return {
         "workload": "1080p GSCache frame: trace 1spp/8 bounces -> 3 target buffers; 3 cache levels "
                     "(1M Gaussians) render + HDR loss + backward + AdamW",
         "width": WIDTH, "height": HEIGHT, "gaussians": TOTAL_GAUSSIANS, "levels": sizes, "spp": SPP,
         "max_bounces": BOUNCES, "volume": "256^3 fp32: 64 blobs + 4-octave fBm, 8-point TF",
-        "lights": "directional 3.0 + environment 0.3", "tile": list(tile), "list_capacity": cap, "bin": b,
+        "lights": "directional 3.0 + environment 0.3", "tile": list(tile), "list_capacity": cap, "bin": b, "pixels_per_thread": q,
         "autotuned": tuned is not None,
         "camera": f"orbit r=2.2, fov_y 45 deg, {ORBIT_DEG_PER_FRAME} deg/frame",
         "l2": "inputs larger than L2 (params+moments 256 MB, pair buffers GBs)", "parallelism": "replicas",
@@ -212,7 +212,7 @@ def run_ours(args, world, rank, local):
             for f in range(args.warmup + args.steps + 1)]
     # pick the launch configuration on this GPU (results do not depend on it)
     best, _ = autotune.autotune([L.params for L in loop.levels], cams[0], loop.ws,
-                                cands=list(autotune.candidates(TUNE_TILES, TUNE_BINS, TUNE_CAPS)), reps=1)
+                                cands=list(autotune.candidates(TUNE_TILES, TUNE_BINS, TUNE_CAPS, TUNE_PPT)), reps=1)
     loop.cfg = best.cfg()
     cfg = workload_config(best)
     stream = torch.cuda.current_stream()
@@ -372,7 +372,8 @@ def run_reference(args, world, rank):
         "metric": METRIC, "impl": "reference", "value": round(value, 1), "unit": "ms/frame", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value, 1), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(workload_config(), tile=None, list_capacity=None, bin=None, autotuned=False),
+        "config": dict(workload_config(), tile=None, list_capacity=None, bin=None, pixels_per_thread=None,
+                       autotuned=False),
         "cpu_baseline": {"value": round(value, 1), "unit": "ms/frame", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 1), "unit": "ms/frame", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -91,6 +91,7 @@ typedef struct gsc_raster_cfg {
     int32_t list_capacity;
     float alpha_max, alpha_min, T_min, near_plane, dilation;
     int32_t bin_size;
+    int32_t pixels_per_thread; /* 1 or 2 (0 = 1): pixels (x, y) and (x, y + tile_h/2) per thread */
 } gsc_raster_cfg;
 
 /* ------------------------------------------------------------------ */

@@ -18,6 +18,7 @@ from . import gsc
 TILES = ((16, 16), (8, 8), (32, 8), (16, 8), (8, 16))
 BINS = (32, 64, 128)
 CAPS = (256, 512, 1024)
+PPTS = (1, 2)
 
 
 @dataclass
@@ -25,23 +26,25 @@ class Trial:
     tile: tuple
     bin_size: int
     list_capacity: int
+    ppt: int
     ms: float
 
     def cfg(self, **kw) -> gsc.RasterCfg:
-        return gsc.raster_cfg(tile=self.tile, list_capacity=self.list_capacity, bin_size=self.bin_size, **kw)
+        return gsc.raster_cfg(tile=self.tile, list_capacity=self.list_capacity, bin_size=self.bin_size,
+                              pixels_per_thread=self.ppt, **kw)
 
 
-def candidates(tiles=TILES, bins=BINS, caps=CAPS):
-    for t, b, c in itertools.product(tiles, bins, caps):
-        if b % t[0] or b % t[1] or c < t[0] * t[1]:
+def candidates(tiles=TILES, bins=BINS, caps=CAPS, ppts=PPTS):
+    for t, b, c, q in itertools.product(tiles, bins, caps, ppts):
+        if b % t[0] or b % t[1] or c < t[0] * t[1] // q or (q == 2 and t[0] * t[1] < 128):
             continue
-        yield t, b, c
+        yield t, b, c, q
 
 
-def time_config(levels, cam, ws: gsc.Workspace, tile, bin_size, cap, backward=True, reps=2, stream=None):
+def time_config(levels, cam, ws: gsc.Workspace, tile, bin_size, cap, ppt=1, backward=True, reps=2, stream=None):
     """Mean ms of rendering (and differentiating) every level once."""
     c = cam if isinstance(cam, gsc.Camera) else gsc.camera(cam)
-    cfg = gsc.raster_cfg(tile=tile, list_capacity=cap, bin_size=bin_size)
+    cfg = gsc.raster_cfg(tile=tile, list_capacity=cap, bin_size=bin_size, pixels_per_thread=ppt)
     dev = levels[0].device
     img = torch.empty((3, c.height, c.width), dtype=torch.float32, device=dev)
     dl = torch.full((3, c.height, c.width), 1e-3, dtype=torch.float32, device=dev)
@@ -67,13 +70,13 @@ def time_config(levels, cam, ws: gsc.Workspace, tile, bin_size, cap, backward=Tr
 
 
 def autotune(levels, cam, ws: gsc.Workspace, backward=True, cands=None, reps=2, verbose=False):
-    """Fastest (tile, bin, capacity) for rendering (and differentiating) the
+    """Fastest (tile, bin, capacity, pixels per thread) for rendering (and differentiating) the
     given levels from `cam`.  Returns (best Trial, all trials)."""
     trials = []
-    for tile, b, cap in (cands if cands is not None else candidates()):
-        ms = time_config(levels, cam, ws, tile, b, cap, backward=backward, reps=reps)
-        trials.append(Trial(tile, b, cap, ms))
+    for tile, b, cap, q in (cands if cands is not None else candidates()):
+        ms = time_config(levels, cam, ws, tile, b, cap, q, backward=backward, reps=reps)
+        trials.append(Trial(tile, b, cap, q, ms))
         if verbose:
-            print(f"tile {tile[0]}x{tile[1]} bin {b} cap {cap}: {ms:.3f} ms", flush=True)
+            print(f"tile {tile[0]}x{tile[1]} bin {b} cap {cap} ppt {q}: {ms:.3f} ms", flush=True)
     best = min(trials, key=lambda t: t.ms)
     return best, trials

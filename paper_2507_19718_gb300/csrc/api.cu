@@ -124,6 +124,9 @@ gsc_status check_cfg(const gsc_raster_cfg* c) {
         return fail(GSC_ERR_INVALID_ARG, "unsupported tile %dx%d", c->tile_w, c->tile_h);
     if (c->list_capacity < 32 || c->list_capacity > 2048 || c->list_capacity % 32)
         return fail(GSC_ERR_INVALID_ARG, "list_capacity %d not a multiple of 32 in [32, 2048]", c->list_capacity);
+    if (c->pixels_per_thread < 0 || c->pixels_per_thread > 2 ||
+        (c->pixels_per_thread == 2 && c->tile_w * c->tile_h < 128))
+        return fail(GSC_ERR_INVALID_ARG, "pixels_per_thread must be 0, 1 or 2 (2 needs >= 128 pixels per tile)");
     if (c->bin_size != 0 && (c->bin_size < 32 || c->bin_size > 512 || c->bin_size % c->tile_w ||
                              c->bin_size % c->tile_h))
         return fail(GSC_ERR_INVALID_ARG, "bin_size %d must be 0 or a multiple of the tile in [32, 512]",
@@ -159,7 +162,8 @@ RasterDev raster_dev(const gsc_raster_cfg* c, const gsc_camera* cam) {
     r.tile_w = c->tile_w; r.tile_h = c->tile_h;
     r.tiles_x = (cam->width + c->tile_w - 1) / c->tile_w;
     r.tiles_y = (cam->height + c->tile_h - 1) / c->tile_h;
-    int nt = c->tile_w * c->tile_h;
+    r.ppt = c->pixels_per_thread == 2 ? 2 : 1;
+    int nt = c->tile_w * c->tile_h / r.ppt;
     r.cap = c->list_capacity < nt ? nt : c->list_capacity;
     r.bin = c->bin_size ? c->bin_size : 64;
     r.bins_x = (cam->width + r.bin - 1) / r.bin;

@@ -33,6 +33,7 @@ struct RasterDev {
     float alpha_max, alpha_min, T_min, near_plane, dilation;
     int tile_w, tile_h, tiles_x, tiles_y, cap;
     int bin, bins_x, bins_y, spt_x, spt_y;  // bin size (px), bin grid, tiles per bin side
+    int ppt;                                // pixels per thread (1 or 2)
 };
 
 // sets the calling thread's last error message (api.cu) and returns st

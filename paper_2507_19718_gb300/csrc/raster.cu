@@ -284,18 +284,22 @@ __device__ __forceinline__ void warp_count(unsigned long long* dst, uint32_t v) 
 
 // ------------------------------------------------------------------ forward
 //
-// One CTA per tile, one thread per pixel.  The tile walks the depth-ordered
-// list of its bin in rounds: the CTA tests NT candidates at a time against
-// the tile (tile rectangle of the Gaussian), compacts the hits in list order
+// One CTA per tile; each thread owns PPT pixels of a column, (x, y) and
+// (x, y + TH/PPT).  The tile walks the depth-ordered list of its bin in
+// rounds: the CTA tests NT candidates at a time against the tile (tile
+// rectangle, then the exact ellipse bound), compacts the hits in list order
 // into shared memory (their 48-B records) until `cap` are staged, then every
 // pixel composites the staged entries.  The CTA stops when all its pixels
 // have reached T_min.
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW* TH) k_render(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
-                                                   const uint2* __restrict__ rect, const float4* __restrict__ rec,
-                                                   CamDev cam, RasterDev rc, float* __restrict__ image,
-                                                   unsigned long long* __restrict__ stats) {
-    constexpr int NT = TW * TH;
+template <int TW, int TH, int PPT>
+__global__ void __launch_bounds__(TW* TH / PPT) k_render(const uint2* __restrict__ ranges,
+                                                         const uint32_t* __restrict__ vals,
+                                                         const uint2* __restrict__ rect,
+                                                         const float4* __restrict__ rec, CamDev cam, RasterDev rc,
+                                                         float* __restrict__ image,
+                                                         unsigned long long* __restrict__ stats) {
+    constexpr int NT = TW * TH / PPT;
+    constexpr int ROWS = TH / PPT;
     extern __shared__ float4 smem[];
     __shared__ int s_warp[NT / 32];
     const int cap = rc.cap;
@@ -304,16 +308,27 @@ __global__ void __launch_bounds__(TW* TH) k_render(const uint2* __restrict__ ran
     float4* s2 = smem + 2 * cap;
     int tile = blockIdx.x;
     int tx = tile % rc.tiles_x, ty = tile / rc.tiles_x;
-    int px = tx * TW + (threadIdx.x % TW), py = ty * TH + (threadIdx.x / TW);
-    bool inside = px < cam.W && py < cam.H;
-    float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    int px = tx * TW + (threadIdx.x % TW), py0 = ty * TH + (threadIdx.x / TW);
+    float fx = (float)px + 0.5f;
+    float fy[PPT], T[PPT], Cr[PPT], Cg[PPT], Cb[PPT];
+    bool inside[PPT], done[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        int py = py0 + q * ROWS;
+        inside[q] = px < cam.W && py < cam.H;
+        fy[q] = (float)py + 0.5f;
+        T[q] = 1.f;
+        Cr[q] = Cg[q] = Cb[q] = 0.f;
+        done[q] = !inside[q];
+    }
     uint2 rg = ranges[(ty / rc.spt_y) * rc.bins_x + tx / rc.spt_x];
-    float T = 1.f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
     uint32_t n_eval = 0, n_comp = 0;
-    bool done = !inside;
     uint32_t pos = rg.x;
     for (;;) {
-        if (__syncthreads_count(done) == NT || pos >= rg.y) break;
+        bool tdone = true;
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) tdone = tdone && done[q];
+        if (__syncthreads_count(tdone) == NT || pos >= rg.y) break;
         int staged = 0;
         while (pos < rg.y && staged + NT <= cap) {
             uint32_t c = pos + threadIdx.x;
@@ -340,37 +355,56 @@ __global__ void __launch_bounds__(TW* TH) k_render(const uint2* __restrict__ ran
             pos += NT;
         }
         __syncthreads();
-        if (!done) {
+        if (!tdone) {
             for (int k = 0; k < staged; ++k) {
                 float4 r0 = s0[k];
                 float4 r1 = s1[k];
-                float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy, r0.y);
-                float p = falloff_log2(r0, r1.x, dx, dy);
-                ++n_eval;
-                if (p < r1.z) continue;
-                float alpha = fminf(rc.alpha_max, __fmul_rn(r1.y, ex2_approx(p)));
-                float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                if (Tn < rc.T_min) {
-                    done = true;
-                    break;
+                bool all = true;
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    if (done[q]) continue;
+                    float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy[q], r0.y);
+                    float p = falloff_log2(r0, r1.x, dx, dy);
+                    ++n_eval;
+                    if (p < r1.z) {
+                        all = false;
+                        continue;
+                    }
+                    float alpha = fminf(rc.alpha_max, __fmul_rn(r1.y, ex2_approx(p)));
+                    float Tn = __fmul_rn(T[q], __fsub_rn(1.f, alpha));
+                    if (Tn < rc.T_min) {
+                        done[q] = true;
+                        continue;
+                    }
+                    all = false;
+                    ++n_comp;
+                    float4 c = s2[k];
+                    float wgt = alpha * T[q];
+                    Cr[q] = fmaf(c.x, wgt, Cr[q]);
+                    Cg[q] = fmaf(c.y, wgt, Cg[q]);
+                    Cb[q] = fmaf(c.z, wgt, Cb[q]);
+                    T[q] = Tn;
                 }
-                ++n_comp;
-                float4 c = s2[k];
-                float wgt = alpha * T;
-                Cr = fmaf(c.x, wgt, Cr);
-                Cg = fmaf(c.y, wgt, Cg);
-                Cb = fmaf(c.z, wgt, Cb);
-                T = Tn;
+                if (all) {
+                    bool alld = true;
+#pragma unroll
+                    for (int q = 0; q < PPT; ++q) alld = alld && done[q];
+                    if (alld) break;
+                }
             }
         }
     }
     warp_count(&stats[kStEvalFwd], n_eval);
     warp_count(&stats[kStCompFwd], n_comp);
-    if (inside) {
-        size_t HW = (size_t)cam.W * cam.H, p = (size_t)py * cam.W + px;
-        image[p] = Cr;
-        image[HW + p] = Cg;
-        image[2 * HW + p] = Cb;
+    size_t HW = (size_t)cam.W * cam.H;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        if (inside[q]) {
+            size_t p = (size_t)(py0 + q * ROWS) * cam.W + px;
+            image[p] = Cr[q];
+            image[HW + p] = Cg[q];
+            image[2 * HW + p] = Cb[q];
+        }
     }
 }
 
@@ -409,53 +443,76 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float (&a)[8], int l
     return d;
 }
 
-// Phase 1 re-walks the bin list front to back with the forward's decisions
-// to find each pixel's final T and the list position after its last
-// composited entry.  Phase 2 walks the list back to front from the tile's
-// largest such position, staging hits top-down so that they are processed
-// in reverse list order; per entry the nine 2D gradient terms are summed
-// over the warp and added with three float4 atomics.
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW* TH) k_render_bwd(const uint2* __restrict__ ranges,
-                                                       const uint32_t* __restrict__ vals,
-                                                       const uint2* __restrict__ rect,
-                                                       const float4* __restrict__ rec, CamDev cam, RasterDev rc,
-                                                       const float* __restrict__ dL_dimg, float4* __restrict__ g2d,
-                                                       unsigned long long* __restrict__ stats) {
-    constexpr int NT = TW * TH;
+// Phase 1 re-walks the bin list front to back with the forward's decisions.
+// The entries that pass the tile filter ("hits") are numbered in list order;
+// their Gaussian ids go to a shared-memory ring of kHitRing slots, and the
+// list position of every kHitRing-th hit is recorded, so that phase 2 can
+// rebuild any chunk of hits without scanning from the start.  Each pixel
+// keeps its final T and the number of hits up to its last composited entry.
+// Phase 2 walks the hits back to front, chunk by chunk (the last chunk is
+// still in the ring; earlier ones are re-filtered from their recorded
+// position), stages their records, and per entry sums the nine 2D gradient
+// terms over the warp (reduce-scatter) before the global atomics.
+constexpr int kHitRing = 2048;
+constexpr int kMaxChunks = 512;
+
+template <int TW, int TH, int PPT>
+__global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const uint2* __restrict__ ranges,
+                                                             const uint32_t* __restrict__ vals,
+                                                             const uint2* __restrict__ rect,
+                                                             const float4* __restrict__ rec, CamDev cam, RasterDev rc,
+                                                             const float* __restrict__ dL_dimg,
+                                                             float4* __restrict__ g2d,
+                                                             unsigned long long* __restrict__ stats) {
+    constexpr int NT = TW * TH / PPT;
+    constexpr int ROWS = TH / PPT;
     extern __shared__ float4 smem[];
     __shared__ int s_warp[NT / 32];
     __shared__ uint32_t s_end;
+    __shared__ uint32_t s_chunk_pos[kMaxChunks];
     const int cap = rc.cap;
     float4* s0 = smem;
     float4* s1 = smem + cap;
     float4* s2 = smem + 2 * cap;
-    uint32_t* sid = reinterpret_cast<uint32_t*>(smem + 3 * cap);
-    uint32_t* spos = sid + cap;
+    uint32_t* hits = reinterpret_cast<uint32_t*>(smem + 3 * cap);
     int tile = blockIdx.x;
     int tx = tile % rc.tiles_x, ty = tile / rc.tiles_x;
-    int px = tx * TW + (threadIdx.x % TW), py = ty * TH + (threadIdx.x / TW);
-    bool inside = px < cam.W && py < cam.H;
-    float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
-    size_t HW = (size_t)cam.W * cam.H, pix = (size_t)py * cam.W + px;
-    float gr = 0.f, gg = 0.f, gb = 0.f;
-    if (inside) {
-        gr = dL_dimg[pix];
-        gg = dL_dimg[HW + pix];
-        gb = dL_dimg[2 * HW + pix];
+    int px = tx * TW + (threadIdx.x % TW), py0 = ty * TH + (threadIdx.x / TW);
+    float fx = (float)px + 0.5f;
+    size_t HW = (size_t)cam.W * cam.H;
+    float fy[PPT], gr[PPT], gg[PPT], gb[PPT], T[PPT];
+    bool active[PPT], done[PPT];
+    uint32_t last[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        int py = py0 + q * ROWS;
+        bool inside = px < cam.W && py < cam.H;
+        fy[q] = (float)py + 0.5f;
+        gr[q] = gg[q] = gb[q] = 0.f;
+        if (inside) {
+            size_t pix = (size_t)py * cam.W + px;
+            gr[q] = dL_dimg[pix];
+            gg[q] = dL_dimg[HW + pix];
+            gb[q] = dL_dimg[2 * HW + pix];
+        }
+        active[q] = inside && (gr[q] != 0.f || gg[q] != 0.f || gb[q] != 0.f);
+        done[q] = !active[q];
+        T[q] = 1.f;
+        last[q] = 0;
     }
-    bool active = inside && (gr != 0.f || gg != 0.f || gb != 0.f);
     uint2 rg = ranges[(ty / rc.spt_y) * rc.bins_x + tx / rc.spt_x];
 
-    // phase 1
-    float T = 1.f;
-    uint32_t last = rg.x;
+    // ---- phase 1
+    uint32_t nhit = 0;  // hits found so far (uniform)
     uint32_t n_eval1 = 0, n_eval2 = 0;
-    bool done = !active;
     uint32_t pos = rg.x;
     for (;;) {
-        if (__syncthreads_count(done) == NT || pos >= rg.y) break;
+        bool tdone = true;
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) tdone = tdone && done[q];
+        if (__syncthreads_count(tdone) == NT || pos >= rg.y) break;
         int staged = 0;
+        uint32_t h0 = nhit;
         while (pos < rg.y && staged + NT <= cap) {
             uint32_t c = pos + threadIdx.x;
             uint32_t g = 0;
@@ -475,127 +532,151 @@ __global__ void __launch_bounds__(TW* TH) k_render_bwd(const uint2* __restrict__
             if (hit) {
                 s0[staged + r] = a0;
                 s1[staged + r] = a1;
-                spos[staged + r] = c;
+                uint32_t hid = nhit + r;
+                hits[hid % kHitRing] = g;
+                if (hid % kHitRing == 0 && hid / kHitRing < kMaxChunks) s_chunk_pos[hid / kHitRing] = c;
             }
             staged += tot;
+            nhit += tot;
             pos += NT;
         }
         __syncthreads();
-        if (!done) {
+        if (!tdone) {
             for (int k = 0; k < staged; ++k) {
                 float4 r0 = s0[k];
                 float4 r1 = s1[k];
-                float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy, r0.y);
-                float p = falloff_log2(r0, r1.x, dx, dy);
-                ++n_eval1;
-                if (p < r1.z) continue;
-                float alpha = fminf(rc.alpha_max, __fmul_rn(r1.y, ex2_approx(p)));
-                float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                if (Tn < rc.T_min) {
-                    done = true;
-                    break;
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    if (done[q]) continue;
+                    float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy[q], r0.y);
+                    float p = falloff_log2(r0, r1.x, dx, dy);
+                    ++n_eval1;
+                    if (p < r1.z) continue;
+                    float alpha = fminf(rc.alpha_max, __fmul_rn(r1.y, ex2_approx(p)));
+                    float Tn = __fmul_rn(T[q], __fsub_rn(1.f, alpha));
+                    if (Tn < rc.T_min) {
+                        done[q] = true;
+                        continue;
+                    }
+                    T[q] = Tn;
+                    last[q] = h0 + k + 1;
                 }
-                T = Tn;
-                last = spos[k] + 1;
             }
         }
     }
-    if (threadIdx.x == 0) s_end = rg.x;
+    if (threadIdx.x == 0) s_end = 0;
     __syncthreads();
-    if (active) atomicMax(&s_end, last);
+    uint32_t mylast = 0;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q)
+        if (active[q]) mylast = max(mylast, last[q]);
+    if (mylast) atomicMax(&s_end, mylast);
     __syncthreads();
-    uint32_t end = s_end;
-    uint32_t wlast = active ? last : rg.x;
+    const uint32_t hend = s_end;
+    uint32_t wlast = mylast;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(kFull, wlast, o));
 
-    // phase 2
-    float Sr = 0.f, Sg = 0.f, Sb = 0.f;
+    // ---- phase 2
+    float Sr[PPT], Sg[PPT], Sb[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) Sr[q] = Sg[q] = Sb[q] = 0.f;
     int lane = threadIdx.x & 31;
-    pos = end;
-    while (pos > rg.x) {
-        int staged = 0;
-        __syncthreads();
-        while (pos > rg.x && staged + NT <= cap) {
-            uint32_t lo = pos - rg.x > (uint32_t)NT ? pos - NT : rg.x;
-            uint32_t c = lo + threadIdx.x;
-            uint32_t g = 0;
-            bool hit = false;
-            float4 a0, a1;
-            if (c < pos) {
-                g = vals[c];
-                uint2 rr = rect[g];
-                if (tile_in(rr, tx, ty)) {
-                    a0 = rec[3 * (size_t)g];
-                    a1 = rec[3 * (size_t)g + 1];
-                    hit = tile_hit(rr, a0, a1, tx, ty, TW, TH);
+    int ring_chunk = nhit ? (int)((nhit - 1) / kHitRing) : -1;  // chunk whose hits the ring holds
+    for (int ch = hend ? (int)((hend - 1) / kHitRing) : -1; ch >= 0; --ch) {
+        const uint32_t hc0 = (uint32_t)ch * kHitRing;
+        const uint32_t hc1 = min(hc0 + kHitRing, hend);
+        if (ch != ring_chunk) {
+            // rebuild hits [hc0, hc1) from the nearest recorded chunk start
+            int base_chunk = ch < kMaxChunks ? ch : kMaxChunks - 1;
+            uint32_t p = s_chunk_pos[base_chunk];
+            uint32_t h = (uint32_t)base_chunk * kHitRing;
+            __syncthreads();
+            while (h < hc1 && p < rg.y) {
+                uint32_t c = p + threadIdx.x;
+                uint32_t g = 0;
+                bool hit = false;
+                if (c < rg.y) {
+                    g = vals[c];
+                    uint2 rr = rect[g];
+                    if (tile_in(rr, tx, ty))
+                        hit = tile_hit(rr, rec[3 * (size_t)g], rec[3 * (size_t)g + 1], tx, ty, TW, TH);
                 }
+                int tot;
+                int r = block_rank<NT>(hit, s_warp, tot);
+                uint32_t hid = h + r;
+                if (hit && hid >= hc0 && hid < hc1) hits[hid % kHitRing] = g;
+                h += tot;
+                p += NT;
             }
-            int tot;
-            int r = block_rank<NT>(hit, s_warp, tot);
-            if (hit) {
-                int sl = cap - staged - tot + r;
-                s0[sl] = a0;
-                s1[sl] = a1;
-                s2[sl] = rec[3 * (size_t)g + 2];
-                sid[sl] = g;
-                spos[sl] = c;
-            }
-            staged += tot;
-            pos = lo;
+            ring_chunk = ch;
         }
-        __syncthreads();
-        for (int k = cap - 1; k >= cap - staged; --k) {
-            uint32_t j = spos[k];
-            if (j >= wlast) continue;  // warp-uniform
-            float4 r0 = s0[k];
-            float4 r1 = s1[k];
-            bool act = active && j < last;
-            float dmx = 0.f, dmy = 0.f, dqa = 0.f, dqb = 0.f, dqc = 0.f, dlo = 0.f, dcr = 0.f, dcg = 0.f, dcb = 0.f;
-            if (act) {
-                float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy, r0.y);
-                float p = falloff_log2(r0, r1.x, dx, dy);
-                ++n_eval2;
-                if (p >= r1.z) {
+        // back to front over the chunk, staged in batches of cap records
+        for (uint32_t b1 = hc1; b1 > hc0;) {
+            uint32_t b0 = b1 - hc0 > (uint32_t)cap ? b1 - cap : hc0;
+            int n = (int)(b1 - b0);
+            __syncthreads();
+            for (int i = threadIdx.x; i < n; i += NT) {
+                uint32_t g = hits[(b0 + i) % kHitRing];
+                s0[i] = rec[3 * (size_t)g];
+                s1[i] = rec[3 * (size_t)g + 1];
+                s2[i] = rec[3 * (size_t)g + 2];
+            }
+            __syncthreads();
+            for (int k = n - 1; k >= 0; --k) {
+                uint32_t j = b0 + k;
+                if (j >= wlast) continue;  // warp-uniform
+                float4 r0 = s0[k];
+                float4 r1 = s1[k];
+                float v8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float dcb = 0.f;
+                bool any = false;
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    if (!(active[q] && j < last[q])) continue;
+                    float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy[q], r0.y);
+                    float p = falloff_log2(r0, r1.x, dx, dy);
+                    ++n_eval2;
+                    if (p < r1.z) continue;
+                    any = true;
                     float e = ex2_approx(p);
                     float araw = __fmul_rn(r1.y, e);
                     float alpha = fminf(rc.alpha_max, araw);
                     float inv = 1.f / (1.f - alpha);
-                    T = T * inv;  // transmittance in front of this entry
+                    T[q] = T[q] * inv;  // transmittance in front of this entry
                     float4 c = s2[k];
-                    float wgt = alpha * T;
-                    dcr = wgt * gr;
-                    dcg = wgt * gg;
-                    dcb = wgt * gb;
-                    float dal = gr * (c.x * T - Sr * inv) + gg * (c.y * T - Sg * inv) + gb * (c.z * T - Sb * inv);
-                    Sr = fmaf(c.x, wgt, Sr);
-                    Sg = fmaf(c.y, wgt, Sg);
-                    Sb = fmaf(c.z, wgt, Sb);
+                    float wgt = alpha * T[q];
+                    v8[6] += wgt * gr[q];
+                    v8[7] += wgt * gg[q];
+                    dcb += wgt * gb[q];
+                    float dal = gr[q] * (c.x * T[q] - Sr[q] * inv) + gg[q] * (c.y * T[q] - Sg[q] * inv) +
+                                gb[q] * (c.z * T[q] - Sb[q] * inv);
+                    Sr[q] = fmaf(c.x, wgt, Sr[q]);
+                    Sg[q] = fmaf(c.y, wgt, Sg[q]);
+                    Sb[q] = fmaf(c.z, wgt, Sb[q]);
                     if (araw < rc.alpha_max) {
-                        dlo = dal * e * r1.y * (1.f - r1.y);
+                        v8[5] += dal * e * r1.y * (1.f - r1.y);
                         float dp = dal * alpha * kLn2;
-                        dqa = dp * dx * dx;
-                        dqb = dp * dx * dy;
-                        dqc = dp * dy * dy;
-                        dmx = -dp * (2.f * r0.z * dx + r0.w * dy);
-                        dmy = -dp * (r0.w * dx + 2.f * r1.x * dy);
+                        v8[2] += dp * dx * dx;
+                        v8[3] += dp * dx * dy;
+                        v8[4] += dp * dy * dy;
+                        v8[0] -= dp * (2.f * r0.z * dx + r0.w * dy);
+                        v8[1] -= dp * (r0.w * dx + 2.f * r1.x * dy);
                     }
-                } else {
-                    act = false;
+                }
+                if (__any_sync(kFull, any)) {
+                    // values 0..7 -> floats 0..5, 8, 9 of the 12-float 2D gradient record
+                    float tot = warp_reduce_scatter8(v8, lane);
+                    float blue = warp_sum(dcb);
+                    float* gg2 = reinterpret_cast<float*>(g2d + 3 * (size_t)hits[j % kHitRing]);
+                    if ((lane & 3) == 0) {
+                        int v = lane >> 2;
+                        atomicAdd(gg2 + (v < 6 ? v : v + 2), tot);
+                    }
+                    if (lane == 1) atomicAdd(gg2 + 10, blue);
                 }
             }
-            if (__any_sync(kFull, act)) {
-                // values 0..7 -> floats 0..5, 8, 9 of the 12-float 2D gradient record
-                const float v8[8] = {dmx, dmy, dqa, dqb, dqc, dlo, dcr, dcg};
-                float tot = warp_reduce_scatter8(v8, lane);
-                float blue = warp_sum(dcb);
-                float* gg2 = reinterpret_cast<float*>(g2d + 3 * (size_t)sid[k]);
-                if ((lane & 3) == 0) {
-                    int v = lane >> 2;
-                    atomicAdd(gg2 + (v < 6 ? v : v + 2), tot);
-                }
-                if (lane == 1) atomicAdd(gg2 + 10, blue);
-            }
+            b1 = b0;
         }
     }
     warp_count(&stats[kStEvalRewalk], n_eval1);
@@ -763,40 +844,48 @@ static cudaError_t ensure_smem(K kern, size_t bytes, int* cached) {
     return e;
 }
 
-template <int TW, int TH>
+template <int TW, int TH, int PPT>
 static cudaError_t render_t(const CamDev& cam, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
                             float* image, cudaStream_t s) {
     size_t smem = sizeof(float4) * 3 * rc.cap;
-    auto kern = k_render<TW, TH>;
+    auto kern = k_render<TW, TH, PPT>;
     static int cached = 32 * 1024;
     cudaError_t e = ensure_smem(kern, smem, &cached);
     if (e != cudaSuccess) return e;
-    kern<<<rc.tiles_x * rc.tiles_y, TW * TH, smem, s>>>(ws->ranges, vals, ws->rect, ws->rec, cam, rc, image,
-                                                         ws->stats);
+    kern<<<rc.tiles_x * rc.tiles_y, TW * TH / PPT, smem, s>>>(ws->ranges, vals, ws->rect, ws->rec, cam, rc, image,
+                                                               ws->stats);
     return cudaGetLastError();
 }
 
-template <int TW, int TH>
+template <int TW, int TH, int PPT>
 static cudaError_t render_bwd_t(const CamDev& cam, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
                                 const float* dL, cudaStream_t s) {
-    size_t smem = (sizeof(float4) * 3 + 2 * sizeof(uint32_t)) * rc.cap;
-    auto kern = k_render_bwd<TW, TH>;
+    size_t smem = sizeof(float4) * 3 * rc.cap + sizeof(uint32_t) * kHitRing;
+    auto kern = k_render_bwd<TW, TH, PPT>;
     static int cached = 32 * 1024;
     cudaError_t e = ensure_smem(kern, smem, &cached);
     if (e != cudaSuccess) return e;
-    kern<<<rc.tiles_x * rc.tiles_y, TW * TH, smem, s>>>(ws->ranges, vals, ws->rect, ws->rec, cam, rc, dL, ws->g2d,
-                                                         ws->stats);
+    kern<<<rc.tiles_x * rc.tiles_y, TW * TH / PPT, smem, s>>>(ws->ranges, vals, ws->rect, ws->rec, cam, rc, dL,
+                                                               ws->g2d, ws->stats);
     return cudaGetLastError();
 }
 
-#define GSC_TILE_DISPATCH(FN, ...)                                                   \
-    if (rc.tile_w == 16 && rc.tile_h == 16) return FN<16, 16>(__VA_ARGS__);          \
-    if (rc.tile_w == 8 && rc.tile_h == 8) return FN<8, 8>(__VA_ARGS__);              \
-    if (rc.tile_w == 32 && rc.tile_h == 8) return FN<32, 8>(__VA_ARGS__);            \
-    if (rc.tile_w == 16 && rc.tile_h == 8) return FN<16, 8>(__VA_ARGS__);            \
-    if (rc.tile_w == 8 && rc.tile_h == 16) return FN<8, 16>(__VA_ARGS__);            \
-    if (rc.tile_w == 8 && rc.tile_h == 32) return FN<8, 32>(__VA_ARGS__);            \
-    if (rc.tile_w == 32 && rc.tile_h == 4) return FN<32, 4>(__VA_ARGS__);            \
+#define GSC_TILE_DISPATCH(FN, ...)                                                            \
+    if (rc.ppt == 2) {                                                                        \
+        if (rc.tile_w == 16 && rc.tile_h == 16) return FN<16, 16, 2>(__VA_ARGS__);            \
+        if (rc.tile_w == 32 && rc.tile_h == 8) return FN<32, 8, 2>(__VA_ARGS__);              \
+        if (rc.tile_w == 16 && rc.tile_h == 8) return FN<16, 8, 2>(__VA_ARGS__);              \
+        if (rc.tile_w == 8 && rc.tile_h == 16) return FN<8, 16, 2>(__VA_ARGS__);              \
+        if (rc.tile_w == 8 && rc.tile_h == 32) return FN<8, 32, 2>(__VA_ARGS__);              \
+        return cudaErrorInvalidValue;                                                         \
+    }                                                                                         \
+    if (rc.tile_w == 16 && rc.tile_h == 16) return FN<16, 16, 1>(__VA_ARGS__);                \
+    if (rc.tile_w == 8 && rc.tile_h == 8) return FN<8, 8, 1>(__VA_ARGS__);                    \
+    if (rc.tile_w == 32 && rc.tile_h == 8) return FN<32, 8, 1>(__VA_ARGS__);                  \
+    if (rc.tile_w == 16 && rc.tile_h == 8) return FN<16, 8, 1>(__VA_ARGS__);                  \
+    if (rc.tile_w == 8 && rc.tile_h == 16) return FN<8, 16, 1>(__VA_ARGS__);                  \
+    if (rc.tile_w == 8 && rc.tile_h == 32) return FN<8, 32, 1>(__VA_ARGS__);                  \
+    if (rc.tile_w == 32 && rc.tile_h == 4) return FN<32, 4, 1>(__VA_ARGS__);                  \
     return cudaErrorInvalidValue;
 
 cudaError_t launch_render(const CamDev& cam, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,

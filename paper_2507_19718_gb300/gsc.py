@@ -36,7 +36,8 @@ class Camera(C.Structure):
 class RasterCfg(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("list_capacity", C.c_int32),
                 ("alpha_max", C.c_float), ("alpha_min", C.c_float), ("T_min", C.c_float),
-                ("near_plane", C.c_float), ("dilation", C.c_float), ("bin_size", C.c_int32)]
+                ("near_plane", C.c_float), ("dilation", C.c_float), ("bin_size", C.c_int32),
+                ("pixels_per_thread", C.c_int32)]
 
 
 class SceneDesc(C.Structure):
@@ -151,8 +152,10 @@ def camera(cam) -> Camera:
 
 
 def raster_cfg(tile=(16, 16), list_capacity: int = 256, alpha_max: float = 0.99, alpha_min: float = 1.0 / 255.0,
-               T_min: float = 1e-4, near: float = 0.2, dilation: float = 0.3, bin_size: int = 0) -> RasterCfg:
+               T_min: float = 1e-4, near: float = 0.2, dilation: float = 0.3, bin_size: int = 0,
+               pixels_per_thread: int = 1) -> RasterCfg:
     r = RasterCfg()
+    r.pixels_per_thread = int(pixels_per_thread)
     r.tile_w, r.tile_h = int(tile[0]), int(tile[1])
     r.list_capacity = int(list_capacity)
     r.bin_size = int(bin_size)

@@ -62,10 +62,13 @@ def test_tile_and_capacity_do_not_change_bits(gpu, orc):
     p, cam = _scene0(angle=75.0)
     ws = _ws(gpu, len(p), 1 << 22, cam.width, cam.height)
     base = _render(gpu, p, cam, gpu.raster_cfg(tile=(16, 16), list_capacity=256), ws)
-    for tile, cap, b in [((8, 8), 64, 32), ((32, 8), 2048, 64), ((16, 8), 32, 128), ((8, 16), 512, 256),
-                         ((8, 32), 128, 64), ((32, 4), 96, 32), ((16, 16), 1024, 512), ((16, 16), 256, 48)]:
-        other = _render(gpu, p, cam, gpu.raster_cfg(tile=tile, list_capacity=cap, bin_size=b), ws)
-        np.testing.assert_array_equal(other, base, err_msg=str((tile, cap, b)))
+    for tile, cap, b, ppt in [((8, 8), 64, 32, 1), ((32, 8), 2048, 64, 1), ((16, 8), 32, 128, 1),
+                              ((8, 16), 512, 256, 1), ((8, 32), 128, 64, 1), ((32, 4), 96, 32, 1),
+                              ((16, 16), 1024, 512, 1), ((16, 16), 256, 48, 1), ((16, 16), 128, 128, 2),
+                              ((32, 8), 512, 64, 2), ((16, 8), 64, 32, 2), ((8, 32), 256, 128, 2)]:
+        cfg = gpu.raster_cfg(tile=tile, list_capacity=cap, bin_size=b, pixels_per_thread=ppt)
+        other = _render(gpu, p, cam, cfg, ws)
+        np.testing.assert_array_equal(other, base, err_msg=str((tile, cap, b, ppt)))
 
 
 def test_ragged_image_and_degenerate_gaussians(gpu, orc):
@@ -126,8 +129,8 @@ def _grad_compare(g_gpu, g_ref, tol=1e-3):
         assert not bad.any(), (name, np.argwhere(bad)[:5], a[bad][:5], b[bad][:5])
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
-def test_backward_matches_oracle_config0(gpu, orc, tile):
+@pytest.mark.parametrize("tile,ppt", [((16, 16), 1), ((8, 8), 1), ((16, 16), 2), ((32, 8), 2)])
+def test_backward_matches_oracle_config0(gpu, orc, tile, ppt):
     torch = _torch()
     p, cam = _scene0(w=96, h=80)
     _, marg, _, _ = orc.render(p, cam, grad_margins=True)
@@ -136,7 +139,7 @@ def test_backward_matches_oracle_config0(gpu, orc, tile):
     dL = dL.astype(np.float32)
     ref, _ = orc.render_backward(p, cam, dL.astype(np.float64))
     ws = _ws(gpu, len(p), 1 << 21, cam.width, cam.height)
-    g = gpu.cache_backward(torch.from_numpy(p).cuda(), cam, gpu.raster_cfg(tile=tile), ws,
+    g = gpu.cache_backward(torch.from_numpy(p).cuda(), cam, gpu.raster_cfg(tile=tile, pixels_per_thread=ppt), ws,
                            torch.from_numpy(dL).cuda())
     ws.status()
     g = g.cpu().numpy().astype(np.float64)
