@@ -176,18 +176,19 @@ gsc_status gsc_trace(const gsc_scene* scene, const gsc_camera* cam, const gsc_tr
 
 typedef struct gsc_workspace gsc_workspace;
 
-/* Bytes of device memory a workspace needs for levels of up to
- * max_gaussians Gaussians, up to max_pairs (Gaussian, tile) pairs per
- * render, images up to max_w x max_h and tiles no smaller than those of cfg
- * (NULL = 8x8). */
+/* Bytes of device memory a workspace needs for renders of up to
+ * max_gaussians Gaussians (summed over the views of a batch), up to
+ * max_pairs (bin, Gaussian) pairs per binning, images up to max_w x max_h,
+ * and batches of up to max_views views (1..32).  cfg is unused (NULL). */
 gsc_status gsc_workspace_size(int64_t max_gaussians, int64_t max_pairs, int32_t max_w, int32_t max_h,
-                              const gsc_raster_cfg* cfg, size_t* bytes);
+                              int32_t max_views, const gsc_raster_cfg* cfg, size_t* bytes);
 
 /* Bind a workspace to the caller's device buffer (>= gsc_workspace_size
  * bytes, 256-byte aligned, owned by the caller and kept alive until
  * gsc_workspace_destroy).  Nothing is enqueued. */
 gsc_status gsc_workspace_create(void* device_buffer, size_t bytes, int64_t max_gaussians, int64_t max_pairs,
-                                int32_t max_w, int32_t max_h, const gsc_raster_cfg* cfg, gsc_workspace** out);
+                                int32_t max_w, int32_t max_h, int32_t max_views, const gsc_raster_cfg* cfg,
+                                gsc_workspace** out);
 
 gsc_status gsc_workspace_destroy(gsc_workspace* ws);
 
@@ -230,6 +231,33 @@ gsc_status gsc_cache_render(const float* params, int64_t N, const gsc_camera* ca
  * per-pixel transmittance, so no per-pixel forward state is kept. */
 gsc_status gsc_cache_backward(const float* params, int64_t N, const gsc_camera* cam, const gsc_raster_cfg* cfg,
                               gsc_workspace* ws, const float* dL_dimage, float* grads, gsc_stream_t stream);
+
+/* One view of a batched render: a cache level seen by a camera. */
+typedef struct gsc_view {
+    const float* params;     /* N x 16 packed records */
+    int64_t N;
+    gsc_camera cam;
+    float* image;            /* 3 x H x W, written by the forward */
+    const float* dL_dimage;  /* 3 x H x W, read by the backward */
+    float* grads;            /* N x 16, accumulated (+=) by the backward; views may share it */
+} gsc_view;
+
+#define GSC_BATCH_FWD 1
+#define GSC_BATCH_BWD 2
+
+/* Render (mode & GSC_BATCH_FWD) and/or differentiate (mode & GSC_BATCH_BWD)
+ * up to 32 views -- cache levels of several scenes, seen by cameras of
+ * different resolutions -- with one binning over all their Gaussians and ONE
+ * launch of persistent CTAs that take the tiles of all views from a shared
+ * counter (the forward; the backward is another such launch).  This is the
+ * paper's "joint rasterization" of several Gaussian sets (Sec. 5) as a batch.
+ * Every view's result equals gsc_cache_render / gsc_cache_backward of that
+ * view alone (bit for bit for the images; the gradients up to the order of
+ * floating-point atomics).  All views use one cfg; the workspace must be
+ * sized for the sum of the views' Gaussians and for n_views views.
+ * Graph-capturable: host arguments are read during the call only. */
+gsc_status gsc_render_batch(const gsc_view* views, int32_t n_views, int32_t mode, const gsc_raster_cfg* cfg,
+                            gsc_workspace* ws, gsc_stream_t stream);
 
 /* ------------------------------------------------------------------ */
 /* losses (Sec. 3.6) and the optimiser step (Sec. 3.6, Eq. 4)           */

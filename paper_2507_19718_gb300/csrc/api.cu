@@ -155,22 +155,47 @@ CamDev cam_dev(const gsc_camera* c) {
     return d;
 }
 
-RasterDev raster_dev(const gsc_raster_cfg* c, const gsc_camera* cam) {
+RasterDev raster_dev(const gsc_raster_cfg* c) {
     RasterDev r;
     r.alpha_max = c->alpha_max; r.alpha_min = c->alpha_min; r.T_min = c->T_min;
     r.near_plane = c->near_plane; r.dilation = c->dilation;
     r.tile_w = c->tile_w; r.tile_h = c->tile_h;
-    r.tiles_x = (cam->width + c->tile_w - 1) / c->tile_w;
-    r.tiles_y = (cam->height + c->tile_h - 1) / c->tile_h;
     r.ppt = c->pixels_per_thread == 2 ? 2 : 1;
     int nt = c->tile_w * c->tile_h / r.ppt;
     r.cap = c->list_capacity < nt ? nt : c->list_capacity;
     r.bin = c->bin_size ? c->bin_size : 64;
-    r.bins_x = (cam->width + r.bin - 1) / r.bin;
-    r.bins_y = (cam->height + r.bin - 1) / r.bin;
     r.spt_x = r.bin / c->tile_w;
     r.spt_y = r.bin / c->tile_h;
     return r;
+}
+
+// Append one view to a batch table (tiles and bins numbered after the
+// previous views').
+void add_view(BatchDev& b, const RasterDev& rc, const gsc_camera* cam, const float* params, int64_t N,
+              float* image, const float* dL, float* grads) {
+    ViewDev& v = b.v[b.nviews];
+    v.cam = cam_dev(cam);
+    v.params = reinterpret_cast<const float4*>(params);
+    v.image = image;
+    v.dL = dL;
+    v.grads = reinterpret_cast<float4*>(grads);
+    v.g_off = b.total_g;
+    v.N = (uint32_t)N;
+    v.tiles_x = (cam->width + rc.tile_w - 1) / rc.tile_w;
+    v.tiles_y = (cam->height + rc.tile_h - 1) / rc.tile_h;
+    v.bins_x = (cam->width + rc.bin - 1) / rc.bin;
+    v.bins_y = (cam->height + rc.bin - 1) / rc.bin;
+    v.tile_off = b.total_tiles;
+    v.bin_off = b.total_bins;
+    b.total_g += (uint32_t)N;
+    b.total_tiles += (uint32_t)(v.tiles_x * v.tiles_y);
+    b.total_bins += (uint32_t)(v.bins_x * v.bins_y);
+    b.nviews += 1;
+}
+
+void batch_init(BatchDev& b) {
+    b.nviews = 0;
+    b.total_g = b.total_tiles = b.total_bins = 0;
 }
 
 int64_t max_tiles_for(int32_t w, int32_t h) {
@@ -184,7 +209,7 @@ int64_t max_tiles_for(int32_t w, int32_t h) {
 }
 
 // Carve the workspace out of `base` (NULL: only measure).  Returns bytes used.
-size_t layout(int64_t NG, int64_t NP, int32_t W, int32_t H, gsc_workspace* ws, char* base) {
+size_t layout(int64_t NG, int64_t NP, int32_t W, int32_t H, int32_t NV, gsc_workspace* ws, char* base) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* {
         off = (off + 255) & ~(size_t)255;
@@ -192,9 +217,10 @@ size_t layout(int64_t NG, int64_t NP, int32_t W, int32_t H, gsc_workspace* ws, c
         off += bytes;
         return p;
     };
-    int64_t tiles = max_tiles_for(W, H);
+    int64_t tiles = max_tiles_for(W, H) * (NV > 0 ? NV : 1);  // bins of all views
     size_t ng = (size_t)(NG > 0 ? NG : 1), np = (size_t)(NP > 0 ? NP : 1);
-    size_t red = 65536;
+    // reduction partials, then three SSIM derivative maps of a full 3-channel image
+    size_t red = 65536 + 9 * (size_t)W * (size_t)H;
     gsc_workspace tmp;
     gsc_workspace* w = ws ? ws : &tmp;
     w->status = (int32_t*)take(sizeof(int32_t) * kStatusWords);
@@ -328,22 +354,23 @@ gsc_status gsc_trace(const gsc_scene* scene, const gsc_camera* cam, const gsc_tr
 // ------------------------------------------------------------------ workspaces
 
 gsc_status gsc_workspace_size(int64_t max_gaussians, int64_t max_pairs, int32_t max_w, int32_t max_h,
-                              const gsc_raster_cfg* cfg, size_t* bytes) {
+                              int32_t max_views, const gsc_raster_cfg* cfg, size_t* bytes) {
     (void)cfg;
     if (!bytes) return fail(GSC_ERR_INVALID_ARG, "bytes is NULL");
     if (max_gaussians < 0 || max_gaussians > (1ll << 31) - 1 || max_pairs < 0 || max_pairs > (1ll << 31) - 1 ||
-        max_w < 1 || max_h < 1 || max_w > 65535 || max_h > 65535)
+        max_w < 1 || max_h < 1 || max_w > 65535 || max_h > 65535 || max_views < 1 || max_views > kMaxViews)
         return fail(GSC_ERR_INVALID_ARG, "workspace limits out of range");
-    *bytes = layout(max_gaussians, max_pairs, max_w, max_h, nullptr, nullptr);
+    *bytes = layout(max_gaussians, max_pairs, max_w, max_h, max_views, nullptr, nullptr);
     return GSC_OK;
 }
 
 gsc_status gsc_workspace_create(void* device_buffer, size_t bytes, int64_t max_gaussians, int64_t max_pairs,
-                                int32_t max_w, int32_t max_h, const gsc_raster_cfg* cfg, gsc_workspace** out) {
+                                int32_t max_w, int32_t max_h, int32_t max_views, const gsc_raster_cfg* cfg,
+                                gsc_workspace** out) {
     if (!out) return fail(GSC_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     size_t need;
-    gsc_status st = gsc_workspace_size(max_gaussians, max_pairs, max_w, max_h, cfg, &need);
+    gsc_status st = gsc_workspace_size(max_gaussians, max_pairs, max_w, max_h, max_views, cfg, &need);
     if (st) return st;
     if (!device_buffer || !aligned(device_buffer, 256)) return fail(GSC_ERR_INVALID_ARG, "buffer not 256-B aligned");
     if (bytes < need) return fail(GSC_ERR_OOM, "workspace buffer has %zu bytes, needs %zu", bytes, need);
@@ -351,7 +378,7 @@ gsc_status gsc_workspace_create(void* device_buffer, size_t bytes, int64_t max_g
     if (!ws) return fail(GSC_ERR_OOM, "host allocation");
     ws->base = (char*)device_buffer;
     ws->bytes = bytes;
-    layout(max_gaussians, max_pairs, max_w, max_h, ws, (char*)device_buffer);
+    layout(max_gaussians, max_pairs, max_w, max_h, max_views, ws, (char*)device_buffer);
     cudaError_t e = cudaMemset(ws->status, 0, sizeof(int32_t) * kStatusWords);
     if (e == cudaSuccess) e = cudaMemset(ws->counters, 0, sizeof(uint32_t) * kCounterWords);
     if (e == cudaSuccess) e = cudaMemset(ws->stats, 0, sizeof(unsigned long long) * kStatWords);
@@ -423,11 +450,13 @@ gsc_status gsc_cache_render(const float* params, int64_t N, const gsc_camera* ca
         GSC_CUDA(cudaMemsetAsync(image, 0, sizeof(float) * 3 * (size_t)cam->width * cam->height, s));
         return GSC_OK;
     }
-    CamDev cd = cam_dev(cam);
-    RasterDev rc = raster_dev(cfg, cam);
+    RasterDev rc = raster_dev(cfg);
+    BatchDev b;
+    batch_init(b);
+    add_view(b, rc, cam, params, N, image, nullptr, nullptr);
     const uint32_t* vals = nullptr;
-    cudaError_t e = bin_gaussians(params, N, cd, rc, ws, &vals, s);
-    if (e == cudaSuccess) e = launch_render(cd, rc, ws, vals, image, s);
+    cudaError_t e = bin_gaussians(b, rc, ws, &vals, s);
+    if (e == cudaSuccess) e = launch_render(b, rc, ws, vals, s);
     if (e != cudaSuccess) return cuda_fail(e, "gsc_cache_render launch");
     return GSC_OK;
 }
@@ -440,12 +469,85 @@ gsc_status gsc_cache_backward(const float* params, int64_t N, const gsc_camera* 
         return fail(GSC_ERR_INVALID_ARG, "dL_dimage/grads NULL or grads not 16-B aligned");
     if (N == 0) return GSC_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    CamDev cd = cam_dev(cam);
-    RasterDev rc = raster_dev(cfg, cam);
+    RasterDev rc = raster_dev(cfg);
+    BatchDev b;
+    batch_init(b);
+    add_view(b, rc, cam, params, N, nullptr, dL_dimage, grads);
     const uint32_t* vals = nullptr;
-    cudaError_t e = bin_gaussians(params, N, cd, rc, ws, &vals, s);
-    if (e == cudaSuccess) e = launch_render_backward(params, N, cd, rc, ws, vals, dL_dimage, grads, s);
+    cudaError_t e = bin_gaussians(b, rc, ws, &vals, s);
+    if (e == cudaSuccess) e = launch_render_backward(b, rc, ws, vals, false, s);
     if (e != cudaSuccess) return cuda_fail(e, "gsc_cache_backward launch");
+    return GSC_OK;
+}
+
+gsc_status gsc_render_batch(const gsc_view* views, int32_t n_views, int32_t mode, const gsc_raster_cfg* cfg,
+                            gsc_workspace* ws, gsc_stream_t stream) {
+    if (!views || n_views < 1 || n_views > kMaxViews)
+        return fail(GSC_ERR_INVALID_ARG, "n_views must be in [1, %d]", kMaxViews);
+    if (mode < GSC_BATCH_FWD || mode > (GSC_BATCH_FWD | GSC_BATCH_BWD))
+        return fail(GSC_ERR_INVALID_ARG, "mode must be GSC_BATCH_FWD, GSC_BATCH_BWD or both");
+    gsc_status st = check_cfg(cfg);
+    if (st) return st;
+    if (!ws) return fail(GSC_ERR_INVALID_ARG, "workspace is NULL");
+    int64_t total = 0;
+    // larger views first: the persistent kernels hand out their tiles first
+    int order[kMaxViews];
+    for (int i = 0; i < n_views; ++i) order[i] = i;
+    for (int i = 1; i < n_views; ++i)
+        for (int j = i; j > 0; --j) {
+            const gsc_camera& a = views[order[j - 1]].cam;
+            const gsc_camera& c = views[order[j]].cam;
+            if ((int64_t)a.width * a.height >= (int64_t)c.width * c.height) break;
+            int t = order[j - 1];
+            order[j - 1] = order[j];
+            order[j] = t;
+        }
+    bool shared = false;
+    for (int i = 0; i < n_views; ++i) {
+        const gsc_view& v = views[i];
+        if ((st = check_cam(&v.cam))) return st;
+        if ((st = check_ws(ws, v.N, &v.cam))) return st;
+        if (v.N > 0 && (!v.params || !aligned(v.params, 16)))
+            return fail(GSC_ERR_INVALID_ARG, "view %d: params NULL or not 16-B aligned", i);
+        if ((mode & GSC_BATCH_FWD) && !v.image) return fail(GSC_ERR_INVALID_ARG, "view %d: image is NULL", i);
+        if ((mode & GSC_BATCH_BWD) && (!v.dL_dimage || (v.N > 0 && (!v.grads || !aligned(v.grads, 16)))))
+            return fail(GSC_ERR_INVALID_ARG, "view %d: dL_dimage/grads NULL or misaligned", i);
+        total += v.N;
+        for (int j = 0; j < i; ++j)
+            if (v.grads && v.grads == views[j].grads) shared = true;
+    }
+    if (total > ws->max_gaussians)
+        return fail(GSC_ERR_INVALID_ARG, "the batch holds %lld Gaussians, the workspace %lld", (long long)total,
+                    (long long)ws->max_gaussians);
+    cudaStream_t s = (cudaStream_t)stream;
+    RasterDev rc = raster_dev(cfg);
+    BatchDev b;
+    batch_init(b);
+    for (int k = 0; k < n_views; ++k) {
+        const gsc_view& v = views[order[k]];
+        add_view(b, rc, &v.cam, v.params, v.N, v.image, v.dL_dimage, v.grads);
+    }
+    if ((int64_t)b.total_bins > ws->max_tiles)
+        return fail(GSC_ERR_INVALID_ARG, "the batch has %u bins, the workspace %lld (raise max_views)", b.total_bins,
+                    (long long)ws->max_tiles);
+    if (total == 0) {
+        if (mode & GSC_BATCH_FWD)
+            for (int i = 0; i < n_views; ++i)
+                GSC_CUDA(cudaMemsetAsync(views[i].image, 0,
+                                         sizeof(float) * 3 * (size_t)views[i].cam.width * views[i].cam.height, s));
+        return GSC_OK;
+    }
+    const uint32_t* vals = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (mode & GSC_BATCH_FWD) {
+        e = bin_gaussians(b, rc, ws, &vals, s);
+        if (e == cudaSuccess) e = launch_render(b, rc, ws, vals, s);
+    }
+    if (e == cudaSuccess && (mode & GSC_BATCH_BWD)) {
+        e = bin_gaussians(b, rc, ws, &vals, s);
+        if (e == cudaSuccess) e = launch_render_backward(b, rc, ws, vals, shared, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "gsc_render_batch launch");
     return GSC_OK;
 }
 
@@ -454,7 +556,7 @@ gsc_status gsc_cache_backward(const float* params, int64_t N, const gsc_camera* 
 gsc_status gsc_loss(int32_t kind, const float* pred, const float* target, int32_t C, int32_t H, int32_t W,
                     const int32_t* crop, float* dL_dpred, float* loss_out, gsc_workspace* ws, gsc_stream_t stream) {
     if (!pred || !target || !loss_out || !ws) return fail(GSC_ERR_INVALID_ARG, "NULL argument");
-    if (kind != GSC_LOSS_HDR && kind != GSC_LOSS_HDR_FULLGRAD)
+    if (kind != GSC_LOSS_HDR && kind != GSC_LOSS_HDR_FULLGRAD && kind != GSC_LOSS_L1_SSIM)
         return fail(GSC_ERR_INVALID_ARG, "loss kind %d not available", kind);
     if (C < 1 || H < 1 || W < 1) return fail(GSC_ERR_INVALID_ARG, "empty image");
     int x0 = 0, y0 = 0, w = W, h = H;
@@ -463,6 +565,8 @@ gsc_status gsc_loss(int32_t kind, const float* pred, const float* target, int32_
         if (x0 < 0 || y0 < 0 || w < 1 || h < 1 || x0 + w > W || y0 + h > H)
             return fail(GSC_ERR_INVALID_ARG, "crop outside the image");
     }
+    if (kind == GSC_LOSS_L1_SSIM && (size_t)65536 + 3 * (size_t)C * w * h > ws->red_floats)
+        return fail(GSC_ERR_OOM, "L1+SSIM over %d x %d x %d needs a workspace made for a larger image", C, w, h);
     cudaError_t e = launch_loss(kind, pred, target, C, H, W, x0, y0, w, h, dL_dpred, loss_out, ws->red,
                                 ws->red_floats, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "gsc_loss launch");

@@ -29,12 +29,44 @@ struct CamDev {
     int W, H;
 };
 
+// launch configuration and compositing constants shared by all views of a call
 struct RasterDev {
     float alpha_max, alpha_min, T_min, near_plane, dilation;
-    int tile_w, tile_h, tiles_x, tiles_y, cap;
-    int bin, bins_x, bins_y, spt_x, spt_y;  // bin size (px), bin grid, tiles per bin side
-    int ppt;                                // pixels per thread (1 or 2)
+    int tile_w, tile_h, cap;
+    int bin, spt_x, spt_y;  // bin size (px), tiles per bin side
+    int ppt;                // pixels per thread (1 or 2)
 };
+
+// One view of a (possibly batched) render: its camera, its Gaussians (global
+// indices [g_off, g_off + N) of the call), its tiles and bins (global
+// numbering from tile_off / bin_off) and its images.
+constexpr int kMaxViews = 32;
+struct ViewDev {
+    CamDev cam;
+    const float4* params;
+    float* image;
+    const float* dL;
+    float4* grads;
+    uint32_t g_off, N, tile_off, bin_off;
+    int tiles_x, tiles_y, bins_x, bins_y;
+};
+struct BatchDev {
+    int nviews;
+    uint32_t total_g, total_tiles, total_bins;
+    ViewDev v[kMaxViews];
+};
+
+// view owning global Gaussian g / global tile t (linear scans: <= 32 views)
+__device__ __forceinline__ int view_of_gaussian(const BatchDev& b, uint32_t g) {
+    int v = 0;
+    while (v + 1 < b.nviews && g >= b.v[v + 1].g_off) ++v;
+    return v;
+}
+__device__ __forceinline__ int view_of_tile(const BatchDev& b, uint32_t t) {
+    int v = 0;
+    while (v + 1 < b.nviews && t >= b.v[v + 1].tile_off) ++v;
+    return v;
+}
 
 // sets the calling thread's last error message (api.cu) and returns st
 gsc_status set_error(gsc_status st, const char* fmt, ...);
@@ -56,7 +88,7 @@ struct PhaseScope {
 // status words in the workspace
 enum : int { kStatusCode = 0, kStatusWords = 4 };
 // counters in the workspace
-enum : int { kCntPairs = 0, kCntPairsMax = 1, kCounterWords = 8 };
+enum : int { kCntPairs = 0, kCntPairsMax = 1, kCntTilesFwd = 2, kCntTilesBwd = 3, kCounterWords = 8 };
 // 64-bit work statistics in the workspace
 enum : int { kStEvalFwd = 0, kStCompFwd = 1, kStEvalRewalk = 2, kStEvalBack = 3, kStPairsSum = 4, kStBinnings = 5,
              kStatWords = 8 };
@@ -104,14 +136,14 @@ int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, con
                      uint32_t n_host, int bits, int blocks, uint32_t* hist, cudaStream_t s);
 int sort_blocks_for(uint64_t n);
 
-// raster.cu
-cudaError_t bin_gaussians(const float* params, int64_t N, const CamDev& cam, const RasterDev& rc,
-                          gsc_workspace* ws, const uint32_t** sorted_vals, cudaStream_t s);
-cudaError_t launch_render(const CamDev& cam, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
-                          float* image, cudaStream_t s);
-cudaError_t launch_render_backward(const float* params, int64_t N, const CamDev& cam, const RasterDev& rc,
-                                   gsc_workspace* ws, const uint32_t* vals, const float* dL_dimage, float* grads,
-                                   cudaStream_t s);
+// raster.cu (every view of the batch shares rc)
+cudaError_t bin_gaussians(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t** sorted_vals,
+                          cudaStream_t s);
+cudaError_t launch_render(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
+                          cudaStream_t s);
+// shared_params: two views write the same parameter gradients (atomics needed)
+cudaError_t launch_render_backward(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
+                                   bool shared_params, cudaStream_t s);
 
 // trace.cu
 cudaError_t launch_trace(const gsc_scene* sc, const CamDev& cam, const gsc_trace_params& p, const float* cache,

@@ -68,6 +68,138 @@ __global__ void k_reduce_final(const float* __restrict__ partial, int n, double 
     }
 }
 
+// ------------------------------------------------------------------ L1 + D-SSIM
+//
+// 0.8 L1 + 0.2 (1 - SSIM) over the crop, treated as its own zero-padded
+// image; SSIM of Wang et al. (2004) per channel with an 11x11 Gaussian window
+// (sigma 1.5, normalised), C1 = 0.01^2, C2 = 0.03^2.  Pass 1 computes the
+// windowed moments of every crop pixel directly (121 taps), the SSIM value
+// and its partial derivatives with respect to mu_x, E[x^2] and E[xy]; pass 2
+// correlates those three maps with the window:
+//   d mean(SSIM) / d x_q = (w * g_mu)(q) + 2 x_q (w * g_xx)(q) + y_q (w * g_xy)(q).
+struct SsimDev {
+    float w[11];
+};
+
+constexpr int kSsimScratchOffset = 65536;  // floats of the reduction area before the maps
+
+__global__ void __launch_bounds__(kRedThreads) k_ssim_fwd(const float* __restrict__ pred,
+                                                          const float* __restrict__ tgt, int C, int H, int W,
+                                                          int x0, int y0, int w, int h, SsimDev win,
+                                                          float* __restrict__ gmaps, float* __restrict__ partial) {
+    __shared__ float sm[32];
+    const float C1 = 1e-4f, C2 = 9e-4f;
+    size_t plane = (size_t)w * h, n = (size_t)C * plane;
+    float l1 = 0.f, ssum = 0.f;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        int ch = (int)(e / plane);
+        size_t r = e - (size_t)ch * plane;
+        int j = (int)(r / w), i = (int)(r - (size_t)j * w);
+        float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+        for (int dy = -5; dy <= 5; ++dy) {
+            int jj = j + dy;
+            if (jj < 0 || jj >= h) continue;
+            const float* px = pred + ((size_t)ch * H + (y0 + jj)) * W + x0;
+            const float* py = tgt + ((size_t)ch * H + (y0 + jj)) * W + x0;
+            float wy = win.w[dy + 5];
+#pragma unroll
+            for (int dx = -5; dx <= 5; ++dx) {
+                int ii = i + dx;
+                if (ii < 0 || ii >= w) continue;
+                float ww = wy * win.w[dx + 5];
+                float xv = px[ii], yv = py[ii];
+                mx = fmaf(ww, xv, mx);
+                my = fmaf(ww, yv, my);
+                exx = fmaf(ww, xv * xv, exx);
+                eyy = fmaf(ww, yv * yv, eyy);
+                exy = fmaf(ww, xv * yv, exy);
+            }
+        }
+        float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+        float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy + C2;
+        float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
+        float inv = 1.f / (B1 * B2);
+        float sv = A1 * A2 * inv;
+        ssum += sv;
+        // partials with mu_y and E[y^2] held fixed
+        float gmu = (2.f * my * A2 - 2.f * my * A1) * inv - sv * (2.f * mx * B2 - 2.f * mx * B1) * inv;
+        gmaps[e] = gmu;
+        gmaps[n + e] = -sv / B2;
+        gmaps[2 * n + e] = 2.f * A1 * inv;
+        size_t p = ((size_t)ch * H + (y0 + j)) * W + (x0 + i);
+        l1 += fabsf(pred[p] - tgt[p]);
+    }
+    float t1 = block_sum(l1, sm);
+    float t2 = block_sum(ssum, sm);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = t1;
+        partial[gridDim.x + blockIdx.x] = t2;
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_ssim_bwd(const float* __restrict__ pred,
+                                                          const float* __restrict__ tgt, int C, int H, int W,
+                                                          int x0, int y0, int w, int h, SsimDev win, float invk,
+                                                          const float* __restrict__ gmaps, float* __restrict__ dL) {
+    size_t plane = (size_t)w * h, n = (size_t)C * plane;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        int ch = (int)(e / plane);
+        size_t r = e - (size_t)ch * plane;
+        int j = (int)(r / w), i = (int)(r - (size_t)j * w);
+        float fmu = 0.f, fxx = 0.f, fxy = 0.f;
+        for (int dy = -5; dy <= 5; ++dy) {
+            int jj = j + dy;
+            if (jj < 0 || jj >= h) continue;
+            size_t rowb = (size_t)ch * plane + (size_t)jj * w;
+            float wy = win.w[dy + 5];
+#pragma unroll
+            for (int dx = -5; dx <= 5; ++dx) {
+                int ii = i + dx;
+                if (ii < 0 || ii >= w) continue;
+                float ww = wy * win.w[dx + 5];
+                size_t q = rowb + ii;
+                fmu = fmaf(ww, gmaps[q], fmu);
+                fxx = fmaf(ww, gmaps[n + q], fxx);
+                fxy = fmaf(ww, gmaps[2 * n + q], fxy);
+            }
+        }
+        size_t p = ((size_t)ch * H + (y0 + j)) * W + (x0 + i);
+        float xv = pred[p], yv = tgt[p];
+        float ds = fmu + 2.f * xv * fxx + yv * fxy;
+        float d = xv - yv;
+        float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+        dL[p] = (0.8f * sg - 0.2f * ds) * invk;
+    }
+}
+
+__global__ void k_ssim_final(const float* __restrict__ partial, int nb, double invk, float* __restrict__ out) {
+    __shared__ double sm1[32], sm2[32];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        a += (double)partial[i];
+        b += (double)partial[nb + i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(kFull, a, o);
+        b += __shfl_xor_sync(kFull, b, o);
+    }
+    int wq = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sm1[wq] = a;
+        sm2[wq] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double l1 = 0.0, ss = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            l1 += sm1[k];
+            ss += sm2[k];
+        }
+        *out = (float)(0.8 * l1 * invk + 0.2 * (1.0 - ss * invk));
+    }
+}
+
 cudaError_t launch_loss(int kind, const float* pred, const float* target, int C, int H, int W, int x0, int y0,
                         int w, int h, float* dL_dpred, float* loss_out, float* red, size_t red_floats,
                         cudaStream_t s) {
@@ -84,6 +216,27 @@ cudaError_t launch_loss(int kind, const float* pred, const float* target, int C,
         k_loss_hdr<<<blocks, kRedThreads, 0, s>>>(pred, target, C, H, W, x0, y0, w, h,
                                                   kind == GSC_LOSS_HDR_FULLGRAD, invk, dL_dpred, red);
         k_reduce_final<<<1, 1024, 0, s>>>(red, blocks, n ? 1.0 / (double)n : 0.0, loss_out);
+        return cudaGetLastError();
+    }
+    if (kind == GSC_LOSS_L1_SSIM) {
+        if (red_floats < (size_t)kSsimScratchOffset + 3 * n) return cudaErrorMemoryAllocation;
+        SsimDev win;
+        double ws[11], tot = 0.0;
+        for (int k = 0; k < 11; ++k) {
+            ws[k] = exp(-(double)((k - 5) * (k - 5)) / (2.0 * 1.5 * 1.5));
+            tot += ws[k];
+        }
+        for (int k = 0; k < 11; ++k) win.w[k] = (float)(ws[k] / tot);
+        int blocks = (int)((n + kRedThreads - 1) / kRedThreads);
+        if (blocks > kRedBlocks) blocks = kRedBlocks;
+        if (blocks < 1) blocks = 1;
+        float* gmaps = red + kSsimScratchOffset;
+        PhaseScope ph(kPhLoss, s, dL_dpred ? 3 : 2);
+        k_ssim_fwd<<<blocks, kRedThreads, 0, s>>>(pred, target, C, H, W, x0, y0, w, h, win, gmaps, red);
+        if (dL_dpred)
+            k_ssim_bwd<<<blocks, kRedThreads, 0, s>>>(pred, target, C, H, W, x0, y0, w, h, win,
+                                                      (float)(1.0 / (double)n), gmaps, dL_dpred);
+        k_ssim_final<<<1, 1024, 0, s>>>(red, blocks, 1.0 / (double)n, loss_out);
         return cudaGetLastError();
     }
     return cudaErrorInvalidValue;

@@ -121,14 +121,17 @@ __device__ __forceinline__ bool project_core(float4 p0, float4 p1, float4 p2, co
     return true;
 }
 
-__global__ void __launch_bounds__(256) k_project(const float4* __restrict__ params, uint32_t N, CamDev cam,
-                                                 RasterDev rc, float4* __restrict__ rec, uint32_t* __restrict__ key,
+// one thread per Gaussian of the batch (global index g of view v)
+__global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchDev b, RasterDev rc,
+                                                 float4* __restrict__ rec, uint32_t* __restrict__ key,
                                                  uint32_t* __restrict__ idx, uint2* __restrict__ rect,
                                                  uint32_t* __restrict__ cnt) {
     uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= N) return;
-    float4 p0 = params[4 * (size_t)g], p1 = params[4 * (size_t)g + 1];
-    float4 p2 = params[4 * (size_t)g + 2], p3 = params[4 * (size_t)g + 3];
+    if (g >= b.total_g) return;
+    const ViewDev& vw = b.v[view_of_gaussian(b, g)];
+    const CamDev& cam = vw.cam;
+    const float4* params = vw.params + 4 * (size_t)(g - vw.g_off);
+    float4 p0 = params[0], p1 = params[1], p2 = params[2], p3 = params[3];
     idx[g] = g;
     key[g] = 0xffffffffu;
     cnt[g] = 0;
@@ -165,22 +168,28 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ para
 // one warp writes the (bin, Gaussian) pairs of 32 consecutive depth-ordered
 // Gaussians, one Gaussian at a time, so that every store instruction is
 // contiguous; the bin rectangle follows from the tile rectangle
-__global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ off,
-                                              const uint32_t* __restrict__ cnt, const uint2* __restrict__ rect,
-                                              uint32_t N, RasterDev rc, const uint32_t* __restrict__ counters,
-                                              uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval) {
+__global__ void __launch_bounds__(256) k_emit(const __grid_constant__ BatchDev b, const uint32_t* __restrict__ sidx,
+                                              const uint32_t* __restrict__ off, const uint32_t* __restrict__ cnt,
+                                              const uint2* __restrict__ rect, RasterDev rc,
+                                              const uint32_t* __restrict__ counters, uint32_t* __restrict__ pkey,
+                                              uint32_t* __restrict__ pval) {
+    const uint32_t N = b.total_g;
     uint32_t total = counters[kCntPairs];
     uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     uint32_t i = wid * 32 + lane;
     if (wid * 32 >= N) return;
     uint32_t g = 0, c = 0, o = 0;
+    int v = 0;
     uint2 rr = make_uint2(0, 0);
     if (i < N) {
         g = sidx[i];
         c = cnt[g];
         o = off[i];
-        if (c) rr = rect[g];
+        if (c) {
+            rr = rect[g];
+            v = view_of_gaussian(b, g);
+        }
     }
     for (int j = 0; j < 32; ++j) {
         uint32_t cj = __shfl_sync(kFull, c, j);
@@ -188,13 +197,15 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ sidx,
         uint32_t gj = __shfl_sync(kFull, g, j);
         uint32_t rx = __shfl_sync(kFull, rr.x, j);
         uint32_t ry = __shfl_sync(kFull, rr.y, j);
+        int vj = __shfl_sync(kFull, v, j);
         if (cj == 0 || (uint64_t)oj + cj > total) continue;
         uint32_t bx0 = (rx & 0xffffu) / rc.spt_x, bx1 = ((rx >> 16) - 1) / rc.spt_x + 1;
         uint32_t by0 = (ry & 0xffffu) / rc.spt_y;
         uint32_t wx = bx1 - bx0;
+        const uint32_t boff = b.v[vj].bin_off, bins_x = (uint32_t)b.v[vj].bins_x;
         for (uint32_t k = lane; k < cj; k += 32) {
             uint32_t ky = k / wx, kx = k - ky * wx;
-            pkey[oj + k] = (by0 + ky) * (uint32_t)rc.bins_x + bx0 + kx;
+            pkey[oj + k] = boff + (by0 + ky) * bins_x + bx0 + kx;
             pval[oj + k] = gj;
         }
     }
@@ -292,11 +303,12 @@ __device__ __forceinline__ void warp_count(unsigned long long* dst, uint32_t v) 
 // pixel composites the staged entries.  The CTA stops when all its pixels
 // have reached T_min.
 template <int TW, int TH, int PPT>
-__global__ void __launch_bounds__(TW* TH / PPT) k_render(const uint2* __restrict__ ranges,
+__global__ void __launch_bounds__(TW* TH / PPT) k_render(const __grid_constant__ BatchDev b,
+                                                         const uint2* __restrict__ ranges,
                                                          const uint32_t* __restrict__ vals,
                                                          const uint2* __restrict__ rect,
-                                                         const float4* __restrict__ rec, CamDev cam, RasterDev rc,
-                                                         float* __restrict__ image,
+                                                         const float4* __restrict__ rec, RasterDev rc,
+                                                         uint32_t* __restrict__ queue,
                                                          unsigned long long* __restrict__ stats) {
     constexpr int NT = TW * TH / PPT;
     constexpr int ROWS = TH / PPT;
@@ -306,8 +318,19 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render(const uint2* __restrict
     float4* s0 = smem;
     float4* s1 = smem + cap;
     float4* s2 = smem + 2 * cap;
-    int tile = blockIdx.x;
-    int tx = tile % rc.tiles_x, ty = tile / rc.tiles_x;
+    uint32_t n_eval = 0, n_comp = 0;
+    __shared__ uint32_t s_tile;
+    // persistent CTAs: tiles of all views are handed out by an atomic counter
+    for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(queue, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    __syncthreads();
+    if (tile >= b.total_tiles) break;
+    const ViewDev& vw = b.v[view_of_tile(b, tile)];
+    const CamDev& cam = vw.cam;
+    const uint32_t lt = tile - vw.tile_off;
+    const int tx = (int)(lt % (uint32_t)vw.tiles_x), ty = (int)(lt / (uint32_t)vw.tiles_x);
     int px = tx * TW + (threadIdx.x % TW), py0 = ty * TH + (threadIdx.x / TW);
     float fx = (float)px + 0.5f;
     float fy[PPT], T[PPT], Cr[PPT], Cg[PPT], Cb[PPT];
@@ -321,8 +344,7 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render(const uint2* __restrict
         Cr[q] = Cg[q] = Cb[q] = 0.f;
         done[q] = !inside[q];
     }
-    uint2 rg = ranges[(ty / rc.spt_y) * rc.bins_x + tx / rc.spt_x];
-    uint32_t n_eval = 0, n_comp = 0;
+    uint2 rg = ranges[vw.bin_off + (ty / rc.spt_y) * vw.bins_x + tx / rc.spt_x];
     uint32_t pos = rg.x;
     for (;;) {
         bool tdone = true;
@@ -394,18 +416,19 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render(const uint2* __restrict
             }
         }
     }
-    warp_count(&stats[kStEvalFwd], n_eval);
-    warp_count(&stats[kStCompFwd], n_comp);
     size_t HW = (size_t)cam.W * cam.H;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
         if (inside[q]) {
             size_t p = (size_t)(py0 + q * ROWS) * cam.W + px;
-            image[p] = Cr[q];
-            image[HW + p] = Cg[q];
-            image[2 * HW + p] = Cb[q];
+            vw.image[p] = Cr[q];
+            vw.image[HW + p] = Cg[q];
+            vw.image[2 * HW + p] = Cb[q];
         }
     }
+    }  // tiles
+    warp_count(&stats[kStEvalFwd], n_eval);
+    warp_count(&stats[kStCompFwd], n_comp);
 }
 
 // ------------------------------------------------------------------ backward
@@ -457,12 +480,12 @@ constexpr int kHitRing = 2048;
 constexpr int kMaxChunks = 512;
 
 template <int TW, int TH, int PPT>
-__global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const uint2* __restrict__ ranges,
+__global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_constant__ BatchDev b,
+                                                             const uint2* __restrict__ ranges,
                                                              const uint32_t* __restrict__ vals,
                                                              const uint2* __restrict__ rect,
-                                                             const float4* __restrict__ rec, CamDev cam, RasterDev rc,
-                                                             const float* __restrict__ dL_dimg,
-                                                             float4* __restrict__ g2d,
+                                                             const float4* __restrict__ rec, RasterDev rc,
+                                                             float4* __restrict__ g2d, uint32_t* __restrict__ queue,
                                                              unsigned long long* __restrict__ stats) {
     constexpr int NT = TW * TH / PPT;
     constexpr int ROWS = TH / PPT;
@@ -475,8 +498,20 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const uint2* __rest
     float4* s1 = smem + cap;
     float4* s2 = smem + 2 * cap;
     uint32_t* hits = reinterpret_cast<uint32_t*>(smem + 3 * cap);
-    int tile = blockIdx.x;
-    int tx = tile % rc.tiles_x, ty = tile / rc.tiles_x;
+    uint32_t n_eval1 = 0, n_eval2 = 0;
+    __shared__ uint32_t s_tile;
+    // persistent CTAs: tiles of all views are handed out by an atomic counter
+    for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(queue, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    __syncthreads();
+    if (tile >= b.total_tiles) break;
+    const ViewDev& vw = b.v[view_of_tile(b, tile)];
+    const CamDev& cam = vw.cam;
+    const uint32_t lt = tile - vw.tile_off;
+    const int tx = (int)(lt % (uint32_t)vw.tiles_x), ty = (int)(lt / (uint32_t)vw.tiles_x);
+    const float* dL_dimg = vw.dL;
     int px = tx * TW + (threadIdx.x % TW), py0 = ty * TH + (threadIdx.x / TW);
     float fx = (float)px + 0.5f;
     size_t HW = (size_t)cam.W * cam.H;
@@ -500,11 +535,10 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const uint2* __rest
         T[q] = 1.f;
         last[q] = 0;
     }
-    uint2 rg = ranges[(ty / rc.spt_y) * rc.bins_x + tx / rc.spt_x];
+    uint2 rg = ranges[vw.bin_off + (ty / rc.spt_y) * vw.bins_x + tx / rc.spt_x];
 
     // ---- phase 1
     uint32_t nhit = 0;  // hits found so far (uniform)
-    uint32_t n_eval1 = 0, n_eval2 = 0;
     uint32_t pos = rg.x;
     for (;;) {
         bool tdone = true;
@@ -679,32 +713,38 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const uint2* __rest
             b1 = b0;
         }
     }
+    }  // tiles
     warp_count(&stats[kStEvalRewalk], n_eval1);
     warp_count(&stats[kStEvalBack], n_eval2);
 }
 
 // 2D gradients -> packed parameter gradients (+=)
-__global__ void __launch_bounds__(128) k_project_bwd(const float4* __restrict__ params, uint32_t N, CamDev cam,
-                                                     RasterDev rc, const uint32_t* __restrict__ cnt,
-                                                     const float4* __restrict__ g2d, float4* __restrict__ grads) {
+// (vector atomics when two views of the batch share a parameter set)
+__global__ void __launch_bounds__(128) k_project_bwd(const __grid_constant__ BatchDev b, RasterDev rc,
+                                                     const uint32_t* __restrict__ cnt,
+                                                     const float4* __restrict__ g2d, int shared_params) {
     uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= N || cnt[g] == 0) return;
+    if (g >= b.total_g || cnt[g] == 0) return;
+    const ViewDev& vw = b.v[view_of_gaussian(b, g)];
+    const CamDev& cam = vw.cam;
+    const size_t l = g - vw.g_off;
+    const float4* prm = vw.params + 4 * l;
+    float4* grd = vw.grads + 4 * l;
     float4 a0 = g2d[3 * (size_t)g], a1 = g2d[3 * (size_t)g + 1], a2 = g2d[3 * (size_t)g + 2];
     if (a0.x == 0.f && a0.y == 0.f && a0.z == 0.f && a0.w == 0.f && a1.x == 0.f && a1.y == 0.f && a2.x == 0.f &&
         a2.y == 0.f && a2.z == 0.f)
         return;
-    float4 p0 = params[4 * (size_t)g], p1 = params[4 * (size_t)g + 1];
-    float4 p2 = params[4 * (size_t)g + 2], p3 = params[4 * (size_t)g + 3];
+    float4 p0 = prm[0], p1 = prm[1], p2 = prm[2], p3 = prm[3];
     Proj x;
     if (!project_core(p0, p1, p2, cam, rc, x)) return;
     const float* R = cam.R;
     // conic entries from the scaled ones used by the rasterizer
     float ga = a0.z * (-0.5f * kLog2e), gb = a0.w * (-kLog2e), gc = a1.x * (-0.5f * kLog2e);
     // dL/dSigma2D = -Q G Q with Q = conic, G = [[ga, gb/2], [gb/2, gc]]
-    float a = x.a, b = x.b, c = x.c;
-    float dA = -(ga * a * a + gb * a * b + gc * b * b);
-    float dC = -(ga * b * b + gb * b * c + gc * c * c);
-    float dB = -(2.f * ga * a * b + gb * (a * c + b * b) + 2.f * gc * b * c);
+    float qa = x.a, qb = x.b, qc = x.c;
+    float dA = -(ga * qa * qa + gb * qa * qb + gc * qb * qb);
+    float dC = -(ga * qb * qb + gb * qb * qc + gc * qc * qc);
+    float dB = -(2.f * ga * qa * qb + gb * (qa * qc + qb * qb) + 2.f * gc * qb * qc);
     const float* T0 = x.Tm;
     const float* T1 = x.Tm + 3;
     float st0[3], st1[3];
@@ -730,8 +770,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(const float4* __restrict__ 
     float dty = dJ12 * (-cam.fy * iz2) + a0.y * cam.fy * iz;
     float dtz = dJ00 * (-cam.fx * iz2) + dJ02 * (2.f * cam.fx * tx * iz3) + dJ11 * (-cam.fy * iz2) +
                 dJ12 * (2.f * cam.fy * ty * iz3) - a0.x * cam.fx * tx * iz2 - a0.y * cam.fy * ty * iz2;
-    float4 o0 = grads[4 * (size_t)g], o1 = grads[4 * (size_t)g + 1];
-    float4 o2 = grads[4 * (size_t)g + 2], o3 = grads[4 * (size_t)g + 3];
+    float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0, o2 = o0, o3 = o0;
     o0.x += R[0] * dtx + R[3] * dty + R[6] * dtz;
     o0.y += R[1] * dtx + R[4] * dty + R[7] * dtz;
     o0.z += R[2] * dtx + R[5] * dty + R[8] * dtz;
@@ -775,10 +814,18 @@ __global__ void __launch_bounds__(128) k_project_bwd(const float4* __restrict__ 
     if (p3.x > 0.f) o3.x += a2.x;
     if (p3.y > 0.f) o3.y += a2.y;
     if (p3.z > 0.f) o3.z += a2.z;
-    grads[4 * (size_t)g] = o0;
-    grads[4 * (size_t)g + 1] = o1;
-    grads[4 * (size_t)g + 2] = o2;
-    grads[4 * (size_t)g + 3] = o3;
+    if (shared_params) {
+        atomicAdd(&grd[0], o0);
+        atomicAdd(&grd[1], o1);
+        atomicAdd(&grd[2], o2);
+        atomicAdd(&grd[3], o3);
+    } else {
+        float4 c0 = grd[0], c1 = grd[1], c2 = grd[2], c3 = grd[3];
+        grd[0] = make_float4(c0.x + o0.x, c0.y + o0.y, c0.z + o0.z, c0.w + o0.w);
+        grd[1] = make_float4(c1.x + o1.x, c1.y + o1.y, c1.z + o1.z, c1.w + o1.w);
+        grd[2] = make_float4(c2.x + o2.x, c2.y + o2.y, c2.z + o2.z, c2.w + o2.w);
+        grd[3] = make_float4(c3.x + o3.x, c3.y + o3.y, c3.z + o3.z, c3.w + o3.w);
+    }
 }
 
 // ------------------------------------------------------------------ host
@@ -789,15 +836,14 @@ static int bits_for(uint32_t n) {
     return b;
 }
 
-cudaError_t bin_gaussians(const float* params, int64_t N, const CamDev& cam, const RasterDev& rc,
-                          gsc_workspace* ws, const uint32_t** sorted_vals, cudaStream_t s) {
-    uint32_t n = (uint32_t)N;
+cudaError_t bin_gaussians(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t** sorted_vals,
+                          cudaStream_t s) {
+    uint32_t n = b.total_g;
     uint32_t nblk = (n + 255) / 256;
     if (nblk == 0) nblk = 1;
     {
         PhaseScope ph(kPhProject, s, 1);
-        k_project<<<nblk, 256, 0, s>>>(reinterpret_cast<const float4*>(params), n, cam, rc, ws->rec, ws->key0,
-                                       ws->idx0, ws->rect, ws->cnt);
+        k_project<<<nblk, 256, 0, s>>>(b, rc, ws->rec, ws->key0, ws->idx0, ws->rect, ws->cnt);
     }
     int w;
     {
@@ -810,14 +856,12 @@ cudaError_t bin_gaussians(const float* params, int64_t N, const CamDev& cam, con
         scan_gathered(ws->cnt, sidx, n, ws->off, ws->scan_sums, ws->counters, ws->status, (uint32_t)ws->max_pairs,
                       ws->stats, s);
     }
-    uint32_t eblk = (n + 255) / 256;
-    if (eblk == 0) eblk = 1;
     {
         PhaseScope ph(kPhEmit, s, 1);
-        k_emit<<<eblk, 256, 0, s>>>(sidx, ws->off, ws->cnt, ws->rect, n, rc, ws->counters, ws->pkey0, ws->pval0);
+        k_emit<<<nblk, 256, 0, s>>>(b, sidx, ws->off, ws->cnt, ws->rect, rc, ws->counters, ws->pkey0, ws->pval0);
     }
-    uint32_t tiles = (uint32_t)rc.bins_x * rc.bins_y;
-    int bits = bits_for(tiles);
+    uint32_t bins = b.total_bins;
+    int bits = bits_for(bins);
     int p;
     {
         PhaseScope ph(kPhTileSort, s, 3 * ((bits + 7) / 8));
@@ -828,7 +872,7 @@ cudaError_t bin_gaussians(const float* params, int64_t N, const CamDev& cam, con
     *sorted_vals = p ? ws->pval1 : ws->pval0;
     {
         PhaseScope ph(kPhRanges, s, 1);
-        cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * tiles, s);
+        cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * bins, s);
         k_ranges<<<152 * 8, 256, 0, s>>>(keys, ws->counters, ws->ranges);
     }
     return cudaGetLastError();
@@ -844,29 +888,52 @@ static cudaError_t ensure_smem(K kern, size_t bytes, int* cached) {
     return e;
 }
 
+// Grid of a persistent kernel: every CTA that fits on the device at once
+// (queried for this kernel, block size and shared memory), at most one per tile.
+template <typename K>
+static int persistent_grid(K kern, int threads, size_t smem, uint32_t tiles, size_t* cached_smem, int* cached_grid) {
+    if (*cached_smem != smem || *cached_grid <= 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem);
+        *cached_grid = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+        *cached_smem = smem;
+    }
+    return (int)((uint32_t)*cached_grid < tiles ? (uint32_t)*cached_grid : (tiles ? tiles : 1));
+}
+
 template <int TW, int TH, int PPT>
-static cudaError_t render_t(const CamDev& cam, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
-                            float* image, cudaStream_t s) {
+static cudaError_t render_t(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
+                            cudaStream_t s) {
     size_t smem = sizeof(float4) * 3 * rc.cap;
     auto kern = k_render<TW, TH, PPT>;
     static int cached = 32 * 1024;
     cudaError_t e = ensure_smem(kern, smem, &cached);
     if (e != cudaSuccess) return e;
-    kern<<<rc.tiles_x * rc.tiles_y, TW * TH / PPT, smem, s>>>(ws->ranges, vals, ws->rect, ws->rec, cam, rc, image,
-                                                               ws->stats);
+    static size_t gs = 0;
+    static int gg = 0;
+    int grid = persistent_grid(kern, TW * TH / PPT, smem, b.total_tiles, &gs, &gg);
+    cudaMemsetAsync(ws->counters + kCntTilesFwd, 0, sizeof(uint32_t), s);
+    kern<<<grid, TW * TH / PPT, smem, s>>>(b, ws->ranges, vals, ws->rect, ws->rec, rc, ws->counters + kCntTilesFwd,
+                                           ws->stats);
     return cudaGetLastError();
 }
 
 template <int TW, int TH, int PPT>
-static cudaError_t render_bwd_t(const CamDev& cam, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
-                                const float* dL, cudaStream_t s) {
+static cudaError_t render_bwd_t(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
+                                cudaStream_t s) {
     size_t smem = sizeof(float4) * 3 * rc.cap + sizeof(uint32_t) * kHitRing;
     auto kern = k_render_bwd<TW, TH, PPT>;
     static int cached = 32 * 1024;
     cudaError_t e = ensure_smem(kern, smem, &cached);
     if (e != cudaSuccess) return e;
-    kern<<<rc.tiles_x * rc.tiles_y, TW * TH / PPT, smem, s>>>(ws->ranges, vals, ws->rect, ws->rec, cam, rc, dL,
-                                                               ws->g2d, ws->stats);
+    static size_t gs = 0;
+    static int gg = 0;
+    int grid = persistent_grid(kern, TW * TH / PPT, smem, b.total_tiles, &gs, &gg);
+    cudaMemsetAsync(ws->counters + kCntTilesBwd, 0, sizeof(uint32_t), s);
+    kern<<<grid, TW * TH / PPT, smem, s>>>(b, ws->ranges, vals, ws->rect, ws->rec, rc, ws->g2d,
+                                           ws->counters + kCntTilesBwd, ws->stats);
     return cudaGetLastError();
 }
 
@@ -888,30 +955,27 @@ static cudaError_t render_bwd_t(const CamDev& cam, const RasterDev& rc, gsc_work
     if (rc.tile_w == 32 && rc.tile_h == 4) return FN<32, 4, 1>(__VA_ARGS__);                  \
     return cudaErrorInvalidValue;
 
-cudaError_t launch_render(const CamDev& cam, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
-                          float* image, cudaStream_t s) {
+cudaError_t launch_render(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
+                          cudaStream_t s) {
     PhaseScope ph(kPhRender, s, 1);
-    GSC_TILE_DISPATCH(render_t, cam, rc, ws, vals, image, s)
+    GSC_TILE_DISPATCH(render_t, b, rc, ws, vals, s)
 }
 
-cudaError_t launch_render_backward(const float* params, int64_t N, const CamDev& cam, const RasterDev& rc,
-                                   gsc_workspace* ws, const uint32_t* vals, const float* dL_dimage, float* grads,
-                                   cudaStream_t s) {
+cudaError_t launch_render_backward(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
+                                   bool shared_params, cudaStream_t s) {
     cudaError_t e;
     {
         PhaseScope ph(kPhRenderBwd, s, 1);
-        cudaMemsetAsync(ws->g2d, 0, sizeof(float4) * 3 * (size_t)N, s);
-        auto launch = [&]() -> cudaError_t { GSC_TILE_DISPATCH(render_bwd_t, cam, rc, ws, vals, dL_dimage, s) };
+        cudaMemsetAsync(ws->g2d, 0, sizeof(float4) * 3 * (size_t)b.total_g, s);
+        auto launch = [&]() -> cudaError_t { GSC_TILE_DISPATCH(render_bwd_t, b, rc, ws, vals, s) };
         e = launch();
     }
     if (e != cudaSuccess) return e;
-    uint32_t n = (uint32_t)N;
-    uint32_t nblk = (n + 127) / 128;
+    uint32_t nblk = (b.total_g + 127) / 128;
     if (nblk == 0) nblk = 1;
     {
         PhaseScope ph(kPhProjectBwd, s, 1);
-        k_project_bwd<<<nblk, 128, 0, s>>>(reinterpret_cast<const float4*>(params), n, cam, rc, ws->cnt, ws->g2d,
-                                           reinterpret_cast<float4*>(grads));
+        k_project_bwd<<<nblk, 128, 0, s>>>(b, rc, ws->cnt, ws->g2d, shared_params ? 1 : 0);
     }
     return cudaGetLastError();
 }

@@ -66,6 +66,19 @@ class FrameLoop:
         self.static_frames = 0
         self._last_pose = None
 
+    def snapshot(self):
+        """Copy of the training state (parameters, moments, step, schedule)."""
+        return ([(L.params.clone(), L.m.clone(), L.v.clone()) for L in self.levels], self.adam_step,
+                self.static_frames, self._last_pose)
+
+    def restore(self, snap):
+        levels, self.adam_step, self.static_frames, self._last_pose = snap
+        for L, (p, m, v) in zip(self.levels, levels):
+            L.params.copy_(p)
+            L.m.copy_(m)
+            L.v.copy_(v)
+            L.grads.zero_()
+
     def _schedule(self, c: gsc.Camera) -> float:
         """Eq. 4: frames the viewport has been unchanged (pose compared bit for bit)."""
         pose = bytes(c)

@@ -52,6 +52,14 @@ class TraceParams(C.Structure):
                 ("seed", C.c_uint64), ("C", C.c_float), ("eps", C.c_float)]
 
 
+class View(C.Structure):
+    _fields_ = [("params", C.c_void_p), ("N", C.c_int64), ("cam", Camera), ("image", C.c_void_p),
+                ("dL_dimage", C.c_void_p), ("grads", C.c_void_p)]
+
+
+BATCH_FWD, BATCH_BWD = 1, 2
+
+
 class Profile(C.Structure):
     _fields_ = [("n_phases", C.c_int32), ("names", (C.c_char * 16) * 24), ("ms", C.c_double * 24),
                 ("launches", C.c_int64 * 24), ("calls", C.c_int64 * 24)]
@@ -74,13 +82,15 @@ SIGNATURES = {
     "gsc_scene_set_tf": (_i32, [_vp, _i32, _vp, _vp]),
     "gsc_scene_destroy": (_i32, [_vp]),
     "gsc_trace": (_i32, [_vp, C.POINTER(Camera), C.POINTER(TraceParams), _vp, _vp, _vp, _vp]),
-    "gsc_workspace_size": (_i32, [_i64, _i64, _i32, _i32, C.POINTER(RasterCfg), C.POINTER(_sz)]),
-    "gsc_workspace_create": (_i32, [_vp, _sz, _i64, _i64, _i32, _i32, C.POINTER(RasterCfg), C.POINTER(_vp)]),
+    "gsc_workspace_size": (_i32, [_i64, _i64, _i32, _i32, _i32, C.POINTER(RasterCfg), C.POINTER(_sz)]),
+    "gsc_workspace_create": (_i32, [_vp, _sz, _i64, _i64, _i32, _i32, _i32, C.POINTER(RasterCfg),
+                                    C.POINTER(_vp)]),
     "gsc_workspace_destroy": (_i32, [_vp]),
     "gsc_workspace_status": (_i32, [_vp, _vp, C.POINTER(_i64)]),
     "gsc_workspace_counters": (_i32, [_vp, _vp, C.POINTER(_i64), _i32]),
     "gsc_cache_render": (_i32, [_vp, _i64, C.POINTER(Camera), C.POINTER(RasterCfg), _vp, _vp, _vp]),
     "gsc_cache_backward": (_i32, [_vp, _i64, C.POINTER(Camera), C.POINTER(RasterCfg), _vp, _vp, _vp, _vp]),
+    "gsc_render_batch": (_i32, [C.POINTER(View), _i32, _i32, C.POINTER(RasterCfg), _vp, _vp]),
     "gsc_loss": (_i32, [_i32, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
     "gsc_loss_noalloc": (_i32, [_i32, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp]),
     "gsc_cache_step": (_i32, [_vp, _vp, _vp, _vp, _i64, C.POINTER(AdamParams), _vp]),
@@ -261,16 +271,18 @@ def trace(scene: Scene, cam, spp: int, max_bounces: int, levels: int, seed: int,
 class Workspace:
     """Rasterizer workspace in a torch-allocated device buffer."""
 
-    def __init__(self, max_gaussians: int, max_pairs: int, max_w: int, max_h: int, device="cuda"):
+    def __init__(self, max_gaussians: int, max_pairs: int, max_w: int, max_h: int, device="cuda",
+                 max_views: int = 1):
         nbytes = C.c_size_t()
-        _check(lib().gsc_workspace_size(max_gaussians, max_pairs, max_w, max_h, None, C.byref(nbytes)))
+        _check(lib().gsc_workspace_size(max_gaussians, max_pairs, max_w, max_h, max_views, None,
+                                        C.byref(nbytes)))
         self.nbytes = nbytes.value
         self.buffer = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device)
         base = self.buffer.data_ptr()
         aligned = (base + 255) & ~255
         h = C.c_void_p()
         _check(lib().gsc_workspace_create(C.c_void_p(aligned), self.nbytes, max_gaussians, max_pairs, max_w, max_h,
-                                          None, C.byref(h)))
+                                          max_views, None, C.byref(h)))
         self.handle = h
         self.max_gaussians, self.max_pairs, self.max_w, self.max_h = max_gaussians, max_pairs, max_w, max_h
 
@@ -325,6 +337,29 @@ def cache_backward(params: torch.Tensor, cam, cfg: RasterCfg, ws: Workspace, dL_
     _check(lib().gsc_cache_backward(_ptr(params), N, C.byref(c), C.byref(cfg), ws.handle, _ptr(dL_dimage),
                                     _ptr(grads), _stream(stream)))
     return grads
+
+
+def render_batch(views, mode: int, cfg: RasterCfg, ws: Workspace, stream=None):
+    """gsc_render_batch.  views: sequence of dicts with params (N x 16), cam,
+    and image (forward) / dL_dimage + grads (backward) tensors."""
+    arr = (View * len(views))()
+    for i, v in enumerate(views):
+        p = v["params"]
+        _need(p, "params")
+        c = v["cam"] if isinstance(v["cam"], Camera) else camera(v["cam"])
+        arr[i].params = p.data_ptr()
+        arr[i].N = p.numel() // 16
+        arr[i].cam = c
+        npx = 3 * c.width * c.height
+        if mode & BATCH_FWD:
+            _need(v["image"], "image", npx)
+            arr[i].image = v["image"].data_ptr()
+        if mode & BATCH_BWD:
+            _need(v["dL_dimage"], "dL_dimage", npx)
+            _need(v["grads"], "grads", p.numel())
+            arr[i].dL_dimage = v["dL_dimage"].data_ptr()
+            arr[i].grads = v["grads"].data_ptr()
+    _check(lib().gsc_render_batch(arr, len(views), mode, C.byref(cfg), ws.handle, _stream(stream)))
 
 
 def loss(kind: int, pred: torch.Tensor, target: torch.Tensor, ws: Workspace, crop=None,

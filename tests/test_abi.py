@@ -43,7 +43,7 @@ def test_workspace_size_grows_with_limits(L):
     from paper_2507_19718_gb300 import gsc
     def size(*a):
         n = C.c_size_t()
-        assert L.gsc_workspace_size(*a, None, C.byref(n)) == 0
+        assert L.gsc_workspace_size(*a, 1, None, C.byref(n)) == 0
         return n.value
     a = size(1024, 100000, 128, 128)
     b = size(2048, 100000, 128, 128)
@@ -53,7 +53,11 @@ def test_workspace_size_grows_with_limits(L):
     # 4 arrays of 4-byte (key, value) per pair
     assert c - a >= 100000 * 16 - 4 * 256
     n = C.c_size_t()
-    assert L.gsc_workspace_size(-1, 10, 8, 8, None, C.byref(n)) == gsc.GSC_ERR_INVALID_ARG
+    assert L.gsc_workspace_size(-1, 10, 8, 8, 1, None, C.byref(n)) == gsc.GSC_ERR_INVALID_ARG
+    assert L.gsc_workspace_size(10, 10, 8, 8, 33, None, C.byref(n)) == gsc.GSC_ERR_INVALID_ARG
+    n4 = C.c_size_t()
+    assert L.gsc_workspace_size(1024, 100000, 128, 128, 4, None, C.byref(n4)) == 0
+    assert n4.value > a
 
 
 def test_host_side_validation(L):
@@ -78,9 +82,14 @@ def test_host_side_validation(L):
     assert L.gsc_scene_destroy(h) == 0
     # workspace: unaligned buffer / too small
     w = C.c_void_p()
-    assert L.gsc_workspace_create(C.c_void_p(0x1001), 1 << 30, 16, 16, 8, 8, None, C.byref(w)) == \
+    assert L.gsc_workspace_create(C.c_void_p(0x1001), 1 << 30, 16, 16, 8, 8, 1, None, C.byref(w)) == \
         gsc.GSC_ERR_INVALID_ARG
-    assert L.gsc_workspace_create(C.c_void_p(0x1000), 16, 16, 16, 8, 8, None, C.byref(w)) == gsc.GSC_ERR_OOM
+    assert L.gsc_workspace_create(C.c_void_p(0x1000), 16, 16, 16, 8, 8, 1, None, C.byref(w)) == gsc.GSC_ERR_OOM
+    # batch: too many views, bad mode
+    views = (gsc.View * 2)()
+    cfg0 = gsc.raster_cfg()
+    assert L.gsc_render_batch(views, 33, 1, C.byref(cfg0), None, None) == gsc.GSC_ERR_INVALID_ARG
+    assert L.gsc_render_batch(views, 2, 4, C.byref(cfg0), None, None) == gsc.GSC_ERR_INVALID_ARG
     # render: bad tile shape, then NULL workspace
     cam = gsc.Camera()
     cam.fx = cam.fy = 100.0

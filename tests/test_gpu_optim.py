@@ -59,3 +59,21 @@ def test_adamw_matches_oracle(gpu, orc):
     assert float(G.abs().max()) == 0.0
     frozen = np.tile(lr == 0, n)
     np.testing.assert_array_equal(P.cpu().numpy().reshape(-1)[frozen], p.reshape(-1)[frozen])
+
+
+@pytest.mark.parametrize("crop", [None, (13, 7, 200, 91), (0, 0, 9, 6)])
+def test_l1ssim_loss_matches_oracle(gpu, orc, crop):
+    rng = np.random.default_rng(21)
+    tgt = synth.smooth_noisy_image(3, 120, 257, 5)
+    pred = np.clip(tgt + rng.normal(0, 0.1, tgt.shape), 0, None).astype(np.float32)
+    ws = gpu.Workspace(16, 16, 257, 120)
+    val, grad = gpu.loss(gpu.LOSS_L1_SSIM, _t(pred), _t(tgt), ws, crop=crop)
+    ref, rgrad, _ = orc.loss_l1ssim(pred, tgt, crop=crop)
+    assert float(val) == pytest.approx(ref, rel=2e-5)
+    g = grad.cpu().numpy()
+    # the SSIM part sums 121-tap window moments in FP32 (variance = E[x^2] - mu^2)
+    np.testing.assert_allclose(g, rgrad, rtol=1e-3, atol=1e-3 * np.abs(rgrad).max())
+    if crop is not None:
+        outside = np.ones_like(g, bool)
+        outside[:, crop[1]:crop[1] + crop[3], crop[0]:crop[0] + crop[2]] = False
+        assert np.all(g[outside] == 0)
