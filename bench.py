@@ -317,7 +317,105 @@ def run_ours(args, world, rank, local):
                 "note": "host-timed frames through the public API, the tracer's device time taken out",
                 "h2d_bytes_per_step": 84, "d2h_bytes_per_step": 3 * WIDTH * HEIGHT * 4 + LEVELS * 4},
     }
-    return result
+    return result, loop.cfg
+
+
+# ------------------------------------------------------------------ batched and served workloads
+
+def run_batched_bench(args, cfg_tuned):
+    """32 views of uneven resolution over 4 scenes (100k/250k/500k/1M
+    Gaussians): forward + HDR loss + backward replayed from one CUDA graph,
+    against the same work one view per call."""
+    import torch
+    from paper_2507_19718_gb300 import batched, gsc, synth
+    sizes = (100_000, 250_000, 500_000, 1_000_000)
+    scenes = [torch.from_numpy(synth.gaussians(n, synth.BASE_SEED + 50 + k)).cuda() for k, n in enumerate(sizes)]
+    views = batched.uneven_views(32, 4, synth.BASE_SEED + 60)
+    step = batched.BatchedStep(scenes, views, cfg_tuned)
+    step.capture()
+    s = torch.cuda.current_stream()
+    for _ in range(3):
+        step.replay()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        step.replay()
+    e1.record(s)
+    torch.cuda.synchronize()
+    step.ws.status()
+    graph_ms = e0.elapsed_time(e1) / reps
+    plain_ws = gsc.Workspace(max(sizes), int(max(sizes) * 24), 1920, 1080)
+    step.plain_step(plain_ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0.record(s)
+    for _ in range(reps):
+        step.plain_step(plain_ws)
+    e1.record(s)
+    torch.cuda.synchronize()
+    plain_wall = (time.perf_counter() - t0) * 1e3 / reps
+    plain_ms = e0.elapsed_time(e1) / reps
+    plain_ws.status()
+    px = sum(v["cam"].width * v["cam"].height for v in step.views)
+    del step, plain_ws
+    torch.cuda.empty_cache()
+    return {"workload": "32 views (256^2 / 640x480 / 1280x720 / 1920x1080, seeded) over 4 scenes of "
+                        "100k/250k/500k/1M Gaussians: render + HDR loss + backward", "views": 32,
+            "pixels": px, "graph_ms_per_step": round(graph_ms, 3), "plain_ms_per_step": round(plain_ms, 3),
+            "plain_host_ms_per_step": round(plain_wall, 3), "speedup_vs_plain": round(plain_ms / graph_ms, 3)}
+
+
+def run_served_bench(args, cfg_tuned):
+    """Eight resident 256^3 scenes with 200k..1M Gaussians (3 levels), Poisson
+    arrivals at 200 requests/s: 90% view requests, 10% transfer-function
+    changes (16 retraining frames).  Continuous batching against the plain
+    one-view-per-call path on the same trace."""
+    import copy
+    import torch
+    from paper_2507_19718_gb300 import serve, synth
+    scenes_np = serve.frame_scenes(8)
+    sizes = [200_000 + k * 800_000 // 7 for k in range(8)]
+    scenes = [serve.ResidentScene(sc, synth.level_sizes(n, LEVELS), seed=synth.BASE_SEED + 3000 + 10 * k)
+              for k, (sc, n) in enumerate(zip(scenes_np, sizes))]
+    snap = [[(L.params.clone(), L.m.clone(), L.v.clone()) for L in sc.levels] for sc in scenes]
+
+    def reset():
+        for sc, sn, desc in zip(scenes, snap, scenes_np):
+            for L, (p, m, v) in zip(sc.levels, sn):
+                L.params.copy_(p)
+                L.m.copy_(m)
+                L.v.copy_(v)
+            sc.handle.set_tf(desc.tf_pos, desc.tf_rgba)
+            sc.adam_step = sc.static_frames = sc.retrain_left = sc.frames_trained = 0
+        torch.cuda.synchronize()
+
+    srv = serve.Server(scenes, cfg_tuned)
+    warm = serve.poisson_trace(200.0, 0.5, 8, seed=synth.BASE_SEED + 70)
+    srv.run_batched(copy.deepcopy(warm))
+    srv.run_plain(copy.deepcopy(warm))
+    trace = serve.poisson_trace(200.0, args.serve_seconds, 8, seed=synth.BASE_SEED + 71)
+    out = {"workload": f"8 resident scenes (256^3, 200k..1M Gaussians x 3 levels), Poisson 200 req/s for "
+                       f"{args.serve_seconds:g} s, 90% views (256^2..1080p), 10% TF changes (16 retraining "
+                       f"frames at 320x240)", "requests": len(trace),
+           "hbm_budget_gb": round(srv.budget / 1e9, 1)}
+    for mode in ("batched", "plain"):
+        reset()
+        tr = copy.deepcopy(trace)
+        (srv.run_batched if mode == "batched" else srv.run_plain)(tr)
+        lat = serve.latency_stats(tr, "view")
+        tfl = serve.latency_stats(tr, "tf")
+        n_views = lat.get("n", 0)
+        out[mode] = {"p50_ms": round(lat.get("p50_ms", float("nan")), 3),
+                     "p99_ms": round(lat.get("p99_ms", float("nan")), 3),
+                     "frames_per_s": round(n_views / srv.stats["wall_s"], 1),
+                     "tf_retrain_p50_ms": round(tfl.get("p50_ms", float("nan")), 1),
+                     "mean_views_per_batch": round(srv.stats["mean_views_per_batch"], 2),
+                     "wall_s": round(srv.stats["wall_s"], 2)}
+    del srv, scenes, snap
+    torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------------ oracle (CPU) arm
@@ -393,6 +491,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -406,7 +507,13 @@ def main():
             import torch.distributed as dist
             dist.destroy_process_group()
         return
-    res = run_ours(args, world, rank, local)
+    res, cfg = run_ours(args, world, rank, local)
+    import torch
+    torch.cuda.empty_cache()
+    if not args.no_batched:
+        res["batched"] = run_batched_bench(args, cfg)
+    if not args.no_served:
+        res["served"] = run_served_bench(args, cfg)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             ms, sample = oracle_sample()
