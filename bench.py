@@ -45,17 +45,23 @@ FALLBACK_HBM_GBS = 6800.0
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
-def workload_config(tuned=None):
+def _launch_cfg(t):
+    return {"tile": list(t.tile), "list_capacity": t.list_capacity, "bin": t.bin_size, "pixels_per_thread": t.ppt}
+
+
+def workload_config(tuned_fwd=None, tuned_bwd=None):
     from paper_2507_19718_gb300 import synth
     sizes = synth.level_sizes(TOTAL_GAUSSIANS, LEVELS)
-    tile, cap, b, q = (tuned.tile, tuned.list_capacity, tuned.bin_size, tuned.ppt) if tuned else ((16, 16), 512, 128, 1)
     return {
         "workload": "1080p GSCache frame: trace 1spp/8 bounces -> 3 target buffers; 3 cache levels "
                     "(1M Gaussians) render + HDR loss + backward + AdamW",
         "width": WIDTH, "height": HEIGHT, "gaussians": TOTAL_GAUSSIANS, "levels": sizes, "spp": SPP,
         "max_bounces": BOUNCES, "volume": "256^3 fp32: 64 blobs + 4-octave fBm, 8-point TF",
-        "lights": "directional 3.0 + environment 0.3", "tile": list(tile), "list_capacity": cap, "bin": b, "pixels_per_thread": q,
-        "autotuned": tuned is not None,
+        "lights": "directional 3.0 + environment 0.3",
+        "levels_fused": True,
+        "forward_launch": _launch_cfg(tuned_fwd) if tuned_fwd else None,
+        "backward_launch": _launch_cfg(tuned_bwd) if tuned_bwd else None,
+        "autotuned": tuned_fwd is not None,
         "camera": f"orbit r=2.2, fov_y 45 deg, {ORBIT_DEG_PER_FRAME} deg/frame",
         "l2": "inputs larger than L2 (params+moments 256 MB, pair buffers GBs)", "parallelism": "replicas",
     }
@@ -167,10 +173,19 @@ def phase_algorithmic(phase, c, n_gauss_calls, n_pixels_calls, frames):
     for the compositing kernels; the per-unit figures are stated in the
     design notes."""
     M = c["pairs_sum"]
+    # FP32 flops with an FMA counted as two (the convention of the peak):
+    # falloff test per evaluated pair 10 (two offsets, three products of the
+    # quadratic form, two of them fused with the sum); per composited pair
+    # 10 (alpha, 1 - alpha, T update, weight, three colour FMAs); re-walk per
+    # composited pair 3; back to front per contributing pair 34 (alpha,
+    # 1 - alpha, reciprocal, T, weight, three colour-gradient FMAs,
+    # dL/dC . c, dL/dalpha, the behind-colour term, the opacity term and the
+    # five geometric sums).  exp runs on the SFU and is not counted.
     if phase == "render":
-        return "flop", 10.0 * c["eval_fwd"] + 13.0 * c["composited_fwd"]
+        return "flop", 10.0 * c["eval_fwd"] + 10.0 * c["composited_fwd"]
     if phase == "render_bwd":
-        return "flop", 10.0 * c["eval_rewalk"] + 40.0 * c["eval_back"]
+        return "flop", (10.0 * (c["eval_rewalk"] + c["eval_back"]) + 3.0 * c["composited_rewalk"]
+                        + 34.0 * c["hits_back"])
     if phase == "tile_sort":
         return "byte", 2 * 20.0 * M   # pairs are (bin, Gaussian); 2 passes of 8-bit digits
     if phase == "depth_sort":
@@ -210,11 +225,15 @@ def run_ours(args, world, rank, local):
                      seed=synth.BASE_SEED + 17 * rank, tile=(16, 16), list_capacity=512, device=dev, bin_size=64)
     cams = [gsc.camera(synth.orbit_camera(WIDTH, HEIGHT, ORBIT_DEG_PER_FRAME * f))
             for f in range(args.warmup + args.steps + 1)]
-    # pick the launch configuration on this GPU (results do not depend on it)
-    best, _ = autotune.autotune([L.params for L in loop.levels], cams[0], loop.ws,
-                                cands=list(autotune.candidates(TUNE_TILES, TUNE_BINS, TUNE_CAPS, TUNE_PPT)), reps=1)
-    loop.cfg = best.cfg()
-    cfg = workload_config(best)
+    # pick the launch configurations on this GPU, separately for the forward
+    # and the backward batch (results do not depend on them)
+    cands = list(autotune.candidates(TUNE_TILES, TUNE_BINS, TUNE_CAPS, TUNE_PPT))
+    lv = [L.params for L in loop.levels]
+    best_f, _ = autotune.autotune(lv, cams[0], loop.ws, cands=cands, reps=1, fused=True, backward=False)
+    best_b, _ = autotune.autotune(lv, cams[0], loop.ws, cands=cands, reps=1, fused=True, forward=False)
+    loop.cfg = best_f.cfg()
+    loop.cfg_bwd = best_b.cfg()
+    cfg = workload_config(best_f, best_b)
     stream = torch.cuda.current_stream()
 
     # warm-up (also sizes nothing: the pair capacity is fixed)
@@ -317,7 +336,7 @@ def run_ours(args, world, rank, local):
                 "note": "host-timed frames through the public API, the tracer's device time taken out",
                 "h2d_bytes_per_step": 84, "d2h_bytes_per_step": 3 * WIDTH * HEIGHT * 4 + LEVELS * 4},
     }
-    return result, loop.cfg
+    return result, loop.cfg_bwd or loop.cfg
 
 
 # ------------------------------------------------------------------ batched and served workloads

@@ -199,12 +199,13 @@ gsc_status gsc_workspace_destroy(gsc_workspace* ws);
 gsc_status gsc_workspace_status(gsc_workspace* ws, gsc_stream_t stream, int64_t* pairs_needed);
 
 /* Work counters of the workspace since the last call, then reset (after
- * synchronising `stream`).  out[0..7]: pairs of the last binning, largest
- * pair count, pairs evaluated / composited by the forward, pairs evaluated
- * by the backward's forward re-walk, pairs processed back to front, the sum
- * of the pair counts of all binnings, and the number of binnings.  n:
- * entries wanted (<= 8). */
-#define GSC_COUNTER_WORDS 8
+ * synchronising `stream`).  out[0..9]: pairs of the last binning, largest
+ * pair count, (pixel, Gaussian) pairs evaluated / composited by the
+ * forward, pairs evaluated by the backward's forward re-walk, pairs
+ * evaluated back to front, the sum of the pair counts of all binnings, the
+ * number of binnings, pairs composited by the re-walk, and pairs that
+ * contributed gradient terms back to front.  n: entries wanted (<= 10). */
+#define GSC_COUNTER_WORDS 10
 gsc_status gsc_workspace_counters(gsc_workspace* ws, gsc_stream_t stream, int64_t* out, int32_t n);
 
 /* ------------------------------------------------------------------ */

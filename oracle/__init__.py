@@ -12,6 +12,8 @@ Passages followed (Bauer et al., "GSCache"):
                      Sec. 3.4 Eq. 2, Sec. 3.5 (intermediate path buffers)
   project / render   Sec. 3.1 (Gaussian splatting of each cache level)
   render_backward    Sec. 3.5 ("inverse splatting step")
+  FrozenLists        the same render with its threshold decisions held fixed,
+                     for central differences of the backward at 1M Gaussians
   loss_hdr           Sec. 3.6 "Loss"
   adamw              Sec. 3.6 "Regularization"; lr_scale Eq. 4
   cache_bytes        Table 3
@@ -73,6 +75,13 @@ def lib():
             L.orc_render.restype = i32
             L.orc_render_backward.argtypes = [i64, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, i32]
             L.orc_render_backward.restype = i32
+            L.orc_render_lists.argtypes = [i64, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, i32]
+            L.orc_render_lists.restype = i32
+            L.orc_frozen_fd.argtypes = [i64, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, i32, vp, vp, f64, vp,
+                                        i32]
+            L.orc_frozen_fd.restype = i32
+            L.orc_render_frozen.argtypes = [i64, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, i32]
+            L.orc_render_frozen.restype = i32
             L.orc_loss_hdr.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp]
             L.orc_loss_hdr.restype = f64
             L.orc_loss_l1ssim.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp]
@@ -220,6 +229,53 @@ def render_backward(params, cam, dL_dimage, cfg=None, window=None, nthreads: int
     if rc:
         raise MemoryError("orc_render_backward")
     return grads, g2d
+
+
+class FrozenLists:
+    """Per-pixel composited lists of a window (Gaussian ids in compositing
+    order and their alpha_max clamp state), recorded at given parameters."""
+
+    def __init__(self, params, cam, cfg=None, window=None, nthreads: int = 0):
+        params = _c(params, np.float32)
+        self.window = tuple(window) if window is not None else (0, 0, cam.width, cam.height)
+        x0, y0, w, h = self.window
+        _, _, ncon, _ = render(params, cam, cfg, self.window, nthreads, grad_margins=True)
+        self.offsets = np.zeros(w * h + 1, np.int64)
+        np.cumsum(ncon.reshape(-1), out=self.offsets[1:])
+        n = int(self.offsets[-1])
+        self.g = np.zeros(max(n, 1), np.int64)
+        self.clamped = np.zeros(max(n, 1), np.uint8)
+        rc = lib().orc_render_lists(len(params), _p(params), _p(cam.packed()), _p(_cfg(cfg)), x0, y0, w, h,
+                                    _p(self.offsets), _p(self.g), _p(self.clamped), _threads(nthreads))
+        if rc:
+            raise RuntimeError(f"orc_render_lists: {rc}")
+        self.cam, self.cfg = cam, cfg
+
+    def render(self, params, nthreads: int = 0) -> np.ndarray:
+        """The window rendered over the frozen lists (3, h, w)."""
+        params = _c(params, np.float32)
+        x0, y0, w, h = self.window
+        img = np.zeros((3, h, w), np.float64)
+        rc = lib().orc_render_frozen(len(params), _p(params), _p(self.cam.packed()), _p(_cfg(self.cfg)), x0, y0, w,
+                                     h, _p(self.offsets), _p(self.g), _p(self.clamped), _p(img), _threads(nthreads))
+        if rc:
+            raise MemoryError("orc_render_frozen")
+        return img
+
+    def fd(self, params, v, gauss, slots, h: float = 1e-3, nthreads: int = 0) -> np.ndarray:
+        """Central differences of sum(v * frozen render) w.r.t. params[gauss[i], slots[i]]."""
+        params = _c(params, np.float32)
+        x0, y0, w, hh = self.window
+        v = _c(v, np.float64)
+        assert v.shape == (3, hh, w)
+        gauss, slots = _c(gauss, np.int64), _c(slots, np.int32)
+        out = np.zeros(len(gauss), np.float64)
+        rc = lib().orc_frozen_fd(len(params), _p(params), _p(self.cam.packed()), _p(_cfg(self.cfg)), x0, y0, w, hh,
+                                 _p(self.offsets), _p(self.g), _p(self.clamped), _p(v), len(gauss), _p(gauss),
+                                 _p(slots), float(h), _p(out), _threads(nthreads))
+        if rc:
+            raise MemoryError("orc_frozen_fd")
+        return out
 
 
 # ---------------------------------------------------------------- losses, optimiser

@@ -671,6 +671,157 @@ int orc_render_backward(int64_t N, const float* params, const float* cam, const 
 }
 
 /* ------------------------------------------------------------------------ */
+/* frozen decisions: finite differences of the backward at scale             */
+
+/*
+ * The analytic backward differentiates the render with every threshold
+ * decision held fixed: which terms a pixel composites, in which order, where
+ * it stops, and which alphas sit at the alpha_max clamp.  A central
+ * difference of the plain render itself crosses some decision somewhere once
+ * a Gaussian covers thousands of pixels, so the large-scale pin differences
+ * the render with those decisions frozen instead.
+ *
+ * orc_render_lists: for every pixel of the window, the ordered composited
+ * Gaussians and their clamp state, written at offsets[p] (offsets: h w + 1
+ * prefix sums of the per-pixel term counts that orc_render reports).
+ * Returns 0, or 3 if a pixel's term count disagrees with its offsets.
+ */
+int orc_render_lists(int64_t N, const float* params, const float* cam, const double* cfg, int x0, int y0, int w,
+                     int h, const int64_t* offsets, int64_t* list_g, uint8_t* list_clamped, int nthreads) {
+    rcam_t c;
+    rcam_setup(&c, cam);
+    proj_t* pr = (proj_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(proj_t));
+    int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    if (!pr || !order) { free(pr); free(order); return 2; }
+    int64_t V = project_sorted(N, params, &c, cfg, pr, order, nthreads);
+    int bad = 0;
+#pragma omp parallel num_threads(nthreads)
+    {
+        int64_t cap = 4096;
+        term_t* terms = (term_t*)malloc(sizeof(term_t) * (size_t)cap);
+#pragma omp for schedule(dynamic, 1)
+        for (int jj = 0; jj < h; ++jj) {
+            for (int ii = 0; ii < w; ++ii) {
+                long p = (long)jj * w + ii;
+                int64_t want = offsets[p + 1] - offsets[p];
+                if (want > cap) {
+                    cap = want;
+                    terms = (term_t*)realloc(terms, sizeof(term_t) * (size_t)cap);
+                }
+                double C[3], T;
+                int marg;
+                int64_t n = walk_pixel(pr, order, V, cfg, x0 + ii + 0.5, y0 + jj + 0.5, C, &T, &marg, terms, cap, 1);
+                if (n != want) {
+#pragma omp atomic write
+                    bad = 1;
+                    continue;
+                }
+                for (int64_t k = 0; k < n; ++k) {
+                    list_g[offsets[p] + k] = terms[k].g;
+                    list_clamped[offsets[p] + k] = (uint8_t)terms[k].clamped;
+                }
+            }
+        }
+        free(terms);
+    }
+    free(pr);
+    free(order);
+    return bad ? 3 : 0;
+}
+
+/* colour of one pixel over its frozen list; Gaussian `gsub` (or -1) uses
+ * the projection *sub instead of its own */
+static void frozen_pixel(const proj_t* pr, const int64_t* lg, const uint8_t* lc, int64_t n, const double* cfg,
+                         double px, double py, int64_t gsub, const proj_t* sub, double C[3]) {
+    double T = 1.0;
+    C[0] = C[1] = C[2] = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+        const proj_t* p = lg[k] == gsub ? sub : &pr[lg[k]];
+        double dx = px - p->mx, dy = py - p->my;
+        double power = -0.5 * (p->a * dx * dx + p->c * dy * dy) - p->b * dx * dy;
+        double alpha = lc[k] ? cfg[0] : p->op * exp(power);
+        for (int ch = 0; ch < 3; ++ch) C[ch] += p->col[ch] * alpha * T;
+        T *= 1.0 - alpha;
+    }
+}
+
+/*
+ * Central differences of F(theta) = sum over the window of v . C(theta)
+ * (v: 3 x h x w), decisions frozen as recorded by orc_render_lists: for
+ * each requested (Gaussian fd_g[i], packed slot fd_slot[i]) the parameter
+ * is stepped to the FP32 values nearest theta +- hstep, and out[i] =
+ * (F+ - F-) / (actual step).  Only pixels whose list holds the Gaussian
+ * change, so only those are evaluated.  The gradient of F is what the
+ * backward computes when handed v as dL/dimage.
+ */
+int orc_frozen_fd(int64_t N, const float* params, const float* cam, const double* cfg, int x0, int y0, int w, int h,
+                  const int64_t* offsets, const int64_t* list_g, const uint8_t* list_clamped, const double* v,
+                  int32_t n_fd, const int64_t* fd_g, const int32_t* fd_slot, double hstep, double* out,
+                  int nthreads) {
+    rcam_t c;
+    rcam_setup(&c, cam);
+    proj_t* pr = (proj_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(proj_t));
+    if (!pr) return 2;
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int64_t g = 0; g < N; ++g) project_one(params + 16 * g, &c, cfg, &pr[g], NULL);
+    long WH = (long)w * h;
+    for (int32_t i = 0; i < n_fd; ++i) {
+        int64_t g = fd_g[i];
+        float pp[16], pm[16];
+        memcpy(pp, params + 16 * g, sizeof pp);
+        memcpy(pm, params + 16 * g, sizeof pm);
+        pp[fd_slot[i]] = (float)((double)pp[fd_slot[i]] + hstep);
+        pm[fd_slot[i]] = (float)((double)pm[fd_slot[i]] - hstep);
+        double step = (double)pp[fd_slot[i]] - (double)pm[fd_slot[i]];
+        proj_t plus, minus;
+        memset(&plus, 0, sizeof plus);
+        memset(&minus, 0, sizeof minus);
+        project_one(pp, &c, cfg, &plus, NULL);
+        project_one(pm, &c, cfg, &minus, NULL);
+        double acc = 0.0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : acc) num_threads(nthreads)
+        for (long p = 0; p < WH; ++p) {
+            int64_t o = offsets[p], n = offsets[p + 1] - offsets[p];
+            int has = 0;
+            for (int64_t k = 0; k < n && !has; ++k) has = list_g[o + k] == g;
+            if (!has) continue;
+            double px = x0 + (p % w) + 0.5, py = y0 + (p / w) + 0.5, Cp[3], Cm[3];
+            frozen_pixel(pr, list_g + o, list_clamped + o, n, cfg, px, py, g, &plus, Cp);
+            frozen_pixel(pr, list_g + o, list_clamped + o, n, cfg, px, py, g, &minus, Cm);
+            for (int ch = 0; ch < 3; ++ch) acc += v[ch * WH + p] * (Cp[ch] - Cm[ch]);
+        }
+        out[i] = acc / step;
+    }
+    free(pr);
+    return 0;
+}
+
+/*
+ * The frozen-decision render itself (for the check that it reproduces
+ * orc_render at the recorded parameters).  image: 3 x h x w.
+ */
+int orc_render_frozen(int64_t N, const float* params, const float* cam, const double* cfg, int x0, int y0, int w,
+                      int h, const int64_t* offsets, const int64_t* list_g, const uint8_t* list_clamped,
+                      double* image, int nthreads) {
+    rcam_t c;
+    rcam_setup(&c, cam);
+    proj_t* pr = (proj_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(proj_t));
+    if (!pr) return 2;
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int64_t g = 0; g < N; ++g) project_one(params + 16 * g, &c, cfg, &pr[g], NULL);
+    long WH = (long)w * h;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+    for (long p = 0; p < WH; ++p) {
+        double C[3];
+        frozen_pixel(pr, list_g + offsets[p], list_clamped + offsets[p], offsets[p + 1] - offsets[p], cfg,
+                     x0 + (p % w) + 0.5, y0 + (p / w) + 0.5, -1, NULL, C);
+        for (int ch = 0; ch < 3; ++ch) image[ch * WH + p] = C[ch];
+    }
+    free(pr);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* losses                                                                    */
 
 /*

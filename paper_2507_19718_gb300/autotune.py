@@ -41,21 +41,31 @@ def candidates(tiles=TILES, bins=BINS, caps=CAPS, ppts=PPTS):
         yield t, b, c, q
 
 
-def time_config(levels, cam, ws: gsc.Workspace, tile, bin_size, cap, ppt=1, backward=True, reps=2, stream=None):
-    """Mean ms of rendering (and differentiating) every level once."""
+def time_config(levels, cam, ws: gsc.Workspace, tile, bin_size, cap, ppt=1, backward=True, reps=2, stream=None,
+                fused=False, forward=True):
+    """Mean ms of rendering (and/or differentiating) every level once; with
+    ``fused`` all levels go through one batched call per direction."""
     c = cam if isinstance(cam, gsc.Camera) else gsc.camera(cam)
     cfg = gsc.raster_cfg(tile=tile, list_capacity=cap, bin_size=bin_size, pixels_per_thread=ppt)
     dev = levels[0].device
-    img = torch.empty((3, c.height, c.width), dtype=torch.float32, device=dev)
+    imgs = [torch.empty((3, c.height, c.width), dtype=torch.float32, device=dev) for _ in levels]
     dl = torch.full((3, c.height, c.width), 1e-3, dtype=torch.float32, device=dev)
     grads = [torch.zeros_like(p) for p in levels]
+    views = [dict(params=p, cam=c, image=im, dL_dimage=dl, grads=g) for p, im, g in zip(levels, imgs, grads)]
     s = torch.cuda.current_stream() if stream is None else stream
 
     def once():
-        for p, g in zip(levels, grads):
-            gsc.cache_render(p, c, cfg, ws, image=img, stream=s)
+        if fused:
+            if forward:
+                gsc.render_batch(views, gsc.BATCH_FWD, cfg, ws, stream=s)
             if backward:
-                gsc.cache_backward(p, c, cfg, ws, dl, g, stream=s)
+                gsc.render_batch(views, gsc.BATCH_BWD, cfg, ws, stream=s)
+            return
+        for v in views:
+            if forward:
+                gsc.cache_render(v["params"], c, cfg, ws, image=v["image"], stream=s)
+            if backward:
+                gsc.cache_backward(v["params"], c, cfg, ws, dl, v["grads"], stream=s)
 
     once()  # warm-up
     ws.status(s)
@@ -69,12 +79,15 @@ def time_config(levels, cam, ws: gsc.Workspace, tile, bin_size, cap, ppt=1, back
     return e0.elapsed_time(e1) / reps
 
 
-def autotune(levels, cam, ws: gsc.Workspace, backward=True, cands=None, reps=2, verbose=False):
-    """Fastest (tile, bin, capacity, pixels per thread) for rendering (and differentiating) the
-    given levels from `cam`.  Returns (best Trial, all trials)."""
+def autotune(levels, cam, ws: gsc.Workspace, backward=True, cands=None, reps=2, verbose=False, fused=False,
+             forward=True):
+    """Fastest (tile, bin, capacity, pixels per thread) for rendering and/or
+    differentiating the given levels from `cam`.  Returns (best Trial, all
+    trials)."""
     trials = []
     for tile, b, cap, q in (cands if cands is not None else candidates()):
-        ms = time_config(levels, cam, ws, tile, b, cap, q, backward=backward, reps=reps)
+        ms = time_config(levels, cam, ws, tile, b, cap, q, backward=backward, reps=reps, fused=fused,
+                         forward=forward)
         trials.append(Trial(tile, b, cap, q, ms))
         if verbose:
             print(f"tile {tile[0]}x{tile[1]} bin {b} cap {cap} ppt {q}: {ms:.3f} ms", flush=True)

@@ -91,7 +91,7 @@ enum : int { kStatusCode = 0, kStatusWords = 4 };
 enum : int { kCntPairs = 0, kCntPairsMax = 1, kCntTilesFwd = 2, kCntTilesBwd = 3, kCounterWords = 8 };
 // 64-bit work statistics in the workspace
 enum : int { kStEvalFwd = 0, kStCompFwd = 1, kStEvalRewalk = 2, kStEvalBack = 3, kStPairsSum = 4, kStBinnings = 5,
-             kStatWords = 8 };
+             kStCompRewalk = 6, kStHitBack = 7, kStatWords = 8 };
 
 }  // namespace gsc
 

@@ -31,6 +31,14 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// reciprocal to about one ulp, enough for the gradient arithmetic (never
+// for a compositing decision)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // FP32 view depth with a fixed operation order ((r20 x + r21 y) + r22 z) + t2;
 // it is the sort key and the near-plane test.
 __device__ __forceinline__ float view_depth(const CamDev& c, float x, float y, float z) {
@@ -498,7 +506,7 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
     float4* s1 = smem + cap;
     float4* s2 = smem + 2 * cap;
     uint32_t* hits = reinterpret_cast<uint32_t*>(smem + 3 * cap);
-    uint32_t n_eval1 = 0, n_eval2 = 0;
+    uint32_t n_eval1 = 0, n_eval2 = 0, n_comp1 = 0, n_hit2 = 0;
     __shared__ uint32_t s_tile;
     // persistent CTAs: tiles of all views are handed out by an atomic counter
     for (;;) {
@@ -594,6 +602,7 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
                     }
                     T[q] = Tn;
                     last[q] = h0 + k + 1;
+                    ++n_comp1;
                 }
             }
         }
@@ -612,9 +621,12 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
     for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(kFull, wlast, o));
 
     // ---- phase 2
-    float Sr[PPT], Sg[PPT], Sb[PPT];
+    // DS = dL/dC . S, with S the colour composited behind the current entry:
+    // dL/dalpha = T dL/dC . c - DS / (1 - alpha), and DS grows by
+    // alpha T dL/dC . c, so the three channels of S need not be kept.
+    float DS[PPT];
 #pragma unroll
-    for (int q = 0; q < PPT; ++q) Sr[q] = Sg[q] = Sb[q] = 0.f;
+    for (int q = 0; q < PPT; ++q) DS[q] = 0.f;
     int lane = threadIdx.x & 31;
     int ring_chunk = nhit ? (int)((nhit - 1) / kHitRing) : -1;  // chunk whose hits the ring holds
     for (int ch = hend ? (int)((hend - 1) / kHitRing) : -1; ch >= 0; --ch) {
@@ -662,6 +674,9 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
                 if (j >= wlast) continue;  // warp-uniform
                 float4 r0 = s0[k];
                 float4 r1 = s1[k];
+                float4 c = s2[k];
+                // per entry: sum w dx, sum w dy, sum w dx^2, sum w dx dy, sum w dy^2
+                // (w = dL/dalpha alpha), sum dL/dalpha G, red, green; blue apart
                 float v8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 float dcb = 0.f;
                 bool any = false;
@@ -673,29 +688,28 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
                     ++n_eval2;
                     if (p < r1.z) continue;
                     any = true;
+                    ++n_hit2;
                     float e = ex2_approx(p);
                     float araw = __fmul_rn(r1.y, e);
                     float alpha = fminf(rc.alpha_max, araw);
-                    float inv = 1.f / (1.f - alpha);
+                    float inv = rcp_approx(1.f - alpha);
                     T[q] = T[q] * inv;  // transmittance in front of this entry
-                    float4 c = s2[k];
                     float wgt = alpha * T[q];
-                    v8[6] += wgt * gr[q];
-                    v8[7] += wgt * gg[q];
-                    dcb += wgt * gb[q];
-                    float dal = gr[q] * (c.x * T[q] - Sr[q] * inv) + gg[q] * (c.y * T[q] - Sg[q] * inv) +
-                                gb[q] * (c.z * T[q] - Sb[q] * inv);
-                    Sr[q] = fmaf(c.x, wgt, Sr[q]);
-                    Sg[q] = fmaf(c.y, wgt, Sg[q]);
-                    Sb[q] = fmaf(c.z, wgt, Sb[q]);
+                    v8[6] = fmaf(wgt, gr[q], v8[6]);
+                    v8[7] = fmaf(wgt, gg[q], v8[7]);
+                    dcb = fmaf(wgt, gb[q], dcb);
+                    float dc = fmaf(gb[q], c.z, fmaf(gg[q], c.y, gr[q] * c.x));
+                    float dal = fmaf(T[q], dc, -inv * DS[q]);
+                    DS[q] = fmaf(wgt, dc, DS[q]);
                     if (araw < rc.alpha_max) {
-                        v8[5] += dal * e * r1.y * (1.f - r1.y);
-                        float dp = dal * alpha * kLn2;
-                        v8[2] += dp * dx * dx;
-                        v8[3] += dp * dx * dy;
-                        v8[4] += dp * dy * dy;
-                        v8[0] -= dp * (2.f * r0.z * dx + r0.w * dy);
-                        v8[1] -= dp * (r0.w * dx + 2.f * r1.x * dy);
+                        v8[5] = fmaf(dal, e, v8[5]);
+                        float w = dal * alpha;
+                        float wx = w * dx, wy = w * dy;
+                        v8[0] += wx;
+                        v8[1] += wy;
+                        v8[2] = fmaf(wx, dx, v8[2]);
+                        v8[3] = fmaf(wx, dy, v8[3]);
+                        v8[4] = fmaf(wy, dy, v8[4]);
                     }
                 }
                 if (__any_sync(kFull, any)) {
@@ -716,6 +730,8 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
     }  // tiles
     warp_count(&stats[kStEvalRewalk], n_eval1);
     warp_count(&stats[kStEvalBack], n_eval2);
+    warp_count(&stats[kStCompRewalk], n_comp1);
+    warp_count(&stats[kStHitBack], n_hit2);
 }
 
 // 2D gradients -> packed parameter gradients (+=)
@@ -738,10 +754,13 @@ __global__ void __launch_bounds__(128) k_project_bwd(const __grid_constant__ Bat
     Proj x;
     if (!project_core(p0, p1, p2, cam, rc, x)) return;
     const float* R = cam.R;
-    // conic entries from the scaled ones used by the rasterizer
-    float ga = a0.z * (-0.5f * kLog2e), gb = a0.w * (-kLog2e), gc = a1.x * (-0.5f * kLog2e);
-    // dL/dSigma2D = -Q G Q with Q = conic, G = [[ga, gb/2], [gb/2, gc]]
+    // The record holds, summed over pixels, w dx, w dy, w dx^2, w dx dy,
+    // w dy^2 with w = dL/dalpha alpha = dL/dpower (power = -d^T Q d / 2,
+    // d = pixel - mean), then dL/dalpha G and the colour terms.
     float qa = x.a, qb = x.b, qc = x.c;
+    float gmx = qa * a0.x + qb * a0.y, gmy = qb * a0.x + qc * a0.y;
+    float ga = -0.5f * a0.z, gb = -a0.w, gc = -0.5f * a1.x;
+    // dL/dSigma2D = -Q G Q with G = [[ga, gb/2], [gb/2, gc]]
     float dA = -(ga * qa * qa + gb * qa * qb + gc * qb * qb);
     float dC = -(ga * qb * qb + gb * qb * qc + gc * qc * qc);
     float dB = -(2.f * ga * qa * qb + gb * (qa * qc + qb * qb) + 2.f * gc * qb * qc);
@@ -766,15 +785,16 @@ __global__ void __launch_bounds__(128) k_project_bwd(const __grid_constant__ Bat
     float dJ12 = dT1[0] * R[6] + dT1[1] * R[7] + dT1[2] * R[8];
     float tx = x.t[0], ty = x.t[1], tz = x.t[2];
     float iz = 1.f / tz, iz2 = iz * iz, iz3 = iz2 * iz;
-    float dtx = dJ02 * (-cam.fx * iz2) + a0.x * cam.fx * iz;
-    float dty = dJ12 * (-cam.fy * iz2) + a0.y * cam.fy * iz;
+    float dtx = dJ02 * (-cam.fx * iz2) + gmx * cam.fx * iz;
+    float dty = dJ12 * (-cam.fy * iz2) + gmy * cam.fy * iz;
     float dtz = dJ00 * (-cam.fx * iz2) + dJ02 * (2.f * cam.fx * tx * iz3) + dJ11 * (-cam.fy * iz2) +
-                dJ12 * (2.f * cam.fy * ty * iz3) - a0.x * cam.fx * tx * iz2 - a0.y * cam.fy * ty * iz2;
+                dJ12 * (2.f * cam.fy * ty * iz3) - gmx * cam.fx * tx * iz2 - gmy * cam.fy * ty * iz2;
     float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0, o2 = o0, o3 = o0;
     o0.x += R[0] * dtx + R[3] * dty + R[6] * dtz;
     o0.y += R[1] * dtx + R[4] * dty + R[7] * dtz;
     o0.z += R[2] * dtx + R[5] * dty + R[8] * dtz;
-    o0.w += a1.y;
+    float op = 1.f / (1.f + expf(-p0.w));
+    o0.w += a1.y * op * (1.f - op);  // alpha = sigmoid(logit) G
     // Sigma = M M^T: dL/dM = (G + G^T) M with G = dA T0 T0^T + dB T0 T1^T + dC T1 T1^T
     float Gs[9];
 #pragma unroll

@@ -17,13 +17,21 @@ from . import gsc, synth
 
 
 class CacheLevel:
-    """Parameters, gradients and Adam moments of one cache level (N x 16 FP32)."""
+    """Parameters, gradients and Adam moments of one cache level (N x 16 FP32).
+    With ``store`` (four tensors of a larger parameter set and the row
+    offset) the level's tensors are views into it."""
 
-    def __init__(self, params: np.ndarray, device="cuda"):
-        self.params = torch.from_numpy(np.ascontiguousarray(params, np.float32)).to(device)
-        self.grads = torch.zeros_like(self.params)
-        self.m = torch.zeros_like(self.params)
-        self.v = torch.zeros_like(self.params)
+    def __init__(self, params: np.ndarray, device="cuda", store=None):
+        if store is None:
+            self.params = torch.from_numpy(np.ascontiguousarray(params, np.float32)).to(device)
+            self.grads = torch.zeros_like(self.params)
+            self.m = torch.zeros_like(self.params)
+            self.v = torch.zeros_like(self.params)
+        else:
+            (P, G, M, V), r0 = store
+            r1 = r0 + params.shape[0]
+            self.params, self.grads, self.m, self.v = P[r0:r1], G[r0:r1], M[r0:r1], V[r0:r1]
+            self.params.copy_(torch.from_numpy(np.ascontiguousarray(params, np.float32)))
 
     @property
     def n(self) -> int:
@@ -31,32 +39,47 @@ class CacheLevel:
 
 
 class FrameLoop:
-    """Path-trace targets, then train and render a multi-level cache, per frame."""
+    """Path-trace targets, then train and render a multi-level cache, per frame.
+
+    ``fused`` (default) renders and differentiates all K levels as one batch
+    (one binning and one persistent launch per direction over all levels,
+    Sec. 5's joint rasterisation of the level sets) and steps all levels with
+    one AdamW launch over their contiguous parameter store; otherwise every
+    level goes through its own calls."""
 
     def __init__(self, scene: synth.Scene, level_sizes, width: int, height: int, spp: int = 1,
                  max_bounces: int = 8, seed: int = synth.BASE_SEED, tile=(16, 16), list_capacity: int = 256,
                  max_pairs: int | None = None, weight_decay: float = 0.01, lr=None, device: str = "cuda",
-                 gaussian_seed: int | None = None, C_term: float = 0.0, bin_size: int = 0):
+                 gaussian_seed: int | None = None, C_term: float = 0.0, bin_size: int = 0, fused: bool = True):
         self.width, self.height = width, height
         self.spp, self.max_bounces, self.seed = spp, max_bounces, seed
         self.K = len(level_sizes)
         self.C_term = C_term
+        self.fused = fused
         self.scene = gsc.Scene.from_synth(scene, device)
         gs = seed + 1000 if gaussian_seed is None else gaussian_seed
-        self.levels = [CacheLevel(synth.gaussians(n, gs + k), device) for k, n in enumerate(level_sizes)]
-        nmax = max(level_sizes)
+        total = int(sum(level_sizes))
+        f32 = dict(dtype=torch.float32, device=device)
+        # one contiguous parameter store; level k owns rows [off_k, off_k + N_k)
+        self.store = tuple(torch.zeros((total, 16), **f32) for _ in range(4))
+        self.levels = []
+        off = 0
+        for k, n in enumerate(level_sizes):
+            self.levels.append(CacheLevel(synth.gaussians(n, gs + k), device, store=(self.store, off)))
+            off += n
+        n_ws = total if fused else max(level_sizes)
         if max_pairs is None:
             # log-normal scales (N(-3, 0.5)) make the large Gaussians dominate:
             # at 1080p a Gaussian's support spans ~300 px, i.e. ~33 bins of
             # 64 px; keep headroom and scale with the pixel count and bin area
             b = bin_size or 64
             per = 96.0 * (width * height) / (1920 * 1080) * (64.0 / b) ** 2
-            max_pairs = int(min((1 << 31) - 1, max(1 << 16, nmax * max(per, 4.0))))
-        self.ws = gsc.Workspace(nmax, max_pairs, width, height, device)
+            max_pairs = int(min((1 << 31) - 1, max(1 << 16, n_ws * max(per, 4.0))))
+        self.ws = gsc.Workspace(n_ws, max_pairs, width, height, device, max_views=self.K if fused else 1)
         self.cfg = gsc.raster_cfg(tile=tile, list_capacity=list_capacity, bin_size=bin_size)
+        self.cfg_bwd = None  # backward launch configuration, if different from cfg
         self.lr = np.asarray(gsc.PAPER_LR if lr is None else lr, np.float32)
         self.weight_decay = weight_decay
-        f32 = dict(dtype=torch.float32, device=device)
         self.targets = torch.zeros((self.K, 3, height, width), **f32)
         self.image = torch.zeros((3, height, width), **f32)
         self.renders = torch.zeros((self.K, 3, height, width), **f32)
@@ -68,16 +91,16 @@ class FrameLoop:
 
     def snapshot(self):
         """Copy of the training state (parameters, moments, step, schedule)."""
-        return ([(L.params.clone(), L.m.clone(), L.v.clone()) for L in self.levels], self.adam_step,
-                self.static_frames, self._last_pose)
+        P, _, M, V = self.store
+        return (P.clone(), M.clone(), V.clone()), self.adam_step, self.static_frames, self._last_pose
 
     def restore(self, snap):
-        levels, self.adam_step, self.static_frames, self._last_pose = snap
-        for L, (p, m, v) in zip(self.levels, levels):
-            L.params.copy_(p)
-            L.m.copy_(m)
-            L.v.copy_(v)
-            L.grads.zero_()
+        (p, m, v), self.adam_step, self.static_frames, self._last_pose = snap
+        P, G, M, V = self.store
+        P.copy_(p)
+        M.copy_(m)
+        V.copy_(v)
+        G.zero_()
 
     def _schedule(self, c: gsc.Camera) -> float:
         """Eq. 4: frames the viewport has been unchanged (pose compared bit for bit)."""
@@ -92,16 +115,29 @@ class FrameLoop:
                   cache=cache, targets=self.targets, image=self.image, stream=stream)
 
     def render_levels(self, c: gsc.Camera, stream=None):
+        if self.fused:
+            views = [dict(params=L.params, cam=c, image=self.renders[k]) for k, L in enumerate(self.levels)]
+            gsc.render_batch(views, gsc.BATCH_FWD, self.cfg, self.ws, stream=stream)
+            return
         for k, L in enumerate(self.levels):
             gsc.cache_render(L.params, c, self.cfg, self.ws, image=self.renders[k], stream=stream)
 
     def train_levels(self, c: gsc.Camera, lr_scale: float, stream=None):
         self.adam_step += 1
         adam = gsc.adam_params(self.lr, weight_decay=self.weight_decay, lr_scale=lr_scale, step=self.adam_step)
-        for k, L in enumerate(self.levels):
+        cfg_b = self.cfg_bwd or self.cfg
+        for k in range(self.K):
             gsc.loss(gsc.LOSS_HDR, self.renders[k], self.targets[k], self.ws, dL_dpred=self.dL[k],
                      loss_out=self.losses[k], stream=stream)
-            gsc.cache_backward(L.params, c, self.cfg, self.ws, self.dL[k], L.grads, stream=stream)
+        if self.fused:
+            views = [dict(params=L.params, cam=c, dL_dimage=self.dL[k], grads=L.grads)
+                     for k, L in enumerate(self.levels)]
+            gsc.render_batch(views, gsc.BATCH_BWD, cfg_b, self.ws, stream=stream)
+            # every level has the same per-slot rates and schedule: one launch
+            gsc.cache_step(*self.store, adam, stream=stream)
+            return
+        for k, L in enumerate(self.levels):
+            gsc.cache_backward(L.params, c, cfg_b, self.ws, self.dL[k], L.grads, stream=stream)
             gsc.cache_step(L.params, L.grads, L.m, L.v, adam, stream=stream)
 
     def frame(self, cam, frame: int, stream=None):

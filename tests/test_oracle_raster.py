@@ -220,3 +220,52 @@ def test_backward_matches_finite_differences(orc, slot):
     if slot == 12:
         assert grads[3, 12] == 0.0
     assert gmax > 0
+
+
+# ----------------------------------------------------------------- frozen decisions
+
+FD_SLOTS = [0, 1, 2, 3, 4, 5, 6, 8, 9, 10, 11, 12, 13, 14]
+
+
+def _dense_scene():
+    """Opaque, overlapping Gaussians: pixels stop at T_min and some alphas sit
+    at the alpha_max clamp, so plain differences cross decisions."""
+    cam = synth.orbit_camera(40, 32, 25.0, radius=2.0)
+    p = synth.gaussians(60, 31, lo=0.35, hi=0.65, logscale_mean=-2.2, logscale_std=0.3)
+    p[:, 3] = np.random.default_rng(32).normal(2.5, 1.0, len(p))
+    p[::7, 3] = 6.0  # alpha = 0.9975 G: clamped near these means
+    p[::7, 4:7] += 1.0
+    toward = np.asarray(cam.pos, np.float64) - 0.5
+    toward /= np.linalg.norm(toward)
+    p[:14:7, 0:3] += (0.3 * toward).astype(np.float32)  # two of them in front of the rest
+    return cam, p
+
+
+def test_frozen_lists_reproduce_the_render(orc):
+    cam, p = _dense_scene()
+    img, _, ncon, T = orc.render(p, cam, CFG)
+    fl = orc.FrozenLists(p, cam, CFG)
+    assert np.array_equal(fl.render(p), img)
+    assert fl.clamped.any()                         # clamped alphas are frozen too
+    assert (T < 1e-3).any()                         # some pixels ran into T_min
+    assert int(fl.offsets[-1]) == int(ncon.sum())
+
+
+def test_frozen_differences_equal_the_backward_for_every_parameter(orc):
+    """Central differences of sum(v * render) with the decisions held fixed
+    equal the analytic backward for all 14 parameter kinds of every
+    Gaussian (clamped alphas and pixels stopped at T_min included)."""
+    cam, p = _dense_scene()
+    v = np.random.default_rng(33).uniform(-1, 1, (3, cam.height, cam.width))
+    grads, _ = orc.render_backward(p, cam, v, CFG)
+    fl = orc.FrozenLists(p, cam, CFG)
+    gauss = np.repeat(np.arange(len(p)), len(FD_SLOTS))
+    slots = np.tile(FD_SLOTS, len(p))
+    fd = fl.fd(p, v, gauss, slots, h=1e-4)
+    an = grads[gauss, slots]
+    for s in FD_SLOTS:
+        m = slots == s
+        gmax = np.abs(an[m]).max()
+        assert gmax > 0, s
+        err = np.abs(fd[m] - an[m])
+        assert (err <= 2e-4 * np.maximum(np.abs(an[m]), 1e-3 * gmax) + 1e-10).all(), (s, err.max(), gmax)
