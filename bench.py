@@ -61,7 +61,7 @@ def workload_config(tuned_fwd=None, tuned_bwd=None):
         "levels_fused": True,
         "forward_launch": _launch_cfg(tuned_fwd) if tuned_fwd else None,
         "backward_launch": _launch_cfg(tuned_bwd) if tuned_bwd else None,
-        "autotuned": tuned_fwd is not None,
+        "autotuned": tuned_fwd is not None and tuned_fwd.ms == tuned_fwd.ms,
         "camera": f"orbit r=2.2, fov_y 45 deg, {ORBIT_DEG_PER_FRAME} deg/frame",
         "l2": "inputs larger than L2 (params+moments 256 MB, pair buffers GBs)", "parallelism": "replicas",
     }
@@ -138,15 +138,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def dist_setup(args):
+def dist_setup(args=None):
+    """One process per GPU from torchrun's environment.  NCCL carries only
+    the timing barrier and the max over ranks; on a host without GPUs (the
+    oracle arm, the CPU tests of this plumbing) the same calls go over gloo."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     return world, rank, local
 
 
@@ -161,7 +167,8 @@ def max_over_ranks(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -227,10 +234,13 @@ def run_ours(args, world, rank, local):
             for f in range(args.warmup + args.steps + 1)]
     # pick the launch configurations on this GPU, separately for the forward
     # and the backward batch (results do not depend on them)
-    cands = list(autotune.candidates(TUNE_TILES, TUNE_BINS, TUNE_CAPS, TUNE_PPT))
-    lv = [L.params for L in loop.levels]
-    best_f, _ = autotune.autotune(lv, cams[0], loop.ws, cands=cands, reps=1, fused=True, backward=False)
-    best_b, _ = autotune.autotune(lv, cams[0], loop.ws, cands=cands, reps=1, fused=True, forward=False)
+    if args.no_autotune:  # the configuration the autotuner picks on a GB300
+        best_f = best_b = autotune.Trial((16, 16), 128, 256, 2, float("nan"))
+    else:
+        cands = list(autotune.candidates(TUNE_TILES, TUNE_BINS, TUNE_CAPS, TUNE_PPT))
+        lv = [L.params for L in loop.levels]
+        best_f, _ = autotune.autotune(lv, cams[0], loop.ws, cands=cands, reps=1, fused=True, backward=False)
+        best_b, _ = autotune.autotune(lv, cams[0], loop.ws, cands=cands, reps=1, fused=True, forward=False)
     loop.cfg = best_f.cfg()
     loop.cfg_bwd = best_b.cfg()
     cfg = workload_config(best_f, best_b)
@@ -495,8 +505,7 @@ def run_reference(args, world, rank):
         "metric": METRIC, "impl": "reference", "value": round(value, 1), "unit": "ms/frame", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value, 1), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(workload_config(), tile=None, list_capacity=None, bin=None, pixels_per_thread=None,
-                       autotuned=False),
+        "config": workload_config(),
         "cpu_baseline": {"value": round(value, 1), "unit": "ms/frame", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 1), "unit": "ms/frame", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -513,6 +522,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the launch autotuner (for profiler runs with few launches)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
