@@ -38,7 +38,7 @@ LEVELS = 3
 SPP, BOUNCES = 1, 8
 ORBIT_DEG_PER_FRAME = 0.5
 # candidates of the start-up autotuner (tile shape x bin size x staging capacity)
-TUNE_TILES, TUNE_BINS, TUNE_CAPS, TUNE_PPT = ((16, 16), (32, 8), (16, 8)), (64, 128), (256, 512), (1, 2)
+TUNE_TILES, TUNE_BINS, TUNE_CAPS, TUNE_PPT = ((16, 16), (32, 8), (8, 32)), (64, 128, 256), (256, 512), (1, 2, 4, 8)
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # FP32 FMA lanes: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (maximum SM clock)
@@ -234,13 +234,14 @@ def run_ours(args, world, rank, local):
             for f in range(args.warmup + args.steps + 1)]
     # pick the launch configurations on this GPU, separately for the forward
     # and the backward batch (results do not depend on them)
-    if args.no_autotune:  # the configuration the autotuner picks on a GB300
-        best_f = best_b = autotune.Trial((16, 16), 128, 256, 2, float("nan"))
+    if args.no_autotune:  # the configurations the autotuner picks on a GB300
+        best_f = autotune.Trial((16, 16), 128, 256, 4, float("nan"))
+        best_b = autotune.Trial((16, 16), 128, 256, 2, float("nan"))
     else:
         cands = list(autotune.candidates(TUNE_TILES, TUNE_BINS, TUNE_CAPS, TUNE_PPT))
         lv = [L.params for L in loop.levels]
-        best_f, _ = autotune.autotune(lv, cams[0], loop.ws, cands=cands, reps=1, fused=True, backward=False)
-        best_b, _ = autotune.autotune(lv, cams[0], loop.ws, cands=cands, reps=1, fused=True, forward=False)
+        best_f, _ = autotune.autotune(lv, cams[0], loop.ws, cands=cands, reps=2, fused=True, backward=False)
+        best_b, _ = autotune.autotune(lv, cams[0], loop.ws, cands=cands, reps=2, fused=True, forward=False)
     loop.cfg = best_f.cfg()
     loop.cfg_bwd = best_b.cfg()
     cfg = workload_config(best_f, best_b)

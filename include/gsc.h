@@ -91,7 +91,10 @@ typedef struct gsc_raster_cfg {
     int32_t list_capacity;
     float alpha_max, alpha_min, T_min, near_plane, dilation;
     int32_t bin_size;
-    int32_t pixels_per_thread; /* 1 or 2 (0 = 1): pixels (x, y) and (x, y + tile_h/2) per thread */
+    int32_t pixels_per_thread; /* 1, 2, 4 or 8 (0 = 1): a thread owns the pixels (x, y + k tile_h/ppt),
+                                  k < ppt, of one column.  Compiled (tile, ppt): ppt 1 with 16x16, 8x8,
+                                  32x8, 16x8, 8x16, 8x32, 32x4; ppt 2 with 16x16, 32x8, 16x8, 8x16, 8x32;
+                                  ppt 4 and 8 with 16x16, 32x8, 8x32.  Others: GSC_ERR_INVALID_ARG. */
 } gsc_raster_cfg;
 
 /* ------------------------------------------------------------------ */

@@ -18,7 +18,12 @@ from . import gsc
 TILES = ((16, 16), (8, 8), (32, 8), (16, 8), (8, 16))
 BINS = (32, 64, 128)
 CAPS = (256, 512, 1024)
-PPTS = (1, 2)
+PPTS = (1, 2, 4, 8)
+# (tile, pixels per thread) pairs the library is compiled for
+COMPILED = {1: {(16, 16), (8, 8), (32, 8), (16, 8), (8, 16), (8, 32), (32, 4)},
+            2: {(16, 16), (32, 8), (16, 8), (8, 16), (8, 32)},
+            4: {(16, 16), (32, 8), (8, 32)},
+            8: {(16, 16), (32, 8), (8, 32)}}
 
 
 @dataclass
@@ -36,7 +41,7 @@ class Trial:
 
 def candidates(tiles=TILES, bins=BINS, caps=CAPS, ppts=PPTS):
     for t, b, c, q in itertools.product(tiles, bins, caps, ppts):
-        if b % t[0] or b % t[1] or c < t[0] * t[1] // q or (q == 2 and t[0] * t[1] < 128):
+        if b % t[0] or b % t[1] or c < t[0] * t[1] // q or tuple(t) not in COMPILED.get(q, ()):
             continue
         yield t, b, c, q
 

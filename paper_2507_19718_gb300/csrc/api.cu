@@ -111,22 +111,24 @@ gsc_status cuda_fail(cudaError_t e, const char* where) {
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-bool valid_tile(int w, int h) {
-    static const int ok[][2] = {{16, 16}, {8, 8}, {32, 8}, {16, 8}, {8, 16}, {8, 32}, {32, 4}};
+// (tile_w, tile_h, pixels per thread) combinations the rasterizer is compiled for
+bool valid_tile(int w, int h, int ppt) {
+    static const int ok[][3] = {{16, 16, 1}, {8, 8, 1},  {32, 8, 1}, {16, 8, 1}, {8, 16, 1}, {8, 32, 1},
+                                {32, 4, 1},  {16, 16, 2}, {32, 8, 2}, {16, 8, 2}, {8, 16, 2}, {8, 32, 2},
+                                {16, 16, 4}, {32, 8, 4},  {8, 32, 4}, {16, 16, 8}, {32, 8, 8}, {8, 32, 8}};
     for (auto& t : ok)
-        if (t[0] == w && t[1] == h) return true;
+        if (t[0] == w && t[1] == h && t[2] == ppt) return true;
     return false;
 }
 
 gsc_status check_cfg(const gsc_raster_cfg* c) {
     if (!c) return fail(GSC_ERR_INVALID_ARG, "raster cfg is NULL");
-    if (!valid_tile(c->tile_w, c->tile_h))
-        return fail(GSC_ERR_INVALID_ARG, "unsupported tile %dx%d", c->tile_w, c->tile_h);
+    int ppt = c->pixels_per_thread ? c->pixels_per_thread : 1;
+    if (!valid_tile(c->tile_w, c->tile_h, ppt))
+        return fail(GSC_ERR_INVALID_ARG, "unsupported tile %dx%d with %d pixels per thread", c->tile_w, c->tile_h,
+                    c->pixels_per_thread);
     if (c->list_capacity < 32 || c->list_capacity > 2048 || c->list_capacity % 32)
         return fail(GSC_ERR_INVALID_ARG, "list_capacity %d not a multiple of 32 in [32, 2048]", c->list_capacity);
-    if (c->pixels_per_thread < 0 || c->pixels_per_thread > 2 ||
-        (c->pixels_per_thread == 2 && c->tile_w * c->tile_h < 128))
-        return fail(GSC_ERR_INVALID_ARG, "pixels_per_thread must be 0, 1 or 2 (2 needs >= 128 pixels per tile)");
     if (c->bin_size != 0 && (c->bin_size < 32 || c->bin_size > 512 || c->bin_size % c->tile_w ||
                              c->bin_size % c->tile_h))
         return fail(GSC_ERR_INVALID_ARG, "bin_size %d must be 0 or a multiple of the tile in [32, 512]",
@@ -160,7 +162,7 @@ RasterDev raster_dev(const gsc_raster_cfg* c) {
     r.alpha_max = c->alpha_max; r.alpha_min = c->alpha_min; r.T_min = c->T_min;
     r.near_plane = c->near_plane; r.dilation = c->dilation;
     r.tile_w = c->tile_w; r.tile_h = c->tile_h;
-    r.ppt = c->pixels_per_thread == 2 ? 2 : 1;
+    r.ppt = c->pixels_per_thread ? c->pixels_per_thread : 1;
     int nt = c->tile_w * c->tile_h / r.ppt;
     r.cap = c->list_capacity < nt ? nt : c->list_capacity;
     r.bin = c->bin_size ? c->bin_size : 64;

@@ -47,12 +47,16 @@ __device__ __forceinline__ float view_depth(const CamDev& c, float x, float y, f
     return __fadd_rn(s, c.t[2]);
 }
 
-// log2 of the Gaussian falloff at pixel-centre offset (dx, dy), fixed rounding
-__device__ __forceinline__ float falloff_log2(float4 r0, float qc, float dx, float dy) {
-    float p = __fmul_rn(__fmul_rn(r0.z, dx), dx);
-    p = __fmaf_rn(__fmul_rn(r0.w, dx), dy, p);
-    p = __fmaf_rn(__fmul_rn(qc, dy), dy, p);
-    return p;
+// log2 of the Gaussian falloff at pixel-centre offset (dx, dy), fixed rounding:
+// p = fma(qc dy, dy, fma(qb dx, dy, (qa dx) dx)).  The dx terms are shared by
+// the pixels of one column, so they are split off.
+__device__ __forceinline__ float falloff_col(float4 r0, float dx, float& wx) {
+    wx = __fmul_rn(r0.w, dx);
+    return __fmul_rn(__fmul_rn(r0.z, dx), dx);
+}
+__device__ __forceinline__ float falloff_row(float xx, float wx, float qc, float dy) {
+    float p = __fmaf_rn(wx, dy, xx);
+    return __fmaf_rn(__fmul_rn(qc, dy), dy, p);
 }
 
 struct Proj {
@@ -120,12 +124,18 @@ __device__ __forceinline__ bool project_core(float4 p0, float4 p1, float4 p2, co
     x.A = x.Tm[0] * u0[0] + x.Tm[1] * u0[1] + x.Tm[2] * u0[2] + rc.dilation;
     x.B = x.Tm[3] * u0[0] + x.Tm[4] * u0[1] + x.Tm[5] * u0[2];
     x.C = x.Tm[3] * u1[0] + x.Tm[4] * u1[1] + x.Tm[5] * u1[2] + rc.dilation;
-    // FP32 products are exact in FP64: the determinant carries one rounding
-    double det = (double)x.A * (double)x.C - (double)x.B * (double)x.B;
-    if (!(det > 0.0)) return false;
-    x.a = (float)((double)x.C / det);
-    x.b = (float)(-(double)x.B / det);
-    x.c = (float)((double)x.A / det);
+    // det = A C - B^2 by Kahan's difference of products (the rounding error of
+    // B^2 recovered with an FMA and added back; within 1.5 ulp, Jeannerod,
+    // Louvet and Muller 2013), so that near-degenerate covariances keep an
+    // accurate determinant without FP64 arithmetic
+    float bb = __fmul_rn(x.B, x.B);
+    float err = __fmaf_rn(-x.B, x.B, bb);
+    float det = __fadd_rn(__fmaf_rn(x.A, x.C, -bb), err);
+    if (!(det > 0.f)) return false;
+    float idet = __frcp_rn(det);
+    x.a = x.C * idet;
+    x.b = -x.B * idet;
+    x.c = x.A * idet;
     return true;
 }
 
@@ -173,48 +183,64 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchDe
     rec[3 * (size_t)g + 2] = make_float4(fmaxf(p3.x, 0.f), fmaxf(p3.y, 0.f), fmaxf(p3.z, 0.f), 0.f);
 }
 
-// one warp writes the (bin, Gaussian) pairs of 32 consecutive depth-ordered
-// Gaussians, one Gaussian at a time, so that every store instruction is
-// contiguous; the bin rectangle follows from the tile rectangle
+// One warp emits the (bin, Gaussian) pairs of 32 consecutive depth-ordered
+// Gaussians.  Their outputs form one contiguous run (the offsets are an
+// exclusive scan in that order), so the warp walks the run 32 elements at a
+// time: element e belongs to the last lane whose offset is <= e (a five-step
+// search over the lanes' offsets), and every store instruction is contiguous.
+// The bin rectangle follows from the tile rectangle.
 __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ BatchDev b, const uint32_t* __restrict__ sidx,
                                               const uint32_t* __restrict__ off, const uint32_t* __restrict__ cnt,
                                               const uint2* __restrict__ rect, RasterDev rc,
                                               const uint32_t* __restrict__ counters, uint32_t* __restrict__ pkey,
                                               uint32_t* __restrict__ pval) {
     const uint32_t N = b.total_g;
-    uint32_t total = counters[kCntPairs];
-    uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    uint32_t i = wid * 32 + lane;
-    if (wid * 32 >= N) return;
+    const uint32_t total = counters[kCntPairs];
+    const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid * 32 >= N || total == 0) return;  // warp-uniform
+    const uint32_t i = wid * 32 + lane;
     uint32_t g = 0, c = 0, o = 0;
-    int v = 0;
-    uint2 rr = make_uint2(0, 0);
     if (i < N) {
         g = sidx[i];
         c = cnt[g];
         o = off[i];
-        if (c) {
-            rr = rect[g];
-            v = view_of_gaussian(b, g);
-        }
     }
-    for (int j = 0; j < 32; ++j) {
-        uint32_t cj = __shfl_sync(kFull, c, j);
-        uint32_t oj = __shfl_sync(kFull, o, j);
-        uint32_t gj = __shfl_sync(kFull, g, j);
-        uint32_t rx = __shfl_sync(kFull, rr.x, j);
-        uint32_t ry = __shfl_sync(kFull, rr.y, j);
-        int vj = __shfl_sync(kFull, v, j);
-        if (cj == 0 || (uint64_t)oj + cj > total) continue;
-        uint32_t bx0 = (rx & 0xffffu) / rc.spt_x, bx1 = ((rx >> 16) - 1) / rc.spt_x + 1;
-        uint32_t by0 = (ry & 0xffffu) / rc.spt_y;
-        uint32_t wx = bx1 - bx0;
-        const uint32_t boff = b.v[vj].bin_off, bins_x = (uint32_t)b.v[vj].bins_x;
-        for (uint32_t k = lane; k < cj; k += 32) {
-            uint32_t ky = k / wx, kx = k - ky * wx;
-            pkey[oj + k] = boff + (by0 + ky) * bins_x + bx0 + kx;
-            pval[oj + k] = gj;
+    // lanes past N continue the run with no pairs, keeping the offsets monotone
+    const uint32_t nv = min(32u, N - wid * 32);
+    const uint32_t last_o = __shfl_sync(kFull, o, nv - 1), last_c = __shfl_sync(kFull, c, nv - 1);
+    if (i >= N) o = last_o + last_c;
+    const uint32_t start = __shfl_sync(kFull, o, 0);
+    const uint32_t end = min(last_o + last_c, total);
+    // per lane: bin rectangle origin and width, bins of its view
+    uint32_t bx0 = 0, by0 = 0, wx = 1, boff = 0, bins_x = 0;
+    if (c) {
+        uint2 rr = rect[g];
+        bx0 = (rr.x & 0xffffu) / rc.spt_x;
+        uint32_t bx1 = ((rr.x >> 16) - 1) / rc.spt_x + 1;
+        by0 = (rr.y & 0xffffu) / rc.spt_y;
+        wx = bx1 - bx0;
+        const ViewDev& vw = b.v[view_of_gaussian(b, g)];
+        boff = vw.bin_off;
+        bins_x = (uint32_t)vw.bins_x;
+    }
+    for (uint32_t e0 = start; e0 < end; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        int j = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            uint32_t oj = __shfl_sync(kFull, o, j + step);
+            if (j + step < 32 && oj <= e) j += step;
+        }
+        const uint32_t k = e - __shfl_sync(kFull, o, j);
+        const uint32_t gj = __shfl_sync(kFull, g, j);
+        const uint32_t wj = __shfl_sync(kFull, wx, j);
+        const uint32_t x0 = __shfl_sync(kFull, bx0, j), y0 = __shfl_sync(kFull, by0, j);
+        const uint32_t bo = __shfl_sync(kFull, boff, j), bxn = __shfl_sync(kFull, bins_x, j);
+        if (e < end) {
+            const uint32_t ky = k / wj, kx = k - ky * wj;
+            pkey[e] = bo + (y0 + ky) * bxn + x0 + kx;
+            pval[e] = gj;
         }
     }
 }
@@ -343,6 +369,7 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render(const __grid_constant__
     float fx = (float)px + 0.5f;
     float fy[PPT], T[PPT], Cr[PPT], Cg[PPT], Cb[PPT];
     bool inside[PPT], done[PPT];
+    uint32_t ev[PPT];  // entries a pixel evaluated, set when it reaches T_min
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
         int py = py0 + q * ROWS;
@@ -351,9 +378,11 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render(const __grid_constant__
         T[q] = 1.f;
         Cr[q] = Cg[q] = Cb[q] = 0.f;
         done[q] = !inside[q];
+        ev[q] = inside[q] ? 0xffffffffu : 0u;
     }
     uint2 rg = ranges[vw.bin_off + (ty / rc.spt_y) * vw.bins_x + tx / rc.spt_x];
     uint32_t pos = rg.x;
+    uint32_t hbase = 0;  // entries staged by earlier batches of this tile
     for (;;) {
         bool tdone = true;
 #pragma unroll
@@ -389,13 +418,12 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render(const __grid_constant__
             for (int k = 0; k < staged; ++k) {
                 float4 r0 = s0[k];
                 float4 r1 = s1[k];
+                float wx, xx = falloff_col(r0, __fsub_rn(fx, r0.x), wx);
                 bool all = true;
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
                     if (done[q]) continue;
-                    float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy[q], r0.y);
-                    float p = falloff_log2(r0, r1.x, dx, dy);
-                    ++n_eval;
+                    float p = falloff_row(xx, wx, r1.x, __fsub_rn(fy[q], r0.y));
                     if (p < r1.z) {
                         all = false;
                         continue;
@@ -404,6 +432,7 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render(const __grid_constant__
                     float Tn = __fmul_rn(T[q], __fsub_rn(1.f, alpha));
                     if (Tn < rc.T_min) {
                         done[q] = true;
+                        ev[q] = hbase + (uint32_t)k + 1u;
                         continue;
                     }
                     all = false;
@@ -423,10 +452,12 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render(const __grid_constant__
                 }
             }
         }
+        hbase += (uint32_t)staged;
     }
     size_t HW = (size_t)cam.W * cam.H;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
+        n_eval += ev[q] == 0xffffffffu ? hbase : ev[q];  // a pixel that never stopped saw every entry
         if (inside[q]) {
             size_t p = (size_t)(py0 + q * ROWS) * cam.W + px;
             vw.image[p] = Cr[q];
@@ -506,7 +537,7 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
     float4* s1 = smem + cap;
     float4* s2 = smem + 2 * cap;
     uint32_t* hits = reinterpret_cast<uint32_t*>(smem + 3 * cap);
-    uint32_t n_eval1 = 0, n_eval2 = 0, n_comp1 = 0, n_hit2 = 0;
+    uint32_t n_eval1 = 0, n_eval2 = 0, n_comp1 = 0;
     __shared__ uint32_t s_tile;
     // persistent CTAs: tiles of all views are handed out by an atomic counter
     for (;;) {
@@ -525,7 +556,7 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
     size_t HW = (size_t)cam.W * cam.H;
     float fy[PPT], gr[PPT], gg[PPT], gb[PPT], T[PPT];
     bool active[PPT], done[PPT];
-    uint32_t last[PPT];
+    uint32_t last[PPT], ev[PPT];
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
         int py = py0 + q * ROWS;
@@ -542,6 +573,7 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
         done[q] = !active[q];
         T[q] = 1.f;
         last[q] = 0;
+        ev[q] = active[q] ? 0xffffffffu : 0u;
     }
     uint2 rg = ranges[vw.bin_off + (ty / rc.spt_y) * vw.bins_x + tx / rc.spt_x];
 
@@ -587,17 +619,17 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
             for (int k = 0; k < staged; ++k) {
                 float4 r0 = s0[k];
                 float4 r1 = s1[k];
+                float wx, xx = falloff_col(r0, __fsub_rn(fx, r0.x), wx);
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
                     if (done[q]) continue;
-                    float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy[q], r0.y);
-                    float p = falloff_log2(r0, r1.x, dx, dy);
-                    ++n_eval1;
+                    float p = falloff_row(xx, wx, r1.x, __fsub_rn(fy[q], r0.y));
                     if (p < r1.z) continue;
                     float alpha = fminf(rc.alpha_max, __fmul_rn(r1.y, ex2_approx(p)));
                     float Tn = __fmul_rn(T[q], __fsub_rn(1.f, alpha));
                     if (Tn < rc.T_min) {
                         done[q] = true;
+                        ev[q] = h0 + (uint32_t)k + 1u;
                         continue;
                     }
                     T[q] = Tn;
@@ -612,7 +644,11 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
     uint32_t mylast = 0;
 #pragma unroll
     for (int q = 0; q < PPT; ++q)
-        if (active[q]) mylast = max(mylast, last[q]);
+        if (active[q]) {
+            mylast = max(mylast, last[q]);
+            n_eval2 += last[q];  // phase 2 evaluates this pixel at entries [0, last)
+            n_eval1 += ev[q] == 0xffffffffu ? nhit : ev[q];
+        }
     if (mylast) atomicMax(&s_end, mylast);
     __syncthreads();
     const uint32_t hend = s_end;
@@ -675,6 +711,8 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
                 float4 r0 = s0[k];
                 float4 r1 = s1[k];
                 float4 c = s2[k];
+                const float dx = __fsub_rn(fx, r0.x);
+                float wx, xx = falloff_col(r0, dx, wx);
                 // per entry: sum w dx, sum w dy, sum w dx^2, sum w dx dy, sum w dy^2
                 // (w = dL/dalpha alpha), sum dL/dalpha G, red, green; blue apart
                 float v8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -683,12 +721,10 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
                     if (!(active[q] && j < last[q])) continue;
-                    float dx = __fsub_rn(fx, r0.x), dy = __fsub_rn(fy[q], r0.y);
-                    float p = falloff_log2(r0, r1.x, dx, dy);
-                    ++n_eval2;
+                    const float dy = __fsub_rn(fy[q], r0.y);
+                    float p = falloff_row(xx, wx, r1.x, dy);
                     if (p < r1.z) continue;
                     any = true;
-                    ++n_hit2;
                     float e = ex2_approx(p);
                     float araw = __fmul_rn(r1.y, e);
                     float alpha = fminf(rc.alpha_max, araw);
@@ -731,7 +767,7 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
     warp_count(&stats[kStEvalRewalk], n_eval1);
     warp_count(&stats[kStEvalBack], n_eval2);
     warp_count(&stats[kStCompRewalk], n_comp1);
-    warp_count(&stats[kStHitBack], n_hit2);
+    warp_count(&stats[kStHitBack], n_comp1);  // back to front: the same composited pairs
 }
 
 // 2D gradients -> packed parameter gradients (+=)
@@ -957,23 +993,36 @@ static cudaError_t render_bwd_t(const BatchDev& b, const RasterDev& rc, gsc_work
     return cudaGetLastError();
 }
 
+// the (tile, pixels per thread) pairs compiled; the API accepts exactly these
 #define GSC_TILE_DISPATCH(FN, ...)                                                            \
-    if (rc.ppt == 2) {                                                                        \
+    switch (rc.ppt) {                                                                         \
+    case 8:                                                                                   \
+        if (rc.tile_w == 16 && rc.tile_h == 16) return FN<16, 16, 8>(__VA_ARGS__);            \
+        if (rc.tile_w == 32 && rc.tile_h == 8) return FN<32, 8, 8>(__VA_ARGS__);              \
+        if (rc.tile_w == 8 && rc.tile_h == 32) return FN<8, 32, 8>(__VA_ARGS__);              \
+        return cudaErrorInvalidValue;                                                         \
+    case 4:                                                                                   \
+        if (rc.tile_w == 16 && rc.tile_h == 16) return FN<16, 16, 4>(__VA_ARGS__);            \
+        if (rc.tile_w == 32 && rc.tile_h == 8) return FN<32, 8, 4>(__VA_ARGS__);              \
+        if (rc.tile_w == 8 && rc.tile_h == 32) return FN<8, 32, 4>(__VA_ARGS__);              \
+        return cudaErrorInvalidValue;                                                         \
+    case 2:                                                                                   \
         if (rc.tile_w == 16 && rc.tile_h == 16) return FN<16, 16, 2>(__VA_ARGS__);            \
         if (rc.tile_w == 32 && rc.tile_h == 8) return FN<32, 8, 2>(__VA_ARGS__);              \
         if (rc.tile_w == 16 && rc.tile_h == 8) return FN<16, 8, 2>(__VA_ARGS__);              \
         if (rc.tile_w == 8 && rc.tile_h == 16) return FN<8, 16, 2>(__VA_ARGS__);              \
         if (rc.tile_w == 8 && rc.tile_h == 32) return FN<8, 32, 2>(__VA_ARGS__);              \
         return cudaErrorInvalidValue;                                                         \
-    }                                                                                         \
-    if (rc.tile_w == 16 && rc.tile_h == 16) return FN<16, 16, 1>(__VA_ARGS__);                \
-    if (rc.tile_w == 8 && rc.tile_h == 8) return FN<8, 8, 1>(__VA_ARGS__);                    \
-    if (rc.tile_w == 32 && rc.tile_h == 8) return FN<32, 8, 1>(__VA_ARGS__);                  \
-    if (rc.tile_w == 16 && rc.tile_h == 8) return FN<16, 8, 1>(__VA_ARGS__);                  \
-    if (rc.tile_w == 8 && rc.tile_h == 16) return FN<8, 16, 1>(__VA_ARGS__);                  \
-    if (rc.tile_w == 8 && rc.tile_h == 32) return FN<8, 32, 1>(__VA_ARGS__);                  \
-    if (rc.tile_w == 32 && rc.tile_h == 4) return FN<32, 4, 1>(__VA_ARGS__);                  \
-    return cudaErrorInvalidValue;
+    default:                                                                                  \
+        if (rc.tile_w == 16 && rc.tile_h == 16) return FN<16, 16, 1>(__VA_ARGS__);            \
+        if (rc.tile_w == 8 && rc.tile_h == 8) return FN<8, 8, 1>(__VA_ARGS__);                \
+        if (rc.tile_w == 32 && rc.tile_h == 8) return FN<32, 8, 1>(__VA_ARGS__);              \
+        if (rc.tile_w == 16 && rc.tile_h == 8) return FN<16, 8, 1>(__VA_ARGS__);              \
+        if (rc.tile_w == 8 && rc.tile_h == 16) return FN<8, 16, 1>(__VA_ARGS__);              \
+        if (rc.tile_w == 8 && rc.tile_h == 32) return FN<8, 32, 1>(__VA_ARGS__);              \
+        if (rc.tile_w == 32 && rc.tile_h == 4) return FN<32, 4, 1>(__VA_ARGS__);              \
+        return cudaErrorInvalidValue;                                                         \
+    }
 
 cudaError_t launch_render(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
                           cudaStream_t s) {

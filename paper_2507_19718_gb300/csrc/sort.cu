@@ -117,6 +117,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
                                                                 const uint32_t* __restrict__ totals, int blocks) {
     __shared__ uint32_t wh[8][256];
     __shared__ uint32_t dbase[256];
+    __shared__ uint32_t tstart[256];
+    __shared__ uint32_t gbase[256];
+    __shared__ uint32_t skey[kSortTile];
+    __shared__ uint32_t sval[kSortTile];
     __shared__ uint32_t sm[8];
     uint32_t n = read_count(n_dev, n_host);
     uint32_t lo, hi;
@@ -152,24 +156,41 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
         }
         __syncthreads();
         {
+            // per digit: warps' offsets within the tile's run of that digit, the
+            // run's start in the tile's locally sorted order, and the global
+            // position of local element e of digit d (gbase[d] + e)
             int d = threadIdx.x;
-            uint32_t run = dbase[d];
+            uint32_t run = 0;
 #pragma unroll
             for (int w = 0; w < 8; ++w) {
                 uint32_t c = wh[w][d];
                 wh[w][d] = run;
                 run += c;
             }
-            dbase[d] = run;
+            uint32_t all;
+            uint32_t ts = block_exclusive_scan_256(run, sm, &all);
+            tstart[d] = ts;
+            gbase[d] = dbase[d] - ts;
+            dbase[d] += run;
         }
         __syncthreads();
+        // local sort of the tile in shared memory (stable: warp order, then rank)
 #pragma unroll
         for (int j = 0; j < kSortIPT; ++j) {
             if (dd[j] < 256) {
-                uint32_t pos = wh[warp][dd[j]] + rank[j];
-                kout[pos] = kk[j];
-                vout[pos] = vv[j];
+                uint32_t lp = tstart[dd[j]] + wh[warp][dd[j]] + rank[j];
+                skey[lp] = kk[j];
+                sval[lp] = vv[j];
             }
+        }
+        __syncthreads();
+        // runs of equal digits are contiguous in the output: coalesced stores
+        const uint32_t cnt = min((uint32_t)kSortTile, hi - tile);
+        for (uint32_t e = threadIdx.x; e < cnt; e += kSortThreads) {
+            uint32_t k = skey[e];
+            uint32_t pos = gbase[(k >> shift) & 255u] + e;
+            kout[pos] = k;
+            vout[pos] = sval[e];
         }
         __syncthreads();
     }

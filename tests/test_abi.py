@@ -100,6 +100,14 @@ def test_host_side_validation(L):
     assert L.gsc_cache_render(None, 0, C.byref(cam), C.byref(cfg), None, None, None) == gsc.GSC_ERR_INVALID_ARG
     cfg = gsc.raster_cfg()
     assert L.gsc_cache_render(None, 0, C.byref(cam), C.byref(cfg), None, None, None) == gsc.GSC_ERR_INVALID_ARG
+    # pixels per thread: only the compiled (tile, ppt) pairs pass the configuration check
+    msg = C.create_string_buffer(256)
+    for tile, ppt, ok in [((16, 16), 8, True), ((8, 32), 4, True), ((32, 8), 2, True), ((8, 8), 4, False),
+                          ((16, 16), 3, False), ((32, 4), 2, False), ((16, 16), 16, False)]:
+        cfg = gsc.raster_cfg(tile=tile, pixels_per_thread=ppt)
+        assert L.gsc_cache_render(None, 0, C.byref(cam), C.byref(cfg), None, None, None) == gsc.GSC_ERR_INVALID_ARG
+        L.gsc_last_error(msg, 256)
+        assert (b"pixels per thread" not in msg.value) == ok, (tile, ppt, msg.value)
     # optimiser: bad hyper-parameters
     a = gsc.adam_params([0.01] * 16, step=0)
     assert L.gsc_cache_step(C.c_void_p(256), C.c_void_p(256), C.c_void_p(256), C.c_void_p(256), 4, C.byref(a),

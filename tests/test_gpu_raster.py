@@ -65,7 +65,9 @@ def test_tile_and_capacity_do_not_change_bits(gpu, orc):
     for tile, cap, b, ppt in [((8, 8), 64, 32, 1), ((32, 8), 2048, 64, 1), ((16, 8), 32, 128, 1),
                               ((8, 16), 512, 256, 1), ((8, 32), 128, 64, 1), ((32, 4), 96, 32, 1),
                               ((16, 16), 1024, 512, 1), ((16, 16), 256, 48, 1), ((16, 16), 128, 128, 2),
-                              ((32, 8), 512, 64, 2), ((16, 8), 64, 32, 2), ((8, 32), 256, 128, 2)]:
+                              ((32, 8), 512, 64, 2), ((16, 8), 64, 32, 2), ((8, 32), 256, 128, 2),
+                              ((16, 16), 64, 64, 4), ((32, 8), 256, 128, 4), ((8, 32), 32, 32, 4),
+                              ((16, 16), 32, 128, 8), ((32, 8), 512, 64, 8), ((8, 32), 256, 256, 8)]:
         cfg = gpu.raster_cfg(tile=tile, list_capacity=cap, bin_size=b, pixels_per_thread=ppt)
         other = _render(gpu, p, cam, cfg, ws)
         np.testing.assert_array_equal(other, base, err_msg=str((tile, cap, b, ppt)))
@@ -129,7 +131,8 @@ def _grad_compare(g_gpu, g_ref, tol=1e-3):
         assert not bad.any(), (name, np.argwhere(bad)[:5], a[bad][:5], b[bad][:5])
 
 
-@pytest.mark.parametrize("tile,ppt", [((16, 16), 1), ((8, 8), 1), ((16, 16), 2), ((32, 8), 2)])
+@pytest.mark.parametrize("tile,ppt", [((16, 16), 1), ((8, 8), 1), ((16, 16), 2), ((32, 8), 2), ((16, 16), 4),
+                                      ((8, 32), 4), ((16, 16), 8), ((32, 8), 8)])
 def test_backward_matches_oracle_config0(gpu, orc, tile, ppt):
     torch = _torch()
     p, cam = _scene0(w=96, h=80)
@@ -194,3 +197,26 @@ def test_full_size_1080p_1M_sampled(gpu, orc):
     touched = np.abs(ref).sum(1) > 0
     assert touched.sum() > 100
     _grad_compare(g, ref)
+
+
+def test_work_counters_count_the_composited_pairs(gpu, orc):
+    """The roofline's numerator comes from device counters: the forward's
+    composited pairs equal the oracle's per-pixel term counts (up to the
+    marginal pixels), and the backward's re-walk and back-to-front phases
+    count the same pairs."""
+    torch = _torch()
+    p, cam = _scene0(w=96, h=80, angle=50.0)
+    ref, marg, ncon, _ = orc.render(p, cam)
+    ws = _ws(gpu, len(p), 1 << 21, cam.width, cam.height)
+    ws.counters()
+    for tile, ppt in [((16, 16), 2), ((8, 32), 8)]:
+        cfg = gpu.raster_cfg(tile=tile, pixels_per_thread=ppt)
+        params = torch.from_numpy(p).cuda()
+        gpu.cache_render(params, cam, cfg, ws)
+        dl = torch.full((3, cam.height, cam.width), 1e-3, device="cuda")
+        gpu.cache_backward(params, cam, cfg, ws, dl)
+        c = ws.counters()
+        assert abs(c["composited_fwd"] - int(ncon.sum())) <= 2 * int(marg.sum()) + 2, (c, int(ncon.sum()))
+        assert c["composited_rewalk"] == c["composited_fwd"] == c["hits_back"]
+        assert c["eval_rewalk"] == c["eval_fwd"] >= c["eval_back"] >= c["composited_fwd"] > 0
+        assert c["binnings"] == 2 and c["pairs_sum"] > 0
