@@ -12,6 +12,7 @@ Passages followed (Bauer et al., "GSCache"):
                      Sec. 3.4 Eq. 2, Sec. 3.5 (intermediate path buffers)
   project / render   Sec. 3.1 (Gaussian splatting of each cache level)
   render_backward    Sec. 3.5 ("inverse splatting step")
+  init_*             Sec. 3.2 "Cache Initialization" and Eq. 3
   FrozenLists        the same render with its threshold decisions held fixed,
                      for central differences of the backward at 1M Gaussians
   loss_hdr           Sec. 3.6 "Loss"
@@ -82,6 +83,10 @@ def lib():
             L.orc_frozen_fd.restype = i32
             L.orc_render_frozen.argtypes = [i64, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, i32]
             L.orc_render_frozen.restype = i32
+            L.orc_init_points.argtypes = [i32, vp, i32, i32, i32, vp, i32, vp, vp, i64, vp, u64, i32, vp, vp, vp,
+                                          i32]
+            L.orc_knn3_mean.argtypes = [vp, i64, vp, i64, vp, i32]
+            L.orc_init_scales.argtypes = [vp, i64, vp, vp, vp]
             L.orc_loss_hdr.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp]
             L.orc_loss_hdr.restype = f64
             L.orc_loss_l1ssim.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp]
@@ -177,6 +182,69 @@ def sigma_t(scene, pts) -> np.ndarray:
     out = np.empty(len(pts), np.float64)
     lib().orc_sigma_t(_p(grid), nx, ny, nz, _p(vol_f), len(tf_pos), _p(tf_pos), _p(tf_rgba), _p(pts), len(pts),
                       _p(out))
+    return out
+
+
+# ---------------------------------------------------------------- cache initialisation
+
+INIT_MAX_ATTEMPTS = 4096
+
+
+def init_points(scene, n: int, seed: int, idx=None, precision: int = 32, max_attempts: int = INIT_MAX_ATTEMPTS,
+                nthreads: int = 0):
+    """Delta-tracked point samples (Sec. 3.2): positions (n, 3), albedos (n, 3),
+    attempts (n,) for points 0..n-1 or the given indices."""
+    grid, nx, ny, nz, vol_f, tf_pos, tf_rgba, _ = _scene_arrays(scene)
+    ix = _c(idx, np.int64) if idx is not None else None
+    m = len(ix) if ix is not None else n
+    pos = np.zeros((m, 3), np.float64)
+    alb = np.zeros((m, 3), np.float64)
+    att = np.zeros(m, np.int32)
+    lib().orc_init_points(precision, _p(grid), nx, ny, nz, _p(vol_f), len(tf_pos), _p(tf_pos), _p(tf_rgba), m,
+                          _p(ix), seed, max_attempts, _p(pos), _p(alb), _p(att), _threads(nthreads))
+    return pos, alb, att
+
+
+def knn3_mean(pts, query=None, nthreads: int = 0) -> np.ndarray:
+    """Mean distance of each (query) point to its three nearest others, brute force."""
+    pts = _c(pts, np.float64).reshape(-1, 3)
+    q = _c(query, np.int64) if query is not None else None
+    out = np.zeros(len(q) if q is not None else len(pts), np.float64)
+    lib().orc_knn3_mean(_p(pts), len(pts), _p(q), len(out), _p(out), _threads(nthreads))
+    return out
+
+
+def init_scales(mbar):
+    """Eq. 3: isotropic scales from the mean 3-NN distances; returns (s, mu, sigma)."""
+    mbar = _c(mbar, np.float64)
+    s = np.zeros_like(mbar)
+    mu, sg = C.c_double(), C.c_double()
+    lib().orc_init_scales(_p(mbar), len(mbar), _p(s), C.byref(mu), C.byref(sg))
+    return s, mu.value, sg.value
+
+
+def init_gaussians(scene, n_points: int, levels: int, seed: int, opacity: float = 0.1, precision: int = 32,
+                   nthreads: int = 0):
+    """The initial cache: level k holds points 0 .. (n_points >> k) - 1 of one
+    sampled cloud, each a Gaussian at the point with the point's albedo as
+    colour, identity rotation, the given opacity and the Eq. 3 scale from the
+    3-NN distances within its level.  Returns one (N_k, 16) array per level."""
+    pos, alb, att = init_points(scene, n_points, seed, precision=precision, nthreads=nthreads)
+    if (att == 0).any():
+        raise RuntimeError("some points found no interaction")
+    pos32 = pos.astype(np.float32).astype(np.float64)
+    out = []
+    for k in range(levels):
+        n = n_points >> k
+        mbar = knn3_mean(pos32[:n], nthreads=nthreads)
+        s, _, _ = init_scales(mbar)
+        p = np.zeros((n, 16), np.float64)
+        p[:, 0:3] = pos32[:n]
+        p[:, 3] = np.log(opacity / (1.0 - opacity))
+        p[:, 4:7] = np.log(s)[:, None]
+        p[:, 8] = 1.0
+        p[:, 12:15] = alb[:n]
+        out.append(p)
     return out
 
 

@@ -20,6 +20,9 @@
  *                       silent on its RNG)
  *   orc_trace           Sec. 3.1 (Eq. 1), 3.2, 3.3 (Algorithm 1), 3.4 (Eq. 2),
  *                       3.5; trace_body.inc
+ *   orc_init_points     Sec. 3.2 "Cache Initialization": delta-tracked point
+ *                       sampling (trace_body.inc); orc_knn3_mean and
+ *                       orc_init_scales: the k-NN scale of Eq. 3
  *   orc_transmittance   delta tracking (Sec. 3.2) vs ratio tracking
  *   orc_project         3D Gaussian splatting projection, Sec. 3.1 / Sec. 3.6
  *                       (SH degree 0)
@@ -44,6 +47,7 @@
 
 #define TRACK_MAX_STEPS (1 << 20)
 #define TRACE_MAX_LEVELS 16
+#define INIT_STREAM 0xffffffffu /* third Philox counter word of the initialisation rays */
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as   */
@@ -254,6 +258,84 @@ void orc_sigma_t(const float* grid, int nx, int ny, int nz, const float* vol_f, 
     float zero3[3] = {0, 0, 0}, up[3] = {0, 0, 1};
     vol_setup_d(&v, grid, nx, ny, nz, vol_f[0], vol_f[1], vol_f[2], tf_n, tf_pos, tf_rgba, up, zero3, zero3);
     for (int64_t k = 0; k < n; ++k) out[k] = sigma_t_d(&v, pts + 3 * k);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cache initialisation (Sec. 3.2 "Cache Initialization", Eq. 3).            */
+
+/*
+ * Point sampling for the points idx[0..n) (NULL: 0..n-1), precision 32 (FP32
+ * mirror) or 64.  pos, alb: n x 3; attempts: n (0 = no collision found).
+ */
+void orc_init_points(int precision, const float* grid, int nx, int ny, int nz, const float* vol_f, int tf_n,
+                     const float* tf_pos, const float* tf_rgba, int64_t n, const int64_t* idx, uint64_t seed,
+                     int max_attempts, double* pos, double* alb, int32_t* attempts, int nthreads) {
+    float zero3[3] = {0, 0, 0}, up[3] = {0, 0, 1};
+    if (precision == 32) {
+        vol_t_f v;
+        vol_setup_f(&v, grid, nx, ny, nz, vol_f[0], vol_f[1], vol_f[2], tf_n, tf_pos, tf_rgba, up, zero3, zero3);
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
+        for (int64_t k = 0; k < n; ++k) {
+            float x[3] = {0, 0, 0}, a[3] = {0, 0, 0};
+            attempts[k] = init_point_f(&v, seed, (uint32_t)(idx ? idx[k] : k), max_attempts, x, a);
+            for (int c = 0; c < 3; ++c) { pos[3 * k + c] = x[c]; alb[3 * k + c] = a[c]; }
+        }
+    } else {
+        vol_t_d v;
+        vol_setup_d(&v, grid, nx, ny, nz, vol_f[0], vol_f[1], vol_f[2], tf_n, tf_pos, tf_rgba, up, zero3, zero3);
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
+        for (int64_t k = 0; k < n; ++k) {
+            double x[3] = {0, 0, 0}, a[3] = {0, 0, 0};
+            attempts[k] = init_point_d(&v, seed, (uint32_t)(idx ? idx[k] : k), max_attempts, x, a);
+            for (int c = 0; c < 3; ++c) { pos[3 * k + c] = x[c]; alb[3 * k + c] = a[c]; }
+        }
+    }
+}
+
+/*
+ * Mean distance to the three nearest other points (Eq. 3's (1/3) sum_j d_ij),
+ * by brute force in FP64: for query q[k] (an index into pts, M x 3) over all
+ * M points but itself.  Fewer than three other points: the mean of those.
+ */
+void orc_knn3_mean(const double* pts, int64_t M, const int64_t* q, int64_t Q, double* out, int nthreads) {
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+    for (int64_t k = 0; k < Q; ++k) {
+        int64_t i = q ? q[k] : k;
+        double b[3] = {INFINITY, INFINITY, INFINITY};
+        for (int64_t j = 0; j < M; ++j) {
+            if (j == i) continue;
+            double dx = pts[3 * j] - pts[3 * i], dy = pts[3 * j + 1] - pts[3 * i + 1], dz = pts[3 * j + 2] - pts[3 * i + 2];
+            double d = sqrt(dx * dx + dy * dy + dz * dz);
+            if (d < b[2]) {
+                if (d < b[1]) {
+                    b[2] = b[1];
+                    if (d < b[0]) { b[1] = b[0]; b[0] = d; } else b[1] = d;
+                } else {
+                    b[2] = d;
+                }
+            }
+        }
+        int m = M - 1 < 3 ? (int)(M - 1) : 3;
+        double acc = 0;
+        for (int t = 0; t < m; ++t) acc += b[t];
+        out[k] = m > 0 ? acc / m : 0.0;
+    }
+}
+
+/*
+ * Eq. 3: s_i = min(mu + 2 sigma, mbar_i) / 2 over the M mean 3-NN distances
+ * mbar (mu, sigma: their mean and population standard deviation).
+ */
+void orc_init_scales(const double* mbar, int64_t M, double* s, double* mu_out, double* sigma_out) {
+    double mu = 0, var = 0;
+    for (int64_t i = 0; i < M; ++i) mu += mbar[i];
+    mu /= (double)(M > 0 ? M : 1);
+    for (int64_t i = 0; i < M; ++i) var += (mbar[i] - mu) * (mbar[i] - mu);
+    var /= (double)(M > 0 ? M : 1);
+    double cap = mu + 2.0 * sqrt(var);
+    for (int64_t i = 0; i < M; ++i) s[i] = (mbar[i] < cap ? mbar[i] : cap) / 2.0;
+    if (mu_out) *mu_out = mu;
+    if (sigma_out) *sigma_out = sqrt(var);
 }
 
 /* ------------------------------------------------------------------------ */
