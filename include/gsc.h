@@ -281,6 +281,65 @@ gsc_status gsc_render_batch(const gsc_view* views, int32_t n_views, int32_t mode
 gsc_status gsc_loss(int32_t kind, const float* pred, const float* target, int32_t C, int32_t H, int32_t W,
                     const int32_t* crop, float* dL_dpred, float* loss_out, gsc_workspace* ws, gsc_stream_t stream);
 
+/* ------------------------------------------------------------------ */
+/* cache initialisation (Sec. 3.2 "Cache Initialization", Eq. 3)         */
+
+typedef struct gsc_init_params {
+    int64_t n_points;     /* N: points of level 0; level k gets N >> k (>= 4) */
+    int32_t levels;       /* K, 1..16 */
+    int32_t max_attempts; /* rays per point before giving up (0 = 4096) */
+    uint64_t seed;        /* Philox key; ray a of point i uses the counter (i, a, 0xffffffff) */
+    float opacity;        /* initial opacity of every Gaussian (0 = 0.1) */
+} gsc_init_params;
+
+/* Device scratch bytes gsc_cache_init needs for n_points points. */
+gsc_status gsc_init_scratch_size(int64_t n_points, size_t* bytes);
+
+/* Initial cache of K levels from one pass over the volume: point i casts
+ * random rays (origin on the unit sphere around the box centre, aimed at a
+ * uniform point of the box) until delta tracking finds a real collision, and
+ * records its position and albedo.  Level k holds points 0 .. (N >> k) - 1;
+ * each becomes a Gaussian at the point, coloured by its albedo, with
+ * identity rotation, the given opacity and the isotropic scale of Eq. 3,
+ * s = min(mu + 2 sigma, mean distance to the 3 nearest points of its level)
+ * / 2, mu and sigma being the mean and population standard deviation of
+ * those distances over the level.
+ *   scratch: device buffer of gsc_init_scratch_size bytes, 256-B aligned.
+ *   params:  device (sum_k N >> k) x 16, levels one after another (written).
+ * Synchronises `stream`; GSC_ERR_TIMEOUT if some point found no collision
+ * (e.g. an empty transfer function).  The paper has no further detail on the
+ * rays; this is the reading used. */
+gsc_status gsc_cache_init(const gsc_scene* sc, const gsc_init_params* p, void* scratch, size_t scratch_bytes,
+                          float* params, gsc_stream_t stream);
+
+/* One view of a training step: a cache level, its camera and its target
+ * buffer (the path tracer's buffer for this level, Sec. 3.5). */
+typedef struct gsc_train_view {
+    const float* params;  /* N x 16 packed records */
+    int64_t N;
+    gsc_camera cam;
+    const float* target;  /* 3 x H x W, the loss target x */
+    float* image;         /* 3 x H x W, the rendered level (written; NULL = not wanted) */
+    float* grads;         /* N x 16, accumulated (+=); views may share it */
+    float* loss;          /* device float: the view's loss (written) */
+} gsc_train_view;
+
+/* The per-frame training step of the cache (render, HDR loss of Sec. 3.6,
+ * backward of Sec. 3.5) for up to 32 views with the loss folded into the
+ * rasterizer: one binning and ONE persistent launch in which every tile
+ * composites its pixels front to back, evaluates the loss and dL/dC of each
+ * pixel against its target, writes the image, and runs the back-to-front
+ * gradient pass on the spot; then the per-Gaussian parameter gradients.  No
+ * per-pixel quantity outlives its tile.  Equals gsc_render_batch(FWD) +
+ * gsc_loss + gsc_render_batch(BWD) of the same views: images bit for bit,
+ * gradients up to the order of floating-point atomics, losses up to the
+ * order of summation.  loss_kind: GSC_LOSS_HDR or GSC_LOSS_HDR_FULLGRAD
+ * (pixel-local losses only; others give GSC_ERR_INVALID_ARG).  The workspace
+ * must be sized for the views' Gaussians and for n_views views.
+ * Graph-capturable. */
+gsc_status gsc_train_batch(const gsc_train_view* views, int32_t n_views, int32_t loss_kind,
+                           const gsc_raster_cfg* cfg, gsc_workspace* ws, gsc_stream_t stream);
+
 /* gsc_loss without a workspace, for callers that cannot allocate device
  * memory or hand the library a buffer at the point of the call: a plug-in
  * running inside a host application that owns every device allocation, a

@@ -47,9 +47,10 @@ def candidates(tiles=TILES, bins=BINS, caps=CAPS, ppts=PPTS):
 
 
 def time_config(levels, cam, ws: gsc.Workspace, tile, bin_size, cap, ppt=1, backward=True, reps=2, stream=None,
-                fused=False, forward=True):
+                fused=False, forward=True, train=False):
     """Mean ms of rendering (and/or differentiating) every level once; with
-    ``fused`` all levels go through one batched call per direction."""
+    ``fused`` all levels go through one batched call per direction; with
+    ``train`` all levels go through one training step (gsc_train_batch)."""
     c = cam if isinstance(cam, gsc.Camera) else gsc.camera(cam)
     cfg = gsc.raster_cfg(tile=tile, list_capacity=cap, bin_size=bin_size, pixels_per_thread=ppt)
     dev = levels[0].device
@@ -58,8 +59,15 @@ def time_config(levels, cam, ws: gsc.Workspace, tile, bin_size, cap, ppt=1, back
     grads = [torch.zeros_like(p) for p in levels]
     views = [dict(params=p, cam=c, image=im, dL_dimage=dl, grads=g) for p, im, g in zip(levels, imgs, grads)]
     s = torch.cuda.current_stream() if stream is None else stream
+    if train:
+        losses = torch.zeros(len(levels), dtype=torch.float32, device=dev)
+        tviews = [dict(params=p, cam=c, target=dl, image=im, grads=g, loss=losses[k])
+                  for k, (p, im, g) in enumerate(zip(levels, imgs, grads))]
 
     def once():
+        if train:
+            gsc.train_batch(tviews, cfg, ws, gsc.LOSS_HDR, stream=s)
+            return
         if fused:
             if forward:
                 gsc.render_batch(views, gsc.BATCH_FWD, cfg, ws, stream=s)
@@ -85,14 +93,14 @@ def time_config(levels, cam, ws: gsc.Workspace, tile, bin_size, cap, ppt=1, back
 
 
 def autotune(levels, cam, ws: gsc.Workspace, backward=True, cands=None, reps=2, verbose=False, fused=False,
-             forward=True):
+             forward=True, train=False):
     """Fastest (tile, bin, capacity, pixels per thread) for rendering and/or
     differentiating the given levels from `cam`.  Returns (best Trial, all
     trials)."""
     trials = []
     for tile, b, cap, q in (cands if cands is not None else candidates()):
         ms = time_config(levels, cam, ws, tile, b, cap, q, backward=backward, reps=reps, fused=fused,
-                         forward=forward)
+                         forward=forward, train=train)
         trials.append(Trial(tile, b, cap, q, ms))
         if verbose:
             print(f"tile {tile[0]}x{tile[1]} bin {b} cap {cap} ppt {q}: {ms:.3f} ms", flush=True)

@@ -20,7 +20,7 @@ OUT = os.path.join(HERE, "_lib")
 SO = os.path.join(OUT, "libgsc.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "sort.cu", "raster.cu", "trace.cu", "optim.cu"]
+SOURCES = ["api.cu", "sort.cu", "raster.cu", "trace.cu", "optim.cu", "init.cu"]
 EXTRA = {"trace.cu": ["-fmad=false"]}
 
 

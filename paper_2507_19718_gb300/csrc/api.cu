@@ -25,7 +25,8 @@ void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 namespace {
 const char* kPhaseNames[kNumPhases] = {"project", "depth_sort", "scan", "emit", "tile_sort", "ranges",
-                                       "render", "render_bwd", "project_bwd", "loss", "adamw", "trace"};
+                                       "render", "render_bwd", "project_bwd", "loss", "adamw", "trace", "train",
+                                       "init"};
 struct Pending {
     int phase, launches;
     cudaEvent_t a, b;
@@ -181,6 +182,9 @@ void add_view(BatchDev& b, const RasterDev& rc, const gsc_camera* cam, const flo
     v.image = image;
     v.dL = dL;
     v.grads = reinterpret_cast<float4*>(grads);
+    v.target = nullptr;
+    v.loss = nullptr;
+    v.invk = 1.f / (3.f * (float)cam->width * (float)cam->height);
     v.g_off = b.total_g;
     v.N = (uint32_t)N;
     v.tiles_x = (cam->width + rc.tile_w - 1) / rc.tile_w;
@@ -551,6 +555,97 @@ gsc_status gsc_render_batch(const gsc_view* views, int32_t n_views, int32_t mode
         if (e == cudaSuccess) e = launch_render_backward(b, rc, ws, vals, shared, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "gsc_render_batch launch");
+    return GSC_OK;
+}
+
+gsc_status gsc_train_batch(const gsc_train_view* views, int32_t n_views, int32_t loss_kind,
+                           const gsc_raster_cfg* cfg, gsc_workspace* ws, gsc_stream_t stream) {
+    if (!views || n_views < 1 || n_views > kMaxViews)
+        return fail(GSC_ERR_INVALID_ARG, "n_views must be in [1, %d]", kMaxViews);
+    if (loss_kind != GSC_LOSS_HDR && loss_kind != GSC_LOSS_HDR_FULLGRAD)
+        return fail(GSC_ERR_INVALID_ARG, "the training step folds in pixel-local losses only (HDR), not %d",
+                    loss_kind);
+    gsc_status st = check_cfg(cfg);
+    if (st) return st;
+    if (!ws) return fail(GSC_ERR_INVALID_ARG, "workspace is NULL");
+    int order[kMaxViews];
+    for (int i = 0; i < n_views; ++i) order[i] = i;
+    for (int i = 1; i < n_views; ++i)
+        for (int j = i; j > 0; --j) {
+            const gsc_camera& a = views[order[j - 1]].cam;
+            const gsc_camera& c = views[order[j]].cam;
+            if ((int64_t)a.width * a.height >= (int64_t)c.width * c.height) break;
+            int t = order[j - 1];
+            order[j - 1] = order[j];
+            order[j] = t;
+        }
+    int64_t total = 0;
+    bool shared = false;
+    for (int i = 0; i < n_views; ++i) {
+        const gsc_train_view& v = views[i];
+        if ((st = check_cam(&v.cam))) return st;
+        if ((st = check_ws(ws, v.N, &v.cam))) return st;
+        if (v.N > 0 && (!v.params || !aligned(v.params, 16) || !v.grads || !aligned(v.grads, 16)))
+            return fail(GSC_ERR_INVALID_ARG, "view %d: params/grads NULL or not 16-B aligned", i);
+        if (!v.target || !v.loss) return fail(GSC_ERR_INVALID_ARG, "view %d: target or loss is NULL", i);
+        total += v.N;
+        for (int j = 0; j < i; ++j)
+            if (v.grads && v.grads == views[j].grads) shared = true;
+    }
+    if (total > ws->max_gaussians)
+        return fail(GSC_ERR_INVALID_ARG, "the batch holds %lld Gaussians, the workspace %lld", (long long)total,
+                    (long long)ws->max_gaussians);
+    cudaStream_t s = (cudaStream_t)stream;
+    RasterDev rc = raster_dev(cfg);
+    BatchDev b;
+    batch_init(b);
+    for (int k = 0; k < n_views; ++k) {
+        const gsc_train_view& v = views[order[k]];
+        add_view(b, rc, &v.cam, v.params, v.N, v.image, nullptr, v.grads);
+        b.v[k].target = v.target;
+        b.v[k].loss = v.loss;
+    }
+    if ((int64_t)b.total_bins > ws->max_tiles)
+        return fail(GSC_ERR_INVALID_ARG, "the batch has %u bins, the workspace %lld (raise max_views)", b.total_bins,
+                    (long long)ws->max_tiles);
+    if ((size_t)b.total_tiles > ws->red_floats)
+        return fail(GSC_ERR_INVALID_ARG, "the batch has %u tiles, the loss scratch %zu", b.total_tiles,
+                    ws->red_floats);
+    const uint32_t* vals = nullptr;
+    cudaError_t e = bin_gaussians(b, rc, ws, &vals, s);
+    if (e == cudaSuccess)
+        e = launch_train(b, rc, ws, vals, loss_kind == GSC_LOSS_HDR_FULLGRAD ? 1 : 0, shared, s);
+    if (e != cudaSuccess) return cuda_fail(e, "gsc_train_batch launch");
+    return GSC_OK;
+}
+
+// ------------------------------------------------------------------ cache initialisation
+
+gsc_status gsc_init_scratch_size(int64_t n_points, size_t* bytes) {
+    if (!bytes || n_points < 4 || n_points > (int64_t)UINT32_MAX)
+        return fail(GSC_ERR_INVALID_ARG, "n_points must be in [4, 2^32)");
+    *bytes = init_layout(n_points, nullptr, nullptr);
+    return GSC_OK;
+}
+
+gsc_status gsc_cache_init(const gsc_scene* sc, const gsc_init_params* p, void* scratch, size_t scratch_bytes,
+                          float* params, gsc_stream_t stream) {
+    if (!sc || !p || !scratch || !params) return fail(GSC_ERR_INVALID_ARG, "NULL argument");
+    if (p->levels < 1 || p->levels > 16 || p->n_points < 4 || p->n_points > (int64_t)UINT32_MAX ||
+        (p->n_points >> (p->levels - 1)) < 4)
+        return fail(GSC_ERR_INVALID_ARG, "need levels in [1, 16] and at least 4 points in the last level");
+    float op = p->opacity > 0.f ? p->opacity : 0.1f;
+    if (!(op < 1.f)) return fail(GSC_ERR_INVALID_ARG, "opacity must be in (0, 1)");
+    int attempts = p->max_attempts > 0 ? p->max_attempts : 4096;
+    size_t need = init_layout(p->n_points, nullptr, nullptr);
+    if (scratch_bytes < need) return fail(GSC_ERR_INVALID_ARG, "scratch holds %zu bytes, %zu needed", scratch_bytes, need);
+    if (!aligned(scratch, 256) || !aligned(params, 16))
+        return fail(GSC_ERR_INVALID_ARG, "scratch must be 256-B and params 16-B aligned");
+    unsigned int fails = 0;
+    cudaError_t e = run_init(sc, p->n_points, p->levels, p->seed, attempts, op, (char*)scratch, params, &fails,
+                             (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "gsc_cache_init");
+    if (fails) return fail(GSC_ERR_TIMEOUT, "%u points found no interaction in %d rays each", fails, attempts);
     return GSC_OK;
 }
 

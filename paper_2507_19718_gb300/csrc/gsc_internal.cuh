@@ -34,7 +34,7 @@ struct RasterDev {
     float alpha_max, alpha_min, T_min, near_plane, dilation;
     int tile_w, tile_h, cap;
     int bin, spt_x, spt_y;  // bin size (px), tiles per bin side
-    int ppt;                // pixels per thread (1 or 2)
+    int ppt;                // pixels per thread (1, 2, 4 or 8)
 };
 
 // One view of a (possibly batched) render: its camera, its Gaussians (global
@@ -47,6 +47,9 @@ struct ViewDev {
     float* image;
     const float* dL;
     float4* grads;
+    const float* target;  // training step: the loss target (3 x H x W)
+    float* loss;          // training step: the view's loss (device scalar)
+    float invk;           // training step: 1 / (3 H W)
     uint32_t g_off, N, tile_off, bin_off;
     int tiles_x, tiles_y, bins_x, bins_y;
 };
@@ -68,13 +71,32 @@ __device__ __forceinline__ int view_of_tile(const BatchDev& b, uint32_t t) {
     return v;
 }
 
+// HDR loss of Sec. 3.6 per element, y = prediction, x = target:
+// (x - y)^2 / (y + 0.01)^2, and its derivative in y scaled by 1/k, with the
+// denominator held constant (full = 0) or differentiated too (full = 1).
+// One definition for the loss kernel and the fused training step, so both
+// produce the same gradient bits.
+constexpr int kLossNone = 0, kLossHdr = 1, kLossHdrFull = 2;
+__device__ __forceinline__ float hdr_term(float y, float x) {
+    float den = __fadd_rn(y, 0.01f), d = __fsub_rn(x, y);
+    float inv2 = __fdiv_rn(1.f, __fmul_rn(den, den));
+    return __fmul_rn(__fmul_rn(d, d), inv2);
+}
+__device__ __forceinline__ float hdr_grad(float y, float x, bool full, float invk) {
+    float den = __fadd_rn(y, 0.01f), d = __fsub_rn(x, y);
+    float inv2 = __fdiv_rn(1.f, __fmul_rn(den, den));
+    float g = __fmul_rn(__fmul_rn(2.f, __fsub_rn(y, x)), inv2);
+    if (full) g = __fsub_rn(g, __fdiv_rn(__fmul_rn(__fmul_rn(__fmul_rn(2.f, d), d), inv2), den));
+    return __fmul_rn(g, invk);
+}
+
 // sets the calling thread's last error message (api.cu) and returns st
 gsc_status set_error(gsc_status st, const char* fmt, ...);
 
 // instrumentation (api.cu): event-timed phases and the launch counter
 enum Phase : int {
     kPhProject, kPhDepthSort, kPhScan, kPhEmit, kPhTileSort, kPhRanges, kPhRender, kPhRenderBwd, kPhProjectBwd,
-    kPhLoss, kPhAdam, kPhTrace, kNumPhases
+    kPhLoss, kPhAdam, kPhTrace, kPhTrain, kPhInit, kNumPhases
 };
 void count_launch(int n);
 struct PhaseScope {
@@ -144,10 +166,25 @@ cudaError_t launch_render(const BatchDev& b, const RasterDev& rc, gsc_workspace*
 // shared_params: two views write the same parameter gradients (atomics needed)
 cudaError_t launch_render_backward(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
                                    bool shared_params, cudaStream_t s);
+// training step: render, HDR loss (full_grad: the denominator differentiated
+// too) and backward in one persistent launch; per-view loss to ViewDev::loss
+cudaError_t launch_train(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
+                         int full_grad, bool shared_params, cudaStream_t s);
 
 // trace.cu
 cudaError_t launch_trace(const gsc_scene* sc, const CamDev& cam, const gsc_trace_params& p, const float* cache,
                          float* targets, float* image, cudaStream_t s);
+// cache initialisation: delta-tracked point samples (pos, albedo; *fails
+// counts points without a collision in max_attempts rays)
+cudaError_t launch_init_sample(const gsc_scene* sc, uint32_t n, uint64_t seed, int max_attempts, float4* pos,
+                               float4* alb, unsigned int* fails, cudaStream_t s);
+
+// init.cu: scratch bytes for N points (layout measured with base = NULL),
+// and the whole initialisation (synchronises s; *fails_host as above)
+struct InitScratch;
+size_t init_layout(int64_t N, char* base, InitScratch* s);
+cudaError_t run_init(const gsc_scene* sc, int64_t N, int K, uint64_t seed, int max_attempts, float opacity,
+                     char* scratch, float* params, unsigned int* fails_host, cudaStream_t s);
 
 // optim.cu
 cudaError_t launch_loss(int kind, const float* pred, const float* target, int C, int H, int W, int x0, int y0,

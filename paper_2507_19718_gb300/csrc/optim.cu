@@ -39,14 +39,8 @@ __global__ void __launch_bounds__(kRedThreads) k_loss_hdr(const float* __restric
         int jj = (int)(r / w), ii = (int)(r - (size_t)jj * w);
         size_t p = ((size_t)ch * H + (y0 + jj)) * W + (x0 + ii);
         float y = pred[p], x = tgt[p];
-        float den = y + 0.01f, d = x - y;
-        float inv2 = 1.f / (den * den);
-        acc += d * d * inv2;
-        if (dL) {
-            float g = 2.f * (y - x) * inv2;
-            if (full) g -= 2.f * d * d * inv2 / den;
-            dL[p] = g * invk;
-        }
+        acc += hdr_term(y, x);
+        if (dL) dL[p] = hdr_grad(y, x, full != 0, invk);
     }
     float t = block_sum(acc, sm);
     if (threadIdx.x == 0) partial[blockIdx.x] = t;

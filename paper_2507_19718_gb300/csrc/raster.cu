@@ -515,23 +515,32 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float (&a)[8], int l
 // still in the ring; earlier ones are re-filtered from their recorded
 // position), stages their records, and per entry sums the nine 2D gradient
 // terms over the warp (reduce-scatter) before the global atomics.
+//
+// LOSS != kLossNone is the training step with the HDR loss folded in: phase 1
+// also composites the colours (the forward's arithmetic, so the image is the
+// forward's bit for bit), then every pixel evaluates the loss against its
+// target and its own dL/dC, writes the image and adds its loss term to the
+// tile's partial sum, and phase 2 runs on that gradient.  Nothing per pixel
+// leaves the tile.
 constexpr int kHitRing = 2048;
 constexpr int kMaxChunks = 512;
 
-template <int TW, int TH, int PPT>
+template <int TW, int TH, int PPT, int LOSS>
 __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_constant__ BatchDev b,
                                                              const uint2* __restrict__ ranges,
                                                              const uint32_t* __restrict__ vals,
                                                              const uint2* __restrict__ rect,
                                                              const float4* __restrict__ rec, RasterDev rc,
                                                              float4* __restrict__ g2d, uint32_t* __restrict__ queue,
-                                                             unsigned long long* __restrict__ stats) {
+                                                             unsigned long long* __restrict__ stats,
+                                                             float* __restrict__ tile_loss) {
     constexpr int NT = TW * TH / PPT;
     constexpr int ROWS = TH / PPT;
     extern __shared__ float4 smem[];
     __shared__ int s_warp[NT / 32];
     __shared__ uint32_t s_end;
     __shared__ uint32_t s_chunk_pos[kMaxChunks];
+    __shared__ float s_loss[NT / 32];
     const int cap = rc.cap;
     float4* s0 = smem;
     float4* s1 = smem + cap;
@@ -557,19 +566,25 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
     float fy[PPT], gr[PPT], gg[PPT], gb[PPT], T[PPT];
     bool active[PPT], done[PPT];
     uint32_t last[PPT], ev[PPT];
+    float Cr[PPT], Cg[PPT], Cb[PPT];  // composited colour (training step only)
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
         int py = py0 + q * ROWS;
         bool inside = px < cam.W && py < cam.H;
         fy[q] = (float)py + 0.5f;
         gr[q] = gg[q] = gb[q] = 0.f;
-        if (inside) {
-            size_t pix = (size_t)py * cam.W + px;
-            gr[q] = dL_dimg[pix];
-            gg[q] = dL_dimg[HW + pix];
-            gb[q] = dL_dimg[2 * HW + pix];
+        Cr[q] = Cg[q] = Cb[q] = 0.f;
+        if (LOSS == kLossNone) {
+            if (inside) {
+                size_t pix = (size_t)py * cam.W + px;
+                gr[q] = dL_dimg[pix];
+                gg[q] = dL_dimg[HW + pix];
+                gb[q] = dL_dimg[2 * HW + pix];
+            }
+            active[q] = inside && (gr[q] != 0.f || gg[q] != 0.f || gb[q] != 0.f);
+        } else {
+            active[q] = inside;  // the gradient is known after phase 1
         }
-        active[q] = inside && (gr[q] != 0.f || gg[q] != 0.f || gb[q] != 0.f);
         done[q] = !active[q];
         T[q] = 1.f;
         last[q] = 0;
@@ -606,6 +621,7 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
             if (hit) {
                 s0[staged + r] = a0;
                 s1[staged + r] = a1;
+                if (LOSS != kLossNone) s2[staged + r] = rec[3 * (size_t)g + 2];
                 uint32_t hid = nhit + r;
                 hits[hid % kHitRing] = g;
                 if (hid % kHitRing == 0 && hid / kHitRing < kMaxChunks) s_chunk_pos[hid / kHitRing] = c;
@@ -632,11 +648,52 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
                         ev[q] = h0 + (uint32_t)k + 1u;
                         continue;
                     }
+                    if (LOSS != kLossNone) {  // the forward's colour arithmetic
+                        float4 c = s2[k];
+                        float wgt = alpha * T[q];
+                        Cr[q] = fmaf(c.x, wgt, Cr[q]);
+                        Cg[q] = fmaf(c.y, wgt, Cg[q]);
+                        Cb[q] = fmaf(c.z, wgt, Cb[q]);
+                    }
                     T[q] = Tn;
                     last[q] = h0 + k + 1;
                     ++n_comp1;
                 }
             }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < PPT; ++q)
+        if (active[q]) n_eval1 += ev[q] == 0xffffffffu ? nhit : ev[q];
+    if (LOSS != kLossNone) {
+        // image out, loss term and dL/dC of every pixel; the tile's loss sum
+        // goes to its partial (fixed order: pixels of a thread, warp
+        // butterfly, warps in order)
+        float lsum = 0.f;
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            if (!active[q]) continue;
+            size_t pix = (size_t)(py0 + q * ROWS) * cam.W + px;
+            if (vw.image) {
+                vw.image[pix] = Cr[q];
+                vw.image[HW + pix] = Cg[q];
+                vw.image[2 * HW + pix] = Cb[q];
+            }
+            const float* tg = vw.target;
+            lsum += hdr_term(Cr[q], tg[pix]) + hdr_term(Cg[q], tg[HW + pix]) + hdr_term(Cb[q], tg[2 * HW + pix]);
+            gr[q] = hdr_grad(Cr[q], tg[pix], LOSS == kLossHdrFull, vw.invk);
+            gg[q] = hdr_grad(Cg[q], tg[HW + pix], LOSS == kLossHdrFull, vw.invk);
+            gb[q] = hdr_grad(Cb[q], tg[2 * HW + pix], LOSS == kLossHdrFull, vw.invk);
+            active[q] = gr[q] != 0.f || gg[q] != 0.f || gb[q] != 0.f;
+        }
+        lsum = warp_sum(lsum);
+        if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = lsum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+#pragma unroll
+            for (int w = 0; w < NT / 32; ++w) t += s_loss[w];
+            tile_loss[tile] = t;
         }
     }
     if (threadIdx.x == 0) s_end = 0;
@@ -647,7 +704,6 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render_bwd(const __grid_consta
         if (active[q]) {
             mylast = max(mylast, last[q]);
             n_eval2 += last[q];  // phase 2 evaluates this pixel at entries [0, last)
-            n_eval1 += ev[q] == 0xffffffffu ? nhit : ev[q];
         }
     if (mylast) atomicMax(&s_end, mylast);
     __syncthreads();
@@ -976,11 +1032,11 @@ static cudaError_t render_t(const BatchDev& b, const RasterDev& rc, gsc_workspac
     return cudaGetLastError();
 }
 
-template <int TW, int TH, int PPT>
+template <int TW, int TH, int PPT, int LOSS>
 static cudaError_t render_bwd_t(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
                                 cudaStream_t s) {
     size_t smem = sizeof(float4) * 3 * rc.cap + sizeof(uint32_t) * kHitRing;
-    auto kern = k_render_bwd<TW, TH, PPT>;
+    auto kern = k_render_bwd<TW, TH, PPT, LOSS>;
     static int cached = 32 * 1024;
     cudaError_t e = ensure_smem(kern, smem, &cached);
     if (e != cudaSuccess) return e;
@@ -989,8 +1045,24 @@ static cudaError_t render_bwd_t(const BatchDev& b, const RasterDev& rc, gsc_work
     int grid = persistent_grid(kern, TW * TH / PPT, smem, b.total_tiles, &gs, &gg);
     cudaMemsetAsync(ws->counters + kCntTilesBwd, 0, sizeof(uint32_t), s);
     kern<<<grid, TW * TH / PPT, smem, s>>>(b, ws->ranges, vals, ws->rect, ws->rec, rc, ws->g2d,
-                                           ws->counters + kCntTilesBwd, ws->stats);
+                                           ws->counters + kCntTilesBwd, ws->stats, ws->red);
     return cudaGetLastError();
+}
+
+template <int TW, int TH, int PPT>
+static cudaError_t bwd_plain(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
+                             cudaStream_t s) {
+    return render_bwd_t<TW, TH, PPT, kLossNone>(b, rc, ws, vals, s);
+}
+template <int TW, int TH, int PPT>
+static cudaError_t bwd_train_hdr(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
+                                 cudaStream_t s) {
+    return render_bwd_t<TW, TH, PPT, kLossHdr>(b, rc, ws, vals, s);
+}
+template <int TW, int TH, int PPT>
+static cudaError_t bwd_train_hdr_full(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws,
+                                      const uint32_t* vals, cudaStream_t s) {
+    return render_bwd_t<TW, TH, PPT, kLossHdrFull>(b, rc, ws, vals, s);
 }
 
 // the (tile, pixels per thread) pairs compiled; the API accepts exactly these
@@ -1030,23 +1102,64 @@ cudaError_t launch_render(const BatchDev& b, const RasterDev& rc, gsc_workspace*
     GSC_TILE_DISPATCH(render_t, b, rc, ws, vals, s)
 }
 
+// per view: the sum of its tiles' loss partials (in order, FP64) / k
+__global__ void k_view_loss(const __grid_constant__ BatchDev b, const float* __restrict__ tile_loss) {
+    __shared__ double sm[32];
+    const ViewDev& vw = b.v[blockIdx.x];
+    const uint32_t n = (uint32_t)vw.tiles_x * (uint32_t)vw.tiles_y;
+    double acc = 0.0;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) acc += (double)tile_loss[vw.tile_off + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sm[k];
+        if (vw.loss) *vw.loss = (float)(t * (double)vw.invk);
+    }
+}
+
+static cudaError_t project_backward(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, bool shared_params,
+                                    cudaStream_t s) {
+    uint32_t nblk = (b.total_g + 127) / 128;
+    if (nblk == 0) nblk = 1;
+    PhaseScope ph(kPhProjectBwd, s, 1);
+    k_project_bwd<<<nblk, 128, 0, s>>>(b, rc, ws->cnt, ws->g2d, shared_params ? 1 : 0);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_render_backward(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
                                    bool shared_params, cudaStream_t s) {
     cudaError_t e;
     {
         PhaseScope ph(kPhRenderBwd, s, 1);
         cudaMemsetAsync(ws->g2d, 0, sizeof(float4) * 3 * (size_t)b.total_g, s);
-        auto launch = [&]() -> cudaError_t { GSC_TILE_DISPATCH(render_bwd_t, b, rc, ws, vals, s) };
+        auto launch = [&]() -> cudaError_t { GSC_TILE_DISPATCH(bwd_plain, b, rc, ws, vals, s) };
         e = launch();
     }
     if (e != cudaSuccess) return e;
-    uint32_t nblk = (b.total_g + 127) / 128;
-    if (nblk == 0) nblk = 1;
+    return project_backward(b, rc, ws, shared_params, s);
+}
+
+cudaError_t launch_train(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
+                         int full_grad, bool shared_params, cudaStream_t s) {
+    cudaError_t e;
     {
-        PhaseScope ph(kPhProjectBwd, s, 1);
-        k_project_bwd<<<nblk, 128, 0, s>>>(b, rc, ws->cnt, ws->g2d, shared_params ? 1 : 0);
+        PhaseScope ph(kPhTrain, s, 2);
+        cudaMemsetAsync(ws->g2d, 0, sizeof(float4) * 3 * (size_t)b.total_g, s);
+        auto launch = [&]() -> cudaError_t {
+            if (full_grad) { GSC_TILE_DISPATCH(bwd_train_hdr_full, b, rc, ws, vals, s) }
+            GSC_TILE_DISPATCH(bwd_train_hdr, b, rc, ws, vals, s)
+        };
+        e = launch();
+        if (e == cudaSuccess) {
+            k_view_loss<<<b.nviews, 256, 0, s>>>(b, ws->red);
+            e = cudaGetLastError();
+        }
     }
-    return cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return project_backward(b, rc, ws, shared_params, s);
 }
 
 }  // namespace gsc

@@ -324,9 +324,45 @@ __global__ void __launch_bounds__(128) k_trace(TraceDev v, CamDev cam, const flo
         for (int c = 0; c < 3; ++c) targets[((size_t)k * 3 + c) * HW + pix] = tgt[k][c] / (float)v.spp;
 }
 
-cudaError_t launch_trace(const gsc_scene* sc, const CamDev& cam, const gsc_trace_params& p, const float* cache,
-                         float* targets, float* image, cudaStream_t s) {
-    TraceDev v;
+// Cache initialisation, point sampling (Sec. 3.2 "Cache Initialization"):
+// point i casts rays until delta tracking finds a real collision and keeps
+// its position and albedo.  Attempt a uses the Philox stream (i, a,
+// kInitStream); the ray starts on the unit sphere around the box centre and
+// points at a uniform point of the box.  Points that find no collision in
+// max_attempts rays are counted in *fails (and left at the origin).
+constexpr uint32_t kInitStream = 0xffffffffu;
+
+__global__ void __launch_bounds__(128) k_init_sample(TraceDev v, uint32_t n, int max_attempts,
+                                                     float4* __restrict__ pos, float4* __restrict__ alb,
+                                                     unsigned int* __restrict__ fails) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float x[3] = {0.0f, 0.0f, 0.0f}, a3[3] = {0.0f, 0.0f, 0.0f};
+    bool found = false;
+    for (int a = 0; a < max_attempts && !found; ++a) {
+        Philox r;
+        r.init(i, (uint32_t)a, kInitStream, v.k0, v.k1);
+        float u0 = r.uniform(), u1 = r.uniform();
+        float sd[3], o[3], d[3];
+        sphere_dir(u0, u1, sd);
+        for (int k = 0; k < 3; ++k) o[k] = 0.5f + sd[k];
+        for (int k = 0; k < 3; ++k) d[k] = r.uniform() - o[k];
+        float n2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+        float inv = 1.0f / sqrtf(n2);
+        for (int k = 0; k < 3; ++k) d[k] = d[k] * inv;
+        if (free_flight(v, r, o, d, x)) {
+            float sn = norm_density(v, x);
+            for (int c = 0; c < 3; ++c) a3[c] = v.albedo * tf_channel(v, sn, c);
+            found = true;
+        }
+    }
+    if (!found) atomicAdd(fails, 1u);
+    pos[i] = make_float4(x[0], x[1], x[2], 0.0f);
+    alb[i] = make_float4(a3[0], a3[1], a3[2], 0.0f);
+}
+
+static TraceDev trace_dev(const gsc_scene* sc) {
+    TraceDev v{};
     const gsc_scene_desc& d = sc->desc;
     v.grid = d.density;
     v.nx = d.nx; v.ny = d.ny; v.nz = d.nz;
@@ -343,6 +379,22 @@ cudaError_t launch_trace(const gsc_scene* sc, const CamDev& cam, const gsc_trace
     }
     v.has_dir = (d.light_radiance[0] > 0.0f || d.light_radiance[1] > 0.0f || d.light_radiance[2] > 0.0f);
     v.has_env = (d.env_radiance[0] > 0.0f || d.env_radiance[1] > 0.0f || d.env_radiance[2] > 0.0f);
+    return v;
+}
+
+cudaError_t launch_init_sample(const gsc_scene* sc, uint32_t n, uint64_t seed, int max_attempts, float4* pos,
+                               float4* alb, unsigned int* fails, cudaStream_t s) {
+    TraceDev v = trace_dev(sc);
+    v.k0 = (uint32_t)seed;
+    v.k1 = (uint32_t)(seed >> 32);
+    PhaseScope ph(kPhInit, s, 1);
+    k_init_sample<<<(n + 127) / 128, 128, 0, s>>>(v, n, max_attempts, pos, alb, fails);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace(const gsc_scene* sc, const CamDev& cam, const gsc_trace_params& p, const float* cache,
+                         float* targets, float* image, cudaStream_t s) {
+    TraceDev v = trace_dev(sc);
     v.spp = p.spp; v.B = p.max_bounces; v.K = p.levels;
     v.frame = p.frame;
     v.k0 = (uint32_t)p.seed;

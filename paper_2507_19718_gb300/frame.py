@@ -45,17 +45,25 @@ class FrameLoop:
     (one binning and one persistent launch per direction over all levels,
     Sec. 5's joint rasterisation of the level sets) and steps all levels with
     one AdamW launch over their contiguous parameter store; otherwise every
-    level goes through its own calls."""
+    level goes through its own calls.
+
+    ``fused_train`` (default, with ``fused``): when the tracer does not read
+    the cache images (C <= 0), a frame is trace -> one training step that
+    renders every level, evaluates the HDR loss against its buffer and
+    differentiates in the same launch (gsc_train_batch) -> AdamW.  The
+    rendered images are the same bits as a separate forward."""
 
     def __init__(self, scene: synth.Scene, level_sizes, width: int, height: int, spp: int = 1,
                  max_bounces: int = 8, seed: int = synth.BASE_SEED, tile=(16, 16), list_capacity: int = 256,
                  max_pairs: int | None = None, weight_decay: float = 0.01, lr=None, device: str = "cuda",
-                 gaussian_seed: int | None = None, C_term: float = 0.0, bin_size: int = 0, fused: bool = True):
+                 gaussian_seed: int | None = None, C_term: float = 0.0, bin_size: int = 0, fused: bool = True,
+                 fused_train: bool = True):
         self.width, self.height = width, height
         self.spp, self.max_bounces, self.seed = spp, max_bounces, seed
         self.K = len(level_sizes)
         self.C_term = C_term
         self.fused = fused
+        self.fused_train = fused and fused_train
         self.scene = gsc.Scene.from_synth(scene, device)
         gs = seed + 1000 if gaussian_seed is None else gaussian_seed
         total = int(sum(level_sizes))
@@ -140,11 +148,24 @@ class FrameLoop:
             gsc.cache_backward(L.params, c, cfg_b, self.ws, self.dL[k], L.grads, stream=stream)
             gsc.cache_step(L.params, L.grads, L.m, L.v, adam, stream=stream)
 
+    def train_step(self, c: gsc.Camera, lr_scale: float, stream=None):
+        """Render + HDR loss + backward of all levels in one launch, then AdamW."""
+        self.adam_step += 1
+        adam = gsc.adam_params(self.lr, weight_decay=self.weight_decay, lr_scale=lr_scale, step=self.adam_step)
+        views = [dict(params=L.params, cam=c, target=self.targets[k], image=self.renders[k], grads=L.grads,
+                      loss=self.losses[k]) for k, L in enumerate(self.levels)]
+        gsc.train_batch(views, self.cfg_bwd or self.cfg, self.ws, gsc.LOSS_HDR, stream=stream)
+        gsc.cache_step(*self.store, adam, stream=stream)
+
     def frame(self, cam, frame: int, stream=None):
         """One frame: render the cache (its images feed the tracer when C > 0),
         trace the targets, then train every level on its buffer."""
         c = cam if isinstance(cam, gsc.Camera) else gsc.camera(cam)
         lr_scale = self._schedule(c)
+        if self.fused_train and self.C_term <= 0:
+            self.trace(c, frame, stream)
+            self.train_step(c, lr_scale, stream)
+            return self.losses
         self.render_levels(c, stream)
         self.trace(c, frame, stream)
         self.train_levels(c, lr_scale, stream)

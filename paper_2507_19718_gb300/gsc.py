@@ -52,12 +52,22 @@ class TraceParams(C.Structure):
                 ("seed", C.c_uint64), ("C", C.c_float), ("eps", C.c_float)]
 
 
+class InitParams(C.Structure):
+    _fields_ = [("n_points", C.c_int64), ("levels", C.c_int32), ("max_attempts", C.c_int32), ("seed", C.c_uint64),
+                ("opacity", C.c_float)]
+
+
 class View(C.Structure):
     _fields_ = [("params", C.c_void_p), ("N", C.c_int64), ("cam", Camera), ("image", C.c_void_p),
                 ("dL_dimage", C.c_void_p), ("grads", C.c_void_p)]
 
 
 BATCH_FWD, BATCH_BWD = 1, 2
+
+
+class TrainView(C.Structure):
+    _fields_ = [("params", C.c_void_p), ("N", C.c_int64), ("cam", Camera), ("target", C.c_void_p),
+                ("image", C.c_void_p), ("grads", C.c_void_p), ("loss", C.c_void_p)]
 
 
 class Profile(C.Structure):
@@ -82,6 +92,8 @@ SIGNATURES = {
     "gsc_scene_set_tf": (_i32, [_vp, _i32, _vp, _vp]),
     "gsc_scene_destroy": (_i32, [_vp]),
     "gsc_trace": (_i32, [_vp, C.POINTER(Camera), C.POINTER(TraceParams), _vp, _vp, _vp, _vp]),
+    "gsc_init_scratch_size": (_i32, [C.c_int64, C.POINTER(_sz)]),
+    "gsc_cache_init": (_i32, [_vp, C.POINTER(InitParams), _vp, _sz, _vp, _vp]),
     "gsc_workspace_size": (_i32, [_i64, _i64, _i32, _i32, _i32, C.POINTER(RasterCfg), C.POINTER(_sz)]),
     "gsc_workspace_create": (_i32, [_vp, _sz, _i64, _i64, _i32, _i32, _i32, C.POINTER(RasterCfg),
                                     C.POINTER(_vp)]),
@@ -91,6 +103,7 @@ SIGNATURES = {
     "gsc_cache_render": (_i32, [_vp, _i64, C.POINTER(Camera), C.POINTER(RasterCfg), _vp, _vp, _vp]),
     "gsc_cache_backward": (_i32, [_vp, _i64, C.POINTER(Camera), C.POINTER(RasterCfg), _vp, _vp, _vp, _vp]),
     "gsc_render_batch": (_i32, [C.POINTER(View), _i32, _i32, C.POINTER(RasterCfg), _vp, _vp]),
+    "gsc_train_batch": (_i32, [C.POINTER(TrainView), _i32, _i32, C.POINTER(RasterCfg), _vp, _vp]),
     "gsc_loss": (_i32, [_i32, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
     "gsc_loss_noalloc": (_i32, [_i32, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp]),
     "gsc_cache_step": (_i32, [_vp, _vp, _vp, _vp, _i64, C.POINTER(AdamParams), _vp]),
@@ -266,6 +279,28 @@ def trace(scene: Scene, cam, spp: int, max_bounces: int, levels: int, seed: int,
     return targets, image
 
 
+def cache_init(scene: Scene, n_points: int, levels: int, seed: int, opacity: float = 0.1, max_attempts: int = 0,
+               stream=None):
+    """gsc_cache_init: the initial cache of Sec. 3.2 / Eq. 3.  Returns the
+    (sum_k N >> k, 16) parameter tensor and its per-level views."""
+    dev = scene.density.device
+    nbytes = _sz()
+    _check(lib().gsc_init_scratch_size(n_points, C.byref(nbytes)))
+    scratch = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=dev)
+    base = (scratch.data_ptr() + 255) & ~255
+    sizes = [n_points >> k for k in range(levels)]
+    params = torch.empty((sum(sizes), 16), dtype=torch.float32, device=dev)
+    p = InitParams()
+    p.n_points, p.levels, p.max_attempts, p.seed, p.opacity = n_points, levels, max_attempts, seed, opacity
+    _check(lib().gsc_cache_init(scene.handle, C.byref(p), C.c_void_p(base), nbytes.value, params.data_ptr(),
+                                _stream(stream)))
+    out, r = [], 0
+    for n in sizes:
+        out.append(params[r:r + n])
+        r += n
+    return params, out
+
+
 # ---------------------------------------------------------------- workspaces, raster
 
 class Workspace:
@@ -361,6 +396,31 @@ def render_batch(views, mode: int, cfg: RasterCfg, ws: Workspace, stream=None):
             arr[i].dL_dimage = v["dL_dimage"].data_ptr()
             arr[i].grads = v["grads"].data_ptr()
     _check(lib().gsc_render_batch(arr, len(views), mode, C.byref(cfg), ws.handle, _stream(stream)))
+
+
+def train_batch(views, cfg: RasterCfg, ws: Workspace, loss_kind: int = 0, stream=None):
+    """gsc_train_batch: render + HDR loss + backward of every view in one
+    launch.  views: dicts with params (N x 16), cam, target (3 x H x W),
+    grads (N x 16, +=), loss (device scalar) and optionally image."""
+    arr = (TrainView * len(views))()
+    for i, v in enumerate(views):
+        p = v["params"]
+        _need(p, "params")
+        c = v["cam"] if isinstance(v["cam"], Camera) else camera(v["cam"])
+        npx = 3 * c.width * c.height
+        _need(v["target"], "target", npx)
+        _need(v["grads"], "grads", p.numel())
+        arr[i].params = p.data_ptr()
+        arr[i].N = p.numel() // 16
+        arr[i].cam = c
+        arr[i].target = v["target"].data_ptr()
+        arr[i].grads = v["grads"].data_ptr()
+        _need(v["loss"], "loss", 1)
+        arr[i].loss = v["loss"].data_ptr()
+        if v.get("image") is not None:
+            _need(v["image"], "image", npx)
+            arr[i].image = v["image"].data_ptr()
+    _check(lib().gsc_train_batch(arr, len(views), loss_kind, C.byref(cfg), ws.handle, _stream(stream)))
 
 
 def loss(kind: int, pred: torch.Tensor, target: torch.Tensor, ws: Workspace, crop=None,

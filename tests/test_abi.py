@@ -90,6 +90,9 @@ def test_host_side_validation(L):
     cfg0 = gsc.raster_cfg()
     assert L.gsc_render_batch(views, 33, 1, C.byref(cfg0), None, None) == gsc.GSC_ERR_INVALID_ARG
     assert L.gsc_render_batch(views, 2, 4, C.byref(cfg0), None, None) == gsc.GSC_ERR_INVALID_ARG
+    tviews = (gsc.TrainView * 2)()
+    assert L.gsc_train_batch(tviews, 0, 0, C.byref(cfg0), None, None) == gsc.GSC_ERR_INVALID_ARG
+    assert L.gsc_train_batch(tviews, 2, gsc.LOSS_L1_SSIM, C.byref(cfg0), None, None) == gsc.GSC_ERR_INVALID_ARG
     # render: bad tile shape, then NULL workspace
     cam = gsc.Camera()
     cam.fx = cam.fy = 100.0

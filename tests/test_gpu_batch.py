@@ -108,10 +108,10 @@ def test_batch_replays_from_a_cuda_graph(gpu):
 
 
 def test_frame_loop_fused_levels_match_per_level_calls(gpu):
-    """The frame loop's fused path (all levels in one batch per direction, one
-    AdamW launch over the contiguous store) gives the per-level path's
-    renders bit for bit and the same trained parameters (up to the order of
-    the FP32 gradient atomics)."""
+    """The frame loop's fused path (all levels in one training step with the
+    loss folded in, one AdamW launch over the contiguous store) gives the
+    per-level path's renders bit for bit and the same trained parameters (up
+    to the order of the FP32 gradient atomics and of the loss sums)."""
     import torch
     from paper_2507_19718_gb300.frame import FrameLoop
     sc = synth.scene_tiny()
@@ -126,9 +126,60 @@ def test_frame_loop_fused_levels_match_per_level_calls(gpu):
         if f == 0:
             assert torch.equal(a.renders, b.renders)
             assert torch.equal(a.targets, b.targets)
-            assert torch.equal(la, lb)
+            # the fused training step sums the loss per tile: same terms, other order
+            np.testing.assert_allclose(la.cpu().numpy(), lb.cpu().numpy(), rtol=2e-6)
     a.ws.status()
     b.ws.status()
     for La, Lb in zip(a.levels, b.levels):
         np.testing.assert_allclose(La.params.cpu().numpy(), Lb.params.cpu().numpy(), rtol=1e-4, atol=1e-5)
     assert float(a.renders.abs().max()) > 0
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_train_batch_equals_render_loss_backward(gpu, kind):
+    """gsc_train_batch (render + HDR loss + backward in one launch) against
+    the separate calls on the same views: images bit for bit, losses to
+    summation order, gradients to atomic order."""
+    import torch
+    scenes, views = _setup(gpu)
+    cfg = gpu.raster_cfg(tile=(16, 16), list_capacity=256, bin_size=32, pixels_per_thread=2)
+    ws = _ws(gpu, scenes, len(views))
+    rng = np.random.default_rng(77)
+    targets = [torch.from_numpy(rng.uniform(0, 1, v["image"].shape).astype(np.float32)).cuda() for v in views]
+    grads_a = [torch.zeros_like(s) for s in scenes]
+    losses_a = torch.zeros(len(views), device="cuda")
+    imgs_a = [torch.zeros_like(v["image"]) for v in views]
+    tv = [dict(params=v["params"], cam=v["cam"], target=t, image=im, grads=grads_a[v["scene"]], loss=losses_a[i])
+          for i, (v, t, im) in enumerate(zip(views, targets, imgs_a))]
+    gpu.train_batch(tv, cfg, ws, kind)
+    ws.status()
+    # the same step through the separate calls
+    grads_b = [torch.zeros_like(s) for s in scenes]
+    for v in views:
+        v["grads"] = grads_b[v["scene"]]
+    gpu.render_batch(views, gpu.BATCH_FWD, cfg, ws)
+    losses_b = []
+    for v, t in zip(views, targets):
+        val, dl = gpu.loss(kind, v["image"], t, ws)
+        v["dL_dimage"] = dl
+        losses_b.append(float(val))
+    gpu.render_batch(views, gpu.BATCH_BWD, cfg, ws)
+    ws.status()
+    for v, im in zip(views, imgs_a):
+        assert torch.equal(v["image"], im)
+    np.testing.assert_allclose(losses_a.cpu().numpy(), losses_b, rtol=2e-6)
+    for a, b in zip(grads_a, grads_b):
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-6 * np.abs(b).max())
+        assert np.abs(b).max() > 0
+
+
+def test_train_batch_rejects_non_local_losses(gpu):
+    import torch
+    scenes, views = _setup(gpu)
+    ws = _ws(gpu, scenes, 1)
+    v = views[0]
+    tv = [dict(params=v["params"], cam=v["cam"], target=torch.zeros_like(v["image"]),
+               grads=torch.zeros_like(v["params"]), loss=torch.zeros((), device="cuda"))]
+    with pytest.raises(gpu.GscError):
+        gpu.train_batch(tv, gpu.raster_cfg(), ws, gpu.LOSS_L1_SSIM)
