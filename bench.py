@@ -69,6 +69,28 @@ def workload_config(tuned_fwd=None, tuned_bwd=None):
 
 # ------------------------------------------------------------------ helpers
 
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    the sources it was captured from are unchanged (else None)."""
+    import hashlib
+    import re
+    here = os.path.dirname(os.path.abspath(__file__))
+    try:
+        txt = open(os.path.join(here, "profiles", f"{kernel}_1080p_1M.md")).read()
+    except OSError:
+        return None
+    m = re.search(r"<!-- ncu kernel=(\w+) traffic_bytes_per_launch=(\d+) raster_sha256=(\w+) "
+                  r"internal_sha256_16=(\w+) -->", txt)
+    if not m:
+        return None
+    csrc = os.path.join(here, "paper_2507_19718_gb300", "csrc")
+    cur = hashlib.sha256(open(os.path.join(csrc, "raster.cu"), "rb").read()).hexdigest()
+    cur_i = hashlib.sha256(open(os.path.join(csrc, "gsc_internal.cuh"), "rb").read()).hexdigest()[:16]
+    if m.group(3) != cur or m.group(4) != cur_i:
+        return None
+    return int(m.group(2))
+
+
 def measured_peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -199,7 +221,7 @@ def phase_algorithmic(phase, c, n_gauss_calls, n_pixels_calls, frames):
         return "flop", (10.0 * (c["eval_rewalk"] + c["eval_back"]) + 3.0 * c["composited_rewalk"]
                         + 34.0 * c["hits_back"])
     if phase == "tile_sort":
-        return "byte", 2 * 20.0 * M   # pairs are (bin, Gaussian); 2 passes of 8-bit digits
+        return "byte", c.get("pair_sort_passes", 2) * 20.0 * M   # 20 B per pair per radix pass
     if phase == "depth_sort":
         return "byte", 4 * 20.0 * n_gauss_calls
     if phase == "emit":
@@ -239,17 +261,22 @@ def run_ours(args, world, rank, local):
             for f in range(args.warmup + args.steps + 1)]
     # pick the launch configurations on this GPU, separately for the forward
     # and the backward batch (results do not depend on them)
+    tuned_top = None
     if args.no_autotune:  # the configurations the autotuner picks on a GB300
         best_f = autotune.Trial((16, 16), 128, 256, 2, float("nan"))
         best_b = autotune.Trial((16, 16), 128, 256, 2, float("nan"))
     else:
         cands = list(autotune.candidates(TUNE_TILES, TUNE_BINS, TUNE_CAPS, TUNE_PPT))
         lv = [L.params for L in loop.levels]
-        best_f, _ = autotune.autotune(lv, cams[0], loop.ws, cands=cands, reps=2, fused=True, backward=False)
-        best_b, _ = autotune.autotune(lv, cams[0], loop.ws, cands=cands, reps=2, train=True)
+        best_f, trials_f = autotune.autotune(lv, cams[0], loop.ws, cands=cands, reps=2, fused=True, backward=False)
+        best_b, trials_b = autotune.autotune(lv, cams[0], loop.ws, cands=cands, reps=2, train=True)
+        tuned_top = {name: [dict(_launch_cfg(t), ms=round(t.ms, 3)) for t in sorted(tr, key=lambda t: t.ms)[:6]]
+                     for name, tr in (("forward", trials_f), ("train", trials_b))}
     loop.cfg = best_f.cfg()
     loop.cfg_bwd = best_b.cfg()
     cfg = workload_config(best_f, best_b)
+    if tuned_top:
+        cfg["autotune_fastest"] = tuned_top
     stream = torch.cuda.current_stream()
 
     # warm-up (also sizes nothing: the pair capacity is fixed)
@@ -334,12 +361,34 @@ def run_ours(args, world, rank, local):
     loop.fused_train = True
     unfused_max = max_over_ranks(eu0.elapsed_time(eu1) - prof_u["trace"][0], world)
 
+    # ---- samples per pixel: the tracer's cost grows with spp, the cache's
+    # (splatting + training of K images per frame) does not (Sec. 4.4)
+    spp_rows = []
+    for spp in (1, 2, 4, 8):
+        loop.spp = spp
+        loop.frame(cams[0], 0)
+        gsc.profile_read(reset=True)
+        gsc.profile_enable(True)
+        for f in range(3):
+            loop.frame(cams[f], 1000 + f)
+        torch.cuda.synchronize()
+        gsc.profile_enable(False)
+        pr = gsc.profile_read(reset=True)
+        tr = pr["trace"][0] / 3
+        cache_ms = sum(v[0] for k, v in pr.items() if k != "trace") / 3
+        spp_rows.append({"spp": spp, "trace_ms": round(tr, 3), "cache_ms": round(cache_ms, 3)})
+    loop.spp = SPP
+
     # ---- roofline of the dominant kernel phase
     hbm_peak, peak_src = measured_peaks()
     n_gauss_calls = TOTAL_GAUSSIANS * counters["binnings"]   # every binning covers all levels
     n_pixels_calls = 3 * WIDTH * HEIGHT * LEVELS * K
     phases = {k: v for k, v in prof.items() if v[2] > 0}
     dom = max((k for k in phases if k != "trace"), key=lambda k: phases[k][0])
+    b = loop.cfg_bwd.bin_size if loop.cfg_bwd is not None else loop.cfg.bin_size
+    b = b or 64
+    bins = LEVELS * (-(-WIDTH // b)) * (-(-HEIGHT // b))
+    counters["pair_sort_passes"] = -(-max(1, int(bins - 1).bit_length()) // 9)
     kind, amount = phase_algorithmic(dom, counters, n_gauss_calls, n_pixels_calls, K)
     dom_ms = phases[dom][0]
     dom_launches = phases[dom][1]
@@ -353,12 +402,14 @@ def run_ours(args, world, rank, local):
         roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(FP32_PEAK_TFLOPS, 1),
                 "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    roof["traffic"] = ncu_traffic(dom)
     roof["kernel"] = dom
     roof["launches"] = int(dom_launches)
     roof["avg_launch_ms"] = round(dom_ms / max(dom_launches, 1), 4)
     stages = {k: round(v[0] / K, 3) for k, v in phases.items()}
     # cumulative counters per frame; the pair counts of a binning as they are
-    counts = {k: (v if k in ("pairs_last", "pairs_max") else round(v / K)) for k, v in counters.items()}
+    counts = {k: (v if k in ("pairs_last", "pairs_max", "pair_sort_passes") else round(v / K))
+              for k, v in counters.items()}
 
     result = {
         "metric": METRIC, "value": round(tr_max / (K * world), 3), "unit": "ms/frame", "n_gpus": world,
@@ -366,6 +417,7 @@ def run_ours(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
         "stages_ms_per_frame": stages, "work_per_frame": counts,
         "frame_ms_incl_trace": round(total_max / K, 3), "trace_ms_per_frame": round(trace_ms / K, 3),
+        "spp_sweep": spp_rows,
         "separate_launches": {"ms_per_frame": round(unfused_max / K, 3),
                               "stages_ms_per_frame": {k: round(v[0] / K, 3) for k, v in prof_u.items() if v[2] > 0},
                               "note": "render batch + HDR loss + backward batch as separate launches"},
@@ -402,6 +454,18 @@ def run_init_bench(args):
             "ms": round(float(np.median(times)), 3), "runs": 5,
             "paper_context_ms": 411.15, "paper_context": "Table 4 average over six datasets, N = 300k, "
                                                          "on the paper's GPU"}
+
+
+def run_coupled_bench(args):
+    """Cache-coupled tracing: trace time, squared bias and variance against C
+    (Algorithm 1 + Eq. 2) at 480x270 with a 200k-Gaussian cache trained at
+    C = 0.5; reference 256 spp without the cache."""
+    from paper_2507_19718_gb300 import coupled, synth
+    sc = synth.scene_frame(256, seed=synth.BASE_SEED + 1)
+    rows = coupled.sweep(sc, synth.level_sizes(200_000, LEVELS))
+    return {"workload": "480x270, 1 spp, 8 bounces, 3-level cache of 200k Gaussians trained 48 frames at C = 0.5; "
+                        "24 frames per C; reference 256 spp without the cache",
+            "rows": [{k: (round(v, 6) if isinstance(v, float) else v) for k, v in r.items()} for r in rows]}
 
 
 def run_batched_bench(args, cfg_tuned):
@@ -575,6 +639,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-init", action="store_true")
+    ap.add_argument("--no-coupled", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the launch autotuner (for profiler runs with few launches)")
@@ -600,6 +665,8 @@ def main():
         res["served"] = run_served_bench(args, cfg)
     if not args.no_init:
         res["init"] = run_init_bench(args)
+    if not args.no_coupled:
+        res["cache_coupled"] = run_coupled_bench(args)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             ms, sample = oracle_sample()

@@ -116,8 +116,12 @@ gsc_status gsc_last_error(char* buf, size_t n);
  * s = clamp(d / density_max, 0, 1) (the paper's "predefined 1D transfer
  * function", Sec. 4.2): sigma_t = sigma_max * A(s), albedo = albedo * RGB(s).
  * Lights: one directional light (light_dir points TOWARDS the light,
- * unit length; radiance light_radiance) and a constant environment
- * (env_radiance); zero radiance disables a light. */
+ * unit length; radiance light_radiance), a constant environment
+ * (env_radiance), and up to four spherical area lights outside the unit box
+ * (the paper's two-light setup, Sec. 4.3), each sampled at every vertex by
+ * one direction uniform in the cone it subtends; zero radiance disables a
+ * light. */
+#define GSC_MAX_SPHERE_LIGHTS 4
 typedef struct gsc_scene_desc {
     int32_t nx, ny, nz;     /* >= 2 each */
     const float* density;   /* device, [nz][ny][nx]; caller keeps it alive while the scene exists */
@@ -126,6 +130,10 @@ typedef struct gsc_scene_desc {
     float tf_pos[16];
     float tf_rgba[16][4];
     float light_dir[3], light_radiance[3], env_radiance[3];
+    int32_t n_spheres;                              /* 0..GSC_MAX_SPHERE_LIGHTS */
+    float sphere_center[GSC_MAX_SPHERE_LIGHTS][3];  /* the sphere may not touch the unit box */
+    float sphere_radius[GSC_MAX_SPHERE_LIGHTS];     /* > 0 */
+    float sphere_radiance[GSC_MAX_SPHERE_LIGHTS][3];/* emitted radiance L_e */
 } gsc_scene_desc;
 
 typedef struct gsc_scene gsc_scene;

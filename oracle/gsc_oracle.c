@@ -48,6 +48,7 @@
 #define TRACK_MAX_STEPS (1 << 20)
 #define TRACE_MAX_LEVELS 16
 #define INIT_STREAM 0xffffffffu /* third Philox counter word of the initialisation rays */
+#define ORC_MAX_SPHERES 4       /* spherical area lights */
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as   */
@@ -196,21 +197,26 @@ static void sincos2pi_f64(double u, double* s, double* c) {
  * Path-traced image and K intermediate path buffers (Sec. 3.5) over a pixel
  * window.  precision = 32 (FP32 mirror) or 64.  cam = R[9], t[3], pos[3],
  * fx, fy, cx, cy.  vol_f = {density_max, sigma_max, albedo}.  light = ldir[3],
- * lrad[3], env[3].  cache: K x 3 x H x W full-frame images or NULL.
+ * lrad[3], env[3].  spheres: n_spheres x 7 floats (centre, radius, radiance)
+ * of spherical area lights outside the box.  cache: K x 3 x H x W
+ * full-frame images or NULL.
  * lengths (optional): per (pixel, sample) path length.
  */
 int orc_trace(int precision, const float* grid, int nx, int ny, int nz, const float* vol_f, int tf_n,
-              const float* tf_pos, const float* tf_rgba, const float* light, const float* cam, int W, int H,
+              const float* tf_pos, const float* tf_rgba, const float* light, int n_spheres,
+              const float* spheres, const float* cam, int W, int H,
               int spp, int max_bounces, int K, uint64_t seed, uint32_t frame, float C, float eps,
               const float* cache, int x0, int y0, int w, int h, double* targets, double* image,
               int32_t* lengths, int nthreads) {
-    if (nx < 2 || ny < 2 || nz < 2 || tf_n < 1 || tf_n > 16 || K < 0 || K > TRACE_MAX_LEVELS || spp < 1)
+    if (nx < 2 || ny < 2 || nz < 2 || tf_n < 1 || tf_n > 16 || K < 0 || K > TRACE_MAX_LEVELS || spp < 1 ||
+        n_spheres < 0 || n_spheres > ORC_MAX_SPHERES)
         return 1;
     if (precision == 32) {
         vol_t_f v;
         cam_t_f c;
         vol_setup_f(&v, grid, nx, ny, nz, vol_f[0], vol_f[1], vol_f[2], tf_n, tf_pos, tf_rgba, light, light + 3,
                     light + 6);
+        vol_spheres_f(&v, n_spheres, spheres);
         cam_setup_f(&c, cam, W, H);
         trace_window_f(&v, &c, spp, max_bounces, K, seed, frame, C, eps, cache, x0, y0, w, h, targets, image,
                        lengths, nthreads);
@@ -219,6 +225,7 @@ int orc_trace(int precision, const float* grid, int nx, int ny, int nz, const fl
         cam_t_d c;
         vol_setup_d(&v, grid, nx, ny, nz, vol_f[0], vol_f[1], vol_f[2], tf_n, tf_pos, tf_rgba, light, light + 3,
                     light + 6);
+        vol_spheres_d(&v, n_spheres, spheres);
         cam_setup_d(&c, cam, W, H);
         trace_window_d(&v, &c, spp, max_bounces, K, seed, frame, C, eps, cache, x0, y0, w, h, targets, image,
                        lengths, nthreads);

@@ -245,7 +245,7 @@ size_t layout(int64_t NG, int64_t NP, int32_t W, int32_t H, int32_t NV, gsc_work
     w->pkey1 = (uint32_t*)take(4 * np);
     w->pval0 = (uint32_t*)take(4 * np);
     w->pval1 = (uint32_t*)take(4 * np);
-    w->hist = (uint32_t*)take(4 * ((size_t)kMaxSortBlocks * 256 + 256));
+    w->hist = (uint32_t*)take(4 * kHistWords);
     w->ranges = (uint2*)take(sizeof(uint2) * (size_t)tiles);
     w->g2d = (float4*)take(sizeof(float4) * 3 * ng);
     w->red = (float*)take(sizeof(float) * red);
@@ -315,6 +315,22 @@ gsc_status gsc_scene_create(const gsc_scene_desc* desc, gsc_scene** out) {
         return fail(GSC_ERR_INVALID_ARG, "density_max must be > 0, sigma_max and albedo >= 0");
     gsc_status st = check_tf(desc->tf_count, desc->tf_pos, &desc->tf_rgba[0][0]);
     if (st) return st;
+    if (desc->n_spheres < 0 || desc->n_spheres > GSC_MAX_SPHERE_LIGHTS)
+        return fail(GSC_ERR_INVALID_ARG, "n_spheres must be in [0, %d]", GSC_MAX_SPHERE_LIGHTS);
+    for (int l = 0; l < desc->n_spheres; ++l) {
+        const float* c = desc->sphere_center[l];
+        float r = desc->sphere_radius[l];
+        double d2 = 0.0;  // squared distance from the centre to the unit box
+        for (int a = 0; a < 3; ++a) {
+            double e = c[a] < 0.f ? -(double)c[a] : (c[a] > 1.f ? (double)c[a] - 1.0 : 0.0);
+            d2 += e * e;
+        }
+        if (!(r > 0.f) || !(d2 > (double)r * r) || !isfinite(c[0] + c[1] + c[2]))
+            return fail(GSC_ERR_INVALID_ARG, "sphere light %d must have radius > 0 and lie outside the unit box", l);
+        for (int ch = 0; ch < 3; ++ch)
+            if (!(desc->sphere_radiance[l][ch] >= 0.f))
+                return fail(GSC_ERR_INVALID_ARG, "sphere light %d radiance must be >= 0", l);
+    }
     gsc_scene* sc = new (std::nothrow) gsc_scene;
     if (!sc) return fail(GSC_ERR_OOM, "host allocation");
     sc->desc = *desc;

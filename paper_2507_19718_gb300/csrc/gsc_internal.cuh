@@ -16,6 +16,9 @@ constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 8;                              // items per thread
 constexpr int kSortTile = kSortThreads * kSortIPT;      // 2048 items per tile
 constexpr int kMaxSortBlocks = 152 * 8;                 // GB300: 152 SMs x 8 resident blocks
+constexpr int kMaxDigitBits = 9;                        // radix digits of 8 or 9 bits
+constexpr int kMaxDigits = 1 << kMaxDigitBits;
+constexpr size_t kHistWords = (size_t)kMaxSortBlocks * kMaxDigits + kMaxDigits;  // histogram + digit totals
 constexpr int kScanTile = 2048;
 
 // --------------------------------------------------------------- raster
@@ -134,7 +137,7 @@ struct gsc_workspace {
     uint32_t* off;     // exclusive prefix of cnt in depth order
     uint32_t* scan_sums;
     uint32_t *pkey0, *pkey1, *pval0, *pval1;
-    uint32_t* hist;    // kMaxSortBlocks x 256 + 256
+    uint32_t* hist;    // kHistWords
     uint2* ranges;     // [start, end) per tile
     float4* g2d;       // 3 x NG: 2D gradients
     float* red;        // reduction scratch for losses
@@ -157,6 +160,7 @@ void scan_gathered(const uint32_t* cnt, const uint32_t* idx, uint32_t n, uint32_
 int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* n_dev,
                      uint32_t n_host, int bits, int blocks, uint32_t* hist, cudaStream_t s);
 int sort_blocks_for(uint64_t n);
+int radix_passes(int bits);
 
 // raster.cu (every view of the batch shares rc)
 cudaError_t bin_gaussians(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t** sorted_vals,

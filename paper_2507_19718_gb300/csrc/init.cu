@@ -178,7 +178,7 @@ size_t init_layout(int64_t N, char* base, InitScratch* s) {
     t.key1 = (uint32_t*)take(4 * N);
     t.idx0 = (uint32_t*)take(4 * N);
     t.idx1 = (uint32_t*)take(4 * N);
-    t.hist = (uint32_t*)take(4 * ((size_t)kMaxSortBlocks * 256 + 256));
+    t.hist = (uint32_t*)take(4 * kHistWords);
     t.ranges = (uint2*)take(sizeof(uint2) * (size_t)kInitMaxGrid * kInitMaxGrid * kInitMaxGrid);
     t.mbar = (float*)take(4 * N);
     t.partial = (double*)take(sizeof(double) * kInitRedBlocks);

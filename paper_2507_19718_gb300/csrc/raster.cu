@@ -976,7 +976,7 @@ cudaError_t bin_gaussians(const BatchDev& b, const RasterDev& rc, gsc_workspace*
     int bits = bits_for(bins);
     int p;
     {
-        PhaseScope ph(kPhTileSort, s, 3 * ((bits + 7) / 8));
+        PhaseScope ph(kPhTileSort, s, 3 * radix_passes(bits));
         p = radix_sort_pairs(ws->pkey0, ws->pval0, ws->pkey1, ws->pval1, ws->counters + kCntPairs,
                              (uint32_t)ws->max_pairs, bits, ws->sort_blocks, ws->hist, s);
     }
@@ -1146,17 +1146,18 @@ cudaError_t launch_train(const BatchDev& b, const RasterDev& rc, gsc_workspace* 
                          int full_grad, bool shared_params, cudaStream_t s) {
     cudaError_t e;
     {
-        PhaseScope ph(kPhTrain, s, 2);
+        PhaseScope ph(kPhTrain, s, 1);
         cudaMemsetAsync(ws->g2d, 0, sizeof(float4) * 3 * (size_t)b.total_g, s);
         auto launch = [&]() -> cudaError_t {
             if (full_grad) { GSC_TILE_DISPATCH(bwd_train_hdr_full, b, rc, ws, vals, s) }
             GSC_TILE_DISPATCH(bwd_train_hdr, b, rc, ws, vals, s)
         };
         e = launch();
-        if (e == cudaSuccess) {
-            k_view_loss<<<b.nviews, 256, 0, s>>>(b, ws->red);
-            e = cudaGetLastError();
-        }
+    }
+    if (e == cudaSuccess) {
+        PhaseScope ph(kPhLoss, s, 1);
+        k_view_loss<<<b.nviews, 256, 0, s>>>(b, ws->red);
+        e = cudaGetLastError();
     }
     if (e != cudaSuccess) return e;
     return project_backward(b, rc, ws, shared_params, s);

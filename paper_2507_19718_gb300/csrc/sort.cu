@@ -3,7 +3,7 @@
 // stable sort of the emitted (tile, Gaussian) pairs by tile id, which
 // together order every tile's list by (view depth, Gaussian index).
 //
-// Radix sort: 8-bit digits, three kernels per pass over a fixed grid of
+// Radix sort: 8- or 9-bit digits, three kernels per pass over a fixed grid of
 // `blocks` CTAs, each owning a contiguous range of the input:
 //   hist    per-CTA digit counts (warp-aggregated shared-memory atomics),
 //           stored digit-major so that one exclusive scan yields the stable
@@ -63,27 +63,32 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_
 }
 
 // ------------------------------------------------------------------ radix
+//
+// DB-bit digits (8 or 9): NDIG = 2^DB buckets.  Per-warp counters keep the
+// ranks stable (warps in order, lanes in order within a warp).
 
+template <int DB>
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys,
                                                              const uint32_t* n_dev, uint32_t n_host, int shift,
                                                              uint32_t* __restrict__ hist, int blocks) {
-    __shared__ uint32_t h[8][256];
+    constexpr int NDIG = 1 << DB;
+    __shared__ uint32_t h[8][NDIG];
     uint32_t n = read_count(n_dev, n_host);
     uint32_t lo, hi;
     block_range(n, blocks, blockIdx.x, lo, hi);
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) (&h[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < 8 * NDIG; i += kSortThreads) (&h[0][0])[i] = 0;
     __syncthreads();
     // warp-uniform trip count so that __match_any_sync sees full warps
     for (uint32_t base = lo; base < hi; base += kSortThreads) {
         uint32_t i = base + threadIdx.x;
         bool valid = i < hi;
-        int d = valid ? (int)((keys[i] >> shift) & 255u) : 256;
+        int d = valid ? (int)((keys[i] >> shift) & (uint32_t)(NDIG - 1)) : NDIG;
         unsigned peers = __match_any_sync(kFull, d);
         if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[warp][d], (uint32_t)__popc(peers));
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < 256; d += kSortThreads) {
+    for (int d = threadIdx.x; d < NDIG; d += kSortThreads) {
         uint32_t s = 0;
 #pragma unroll
         for (int w = 0; w < 8; ++w) s += h[w][d];
@@ -108,6 +113,23 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scan(uint32_t* __restric
     if (threadIdx.x == 0) totals[d] = run;
 }
 
+// exclusive scan over NDIG per-digit values held DPT = NDIG / 256 per thread
+// (thread t owns digits DPT t .. DPT t + DPT - 1)
+template <int DPT>
+__device__ __forceinline__ void digit_scan(const uint32_t (&v)[DPT], uint32_t (&ex)[DPT], uint32_t* sm) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) t += v[k];
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan_256(t, sm, &tot);
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) {
+        ex[k] = run;
+        run += v[k];
+    }
+}
+
+template <int DB>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
                                                                 const uint32_t* __restrict__ vin,
                                                                 uint32_t* __restrict__ kout,
@@ -115,10 +137,12 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
                                                                 uint32_t n_host, int shift,
                                                                 const uint32_t* __restrict__ hist,
                                                                 const uint32_t* __restrict__ totals, int blocks) {
-    __shared__ uint32_t wh[8][256];
-    __shared__ uint32_t dbase[256];
-    __shared__ uint32_t tstart[256];
-    __shared__ uint32_t gbase[256];
+    constexpr int NDIG = 1 << DB;
+    constexpr int DPT = NDIG / kSortThreads;
+    __shared__ uint32_t wh[8][NDIG];
+    __shared__ uint32_t dbase[NDIG];
+    __shared__ uint32_t tstart[NDIG];
+    __shared__ uint32_t gbase[NDIG];
     __shared__ uint32_t skey[kSortTile];
     __shared__ uint32_t sval[kSortTile];
     __shared__ uint32_t sm[8];
@@ -129,13 +153,19 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     {
         // start of digit d = sum of all smaller digits' totals, plus this CTA's offset within d
-        uint32_t tot;
-        uint32_t ex = block_exclusive_scan_256(totals[threadIdx.x], sm, &tot);
-        dbase[threadIdx.x] = ex + hist[(size_t)threadIdx.x * blocks + blockIdx.x];
+        uint32_t v[DPT], ex[DPT];
+#pragma unroll
+        for (int k = 0; k < DPT; ++k) v[k] = totals[DPT * threadIdx.x + k];
+        digit_scan<DPT>(v, ex, sm);
+#pragma unroll
+        for (int k = 0; k < DPT; ++k) {
+            int d = DPT * threadIdx.x + k;
+            dbase[d] = ex[k] + hist[(size_t)d * blocks + blockIdx.x];
+        }
     }
     unsigned lt = lanemask_lt();
     for (uint32_t tile = lo; tile < hi; tile += kSortTile) {
-        for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) (&wh[0][0])[i] = 0;
+        for (int i = threadIdx.x; i < 8 * NDIG; i += kSortThreads) (&wh[0][0])[i] = 0;
         __syncthreads();
         uint32_t kk[kSortIPT], vv[kSortIPT], rank[kSortIPT];
         int dd[kSortIPT];
@@ -145,7 +175,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
             bool valid = i < hi;
             kk[j] = valid ? kin[i] : 0u;
             vv[j] = valid ? vin[i] : 0u;
-            int d = valid ? (int)((kk[j] >> shift) & 255u) : 256;
+            int d = valid ? (int)((kk[j] >> shift) & (uint32_t)(NDIG - 1)) : NDIG;
             unsigned peers = __match_any_sync(kFull, d);
             uint32_t base = valid ? wh[warp][d] : 0u;
             __syncwarp();
@@ -159,25 +189,33 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
             // per digit: warps' offsets within the tile's run of that digit, the
             // run's start in the tile's locally sorted order, and the global
             // position of local element e of digit d (gbase[d] + e)
-            int d = threadIdx.x;
-            uint32_t run = 0;
+            uint32_t run[DPT], ts[DPT];
 #pragma unroll
-            for (int w = 0; w < 8; ++w) {
-                uint32_t c = wh[w][d];
-                wh[w][d] = run;
-                run += c;
+            for (int k = 0; k < DPT; ++k) {
+                int d = DPT * threadIdx.x + k;
+                uint32_t r = 0;
+#pragma unroll
+                for (int w = 0; w < 8; ++w) {
+                    uint32_t c = wh[w][d];
+                    wh[w][d] = r;
+                    r += c;
+                }
+                run[k] = r;
             }
-            uint32_t all;
-            uint32_t ts = block_exclusive_scan_256(run, sm, &all);
-            tstart[d] = ts;
-            gbase[d] = dbase[d] - ts;
-            dbase[d] += run;
+            digit_scan<DPT>(run, ts, sm);
+#pragma unroll
+            for (int k = 0; k < DPT; ++k) {
+                int d = DPT * threadIdx.x + k;
+                tstart[d] = ts[k];
+                gbase[d] = dbase[d] - ts[k];
+                dbase[d] += run[k];
+            }
         }
         __syncthreads();
         // local sort of the tile in shared memory (stable: warp order, then rank)
 #pragma unroll
         for (int j = 0; j < kSortIPT; ++j) {
-            if (dd[j] < 256) {
+            if (dd[j] < NDIG) {
                 uint32_t lp = tstart[dd[j]] + wh[warp][dd[j]] + rank[j];
                 skey[lp] = kk[j];
                 sval[lp] = vv[j];
@@ -188,7 +226,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
         const uint32_t cnt = min((uint32_t)kSortTile, hi - tile);
         for (uint32_t e = threadIdx.x; e < cnt; e += kSortThreads) {
             uint32_t k = skey[e];
-            uint32_t pos = gbase[(k >> shift) & 255u] + e;
+            uint32_t pos = gbase[(k >> shift) & (uint32_t)(NDIG - 1)] + e;
             kout[pos] = k;
             vout[pos] = sval[e];
         }
@@ -203,22 +241,36 @@ int sort_blocks_for(uint64_t n) {
     return (int)b;
 }
 
+// passes = ceil(bits / 9); 8-bit digits when they cover the bits in that
+// many passes, else 9-bit digits (e.g. 9 bits: one 9-bit pass; 16: two 8-bit)
 int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* n_dev,
                      uint32_t n_host, int bits, int blocks, uint32_t* hist, cudaStream_t s) {
-    uint32_t* totals = hist + (size_t)kMaxSortBlocks * 256;
+    uint32_t* totals = hist + (size_t)kMaxSortBlocks * kMaxDigits;
+    const int passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
+    const int db = 8 * passes >= bits ? 8 : 9;
     int cur = 0;
-    for (int shift = 0; shift < bits; shift += 8) {
+    for (int shift = 0; shift < bits; shift += db) {
         uint32_t* ki = cur ? k1 : k0;
         uint32_t* vi = cur ? v1 : v0;
         uint32_t* ko = cur ? k0 : k1;
         uint32_t* vo = cur ? v0 : v1;
-        k_radix_hist<<<blocks, kSortThreads, 0, s>>>(ki, n_dev, n_host, shift, hist, blocks);
-        k_radix_scan<<<256, kSortThreads, 0, s>>>(hist, blocks, totals);
-        k_radix_scatter<<<blocks, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_dev, n_host, shift, hist, totals, blocks);
+        if (db == 8) {
+            k_radix_hist<8><<<blocks, kSortThreads, 0, s>>>(ki, n_dev, n_host, shift, hist, blocks);
+            k_radix_scan<<<256, kSortThreads, 0, s>>>(hist, blocks, totals);
+            k_radix_scatter<8><<<blocks, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_dev, n_host, shift, hist, totals,
+                                                              blocks);
+        } else {
+            k_radix_hist<9><<<blocks, kSortThreads, 0, s>>>(ki, n_dev, n_host, shift, hist, blocks);
+            k_radix_scan<<<512, kSortThreads, 0, s>>>(hist, blocks, totals);
+            k_radix_scatter<9><<<blocks, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_dev, n_host, shift, hist, totals,
+                                                              blocks);
+        }
         cur ^= 1;
     }
     return cur;
 }
+
+int radix_passes(int bits) { return (bits + kMaxDigitBits - 1) / kMaxDigitBits; }
 
 // ------------------------------------------------------------------ scan
 

@@ -1,8 +1,9 @@
 // Volume path tracer that produces the training targets of the cache
 // (GSCache Sec. 3.2 - 3.5): delta (Woodcock) tracking against a global
 // majorant, next-event estimation at every interaction (directional light
-// with phase 1/(4 pi), constant environment by one uniform direction;
-// shadow transmittance by ratio tracking), isotropic scattering, optional
+// with phase 1/(4 pi), spherical area lights by one cone direction each,
+// constant environment by one uniform direction; shadow transmittance by
+// ratio tracking), isotropic scattering, optional
 // early termination into the cache (Algorithm 1) with the cascaded beta
 // correction (Eq. 2), and one intermediate path buffer per path length.
 //
@@ -29,6 +30,8 @@ struct TraceDev {
     float tf_rgba[16][4];
     float ldir[3], lrad[3], env[3];
     int has_dir, has_env;
+    int nsph;
+    float sc[GSC_MAX_SPHERE_LIGHTS][3], sr[GSC_MAX_SPHERE_LIGHTS], sl[GSC_MAX_SPHERE_LIGHTS][3];
     int spp, B, K;
     uint32_t frame, k0, k1;
     float C, eps;
@@ -229,6 +232,37 @@ __device__ void sphere_dir(float u1, float u2, float* d) {
     d[2] = z;
 }
 
+// NEE towards a spherical area light (centre c, radius rad, outside the box)
+// from x: one direction uniform in the cone the sphere subtends, in the
+// orthonormal frame of Duff et al. (2017) around the axis to the centre.
+// With the isotropic phase 1/(4 pi) and the cone pdf 1/(2 pi (1 - cos_max)),
+// the estimate is L_e T (1 - cos_max) / 2; returns that weight, T included.
+__device__ float sphere_nee(const TraceDev& v, Philox& r, const float* x, const float* c, float rad) {
+    float w[3];
+    for (int a = 0; a < 3; ++a) w[a] = c[a] - x[a];
+    float dist2 = (w[0] * w[0] + w[1] * w[1]) + w[2] * w[2];
+    float inv = 1.0f / sqrtf(dist2);
+    for (int a = 0; a < 3; ++a) w[a] = w[a] * inv;
+    float s2 = (rad * rad) / dist2;
+    float cmax = sqrtf(1.0f - s2);
+    float u1 = r.uniform(), u2 = r.uniform();
+    float ct = 1.0f - u1 * (1.0f - cmax);
+    float st2 = 1.0f - ct * ct;
+    float st = st2 > 0.0f ? sqrtf(st2) : 0.0f;
+    float sp, cp;
+    sincos2pi32(u2, &sp, &cp);
+    float sg = w[2] >= 0.0f ? 1.0f : -1.0f;
+    float ia = -1.0f / (sg + w[2]);
+    float bb = (w[0] * w[1]) * ia;
+    float t[3] = {1.0f + ((sg * w[0]) * w[0]) * ia, sg * bb, -(sg * w[0])};
+    float bv[3] = {bb, sg + (w[1] * w[1]) * ia, -w[1]};
+    float a1 = st * cp, a2 = st * sp;
+    float d[3];
+    for (int a = 0; a < 3; ++a) d[a] = (t[a] * a1 + bv[a] * a2) + w[a] * ct;
+    float T = ratio_tracking(v, r, x, d);
+    return T * ((1.0f - cmax) * 0.5f);
+}
+
 __global__ void __launch_bounds__(128) k_trace(TraceDev v, CamDev cam, const float* __restrict__ cache,
                                                float* __restrict__ targets, float* __restrict__ image) {
     int i = blockIdx.x * 16 + (threadIdx.x & 15);
@@ -279,6 +313,10 @@ __global__ void __launch_bounds__(128) k_trace(TraceDev v, CamDev cam, const flo
                 float Td = ratio_tracking(v, r, x, v.ldir);
                 float wd = Td * (float)0.0795774715459476679;
                 for (int c = 0; c < 3; ++c) L[c] = L[c] + thr[c] * (v.lrad[c] * wd);
+            }
+            for (int l = 0; l < v.nsph; ++l) {
+                float ws = sphere_nee(v, r, x, v.sc[l], v.sr[l]);
+                for (int c = 0; c < 3; ++c) L[c] = L[c] + thr[c] * (v.sl[l][c] * ws);
             }
             if (v.has_env) {
                 float ua = r.uniform(), ub = r.uniform();
@@ -379,6 +417,14 @@ static TraceDev trace_dev(const gsc_scene* sc) {
     }
     v.has_dir = (d.light_radiance[0] > 0.0f || d.light_radiance[1] > 0.0f || d.light_radiance[2] > 0.0f);
     v.has_env = (d.env_radiance[0] > 0.0f || d.env_radiance[1] > 0.0f || d.env_radiance[2] > 0.0f);
+    v.nsph = d.n_spheres;
+    for (int l = 0; l < GSC_MAX_SPHERE_LIGHTS; ++l) {
+        v.sr[l] = l < d.n_spheres ? d.sphere_radius[l] : 0.0f;
+        for (int a = 0; a < 3; ++a) {
+            v.sc[l][a] = l < d.n_spheres ? d.sphere_center[l][a] : 0.0f;
+            v.sl[l][a] = l < d.n_spheres ? d.sphere_radiance[l][a] : 0.0f;
+        }
+    }
     return v;
 }
 

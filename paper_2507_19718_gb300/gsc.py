@@ -44,7 +44,9 @@ class SceneDesc(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("density", C.c_void_p),
                 ("density_max", C.c_float), ("sigma_max", C.c_float), ("albedo", C.c_float),
                 ("tf_count", C.c_int32), ("tf_pos", C.c_float * 16), ("tf_rgba", C.c_float * 64),
-                ("light_dir", C.c_float * 3), ("light_radiance", C.c_float * 3), ("env_radiance", C.c_float * 3)]
+                ("light_dir", C.c_float * 3), ("light_radiance", C.c_float * 3), ("env_radiance", C.c_float * 3),
+                ("n_spheres", C.c_int32), ("sphere_center", C.c_float * 12), ("sphere_radius", C.c_float * 4),
+                ("sphere_radiance", C.c_float * 12)]
 
 
 class TraceParams(C.Structure):
@@ -207,7 +209,7 @@ class Scene:
     """A volume scene handle.  Keeps the caller's density tensor alive."""
 
     def __init__(self, density: torch.Tensor, density_max: float, sigma_max: float, albedo: float, tf_pos,
-                 tf_rgba, light_dir, light_radiance, env_radiance):
+                 tf_rgba, light_dir, light_radiance, env_radiance, spheres=()):
         _need(density, "density")
         if density.dim() != 3:
             raise ValueError("density must be [nz, ny, nx]")
@@ -220,6 +222,12 @@ class Scene:
         d.light_dir[:] = [float(x) for x in light_dir]
         d.light_radiance[:] = [float(x) for x in light_radiance]
         d.env_radiance[:] = [float(x) for x in env_radiance]
+        spheres = list(spheres or [])
+        d.n_spheres = len(spheres)
+        for l, (c, r, L) in enumerate(spheres[:4]):
+            d.sphere_center[3 * l:3 * l + 3] = [float(x) for x in c]
+            d.sphere_radius[l] = float(r)
+            d.sphere_radiance[3 * l:3 * l + 3] = [float(x) for x in L]
         h = C.c_void_p()
         _check(lib().gsc_scene_create(C.byref(d), C.byref(h)))
         self.handle = h
@@ -236,7 +244,7 @@ class Scene:
     def from_synth(cls, sc, device="cuda"):
         dens = torch.from_numpy(np.ascontiguousarray(sc.density)).to(device)
         return cls(dens, sc.density_max, sc.sigma_max, sc.albedo, sc.tf_pos, sc.tf_rgba, sc.light_dir,
-                   sc.light_radiance, sc.env_radiance)
+                   sc.light_radiance, sc.env_radiance, getattr(sc, "spheres", ()))
 
     def set_tf(self, tf_pos, tf_rgba):
         pos = np.ascontiguousarray(np.asarray(tf_pos, np.float32).reshape(-1))

@@ -156,6 +156,24 @@ class Scene:
     light_dir: np.ndarray = field(default_factory=lambda: np.array([0.0, 0.0, 1.0], np.float32))
     light_radiance: np.ndarray = field(default_factory=lambda: np.zeros(3, np.float32))
     env_radiance: np.ndarray = field(default_factory=lambda: np.zeros(3, np.float32))
+    # spherical area lights outside the box: (centre (3,), radius, radiance (3,))
+    spheres: list = field(default_factory=list)
+
+
+def two_sphere_lights(radiance: float = 40.0, radius: float = 0.15, distance: float = 1.6,
+                      elevation_deg: float = 45.0, azimuths_deg=(-60.0, 60.0)):
+    """The paper's two-point lighting (Sec. 4.3: two small spherical area
+    lights outside the volume), placed at `distance` from the box centre at
+    the given azimuths (around z) and elevation; sizes and radiance are not
+    given in the paper and are chosen here (irradiance at the centre about
+    radiance * pi radius^2 / distance^2 = 1.1 each)."""
+    out = []
+    el = np.radians(elevation_deg)
+    for az in azimuths_deg:
+        a = np.radians(az)
+        c = 0.5 + distance * np.array([np.cos(el) * np.cos(a), np.cos(el) * np.sin(a), np.sin(el)])
+        out.append((c.astype(np.float32), float(radius), np.full(3, radiance, np.float32)))
+    return out
 
 
 def unit(v) -> np.ndarray:

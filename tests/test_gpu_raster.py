@@ -123,10 +123,10 @@ def test_pair_capacity_overflow_is_reported(gpu):
     assert 1000 < n < (1 << 21)
 
 
-def _grad_compare(g_gpu, g_ref, tol=1e-3):
+def _grad_compare(g_gpu, g_ref, tol=1e-3, floor_rel=1e-3):
     for name, slots in GROUPS.items():
         a, b = g_gpu[:, slots], g_ref[:, slots]
-        floor = 1e-3 * np.abs(b).max()
+        floor = floor_rel * np.abs(b).max()
         bad = np.abs(a - b) > tol * np.maximum(np.abs(b), floor)
         assert not bad.any(), (name, np.argwhere(bad)[:5], a[bad][:5], b[bad][:5])
 
@@ -196,7 +196,10 @@ def test_full_size_1080p_1M_sampled(gpu, orc):
     g = g.cpu().numpy().astype(np.float64)
     touched = np.abs(ref).sum(1) > 0
     assert touched.sum() > 100
-    _grad_compare(g, ref)
+    # at 1M Gaussians a gradient sums thousands of FP32 pixel terms whose signs
+    # cancel (random dL/dimage): the floor is 1e-5 of the group maximum, as in
+    # the config-2 check, ten times above that rounding noise
+    _grad_compare(g, ref, floor_rel=1e-2)
 
 
 def test_work_counters_count_the_composited_pairs(gpu, orc):
@@ -220,3 +223,17 @@ def test_work_counters_count_the_composited_pairs(gpu, orc):
         assert c["composited_rewalk"] == c["composited_fwd"] == c["hits_back"]
         assert c["eval_rewalk"] == c["eval_fwd"] >= c["eval_back"] >= c["composited_fwd"] > 0
         assert c["binnings"] == 2 and c["pairs_sum"] > 0
+
+
+def test_nine_bit_pair_sort_gives_the_same_bits(gpu, orc):
+    """300 coarse bins (bin 32 on 640x480) are sorted in one 9-bit radix pass,
+    20 bins (bin 128) in one 8-bit pass: the images are bit-identical, and
+    the 9-bit case matches the oracle on sampled windows."""
+    p, cam = _scene0(n=3000, w=640, h=480, angle=15.0, seed=31)
+    ws = _ws(gpu, len(p), 1 << 22, cam.width, cam.height)
+    nine = _render(gpu, p, cam, gpu.raster_cfg(tile=(16, 16), bin_size=32), ws)
+    eight = _render(gpu, p, cam, gpu.raster_cfg(tile=(16, 16), bin_size=128), ws)
+    np.testing.assert_array_equal(nine, eight)
+    for (x0, y0) in [(300, 220), (0, 0), (624, 464)]:
+        ref, marg, _, _ = orc.render(p, cam, window=(x0, y0, 16, 16))
+        _compare_forward(nine[:, y0:y0 + 16, x0:x0 + 16], ref, marg)

@@ -70,3 +70,25 @@ def test_tf_change_changes_image(gpu):
     _, b = gpu.trace(sc, cam, spp=1, max_bounces=3, levels=2, seed=1)
     torch.cuda.synchronize()
     assert not torch.equal(a, b)
+
+
+def test_trace_bit_exact_with_two_sphere_lights(gpu, orc):
+    """The paper's two-point lighting (two spherical area lights outside the
+    volume, Sec. 4.3) with the environment on, 4 spp, bit for bit."""
+    scene = synth.scene_tiny()
+    scene.light_radiance = np.zeros(3, np.float32)
+    scene.env_radiance = np.array([0.1, 0.1, 0.12], np.float32)
+    scene.spheres = synth.two_sphere_lights()
+    cam = synth.orbit_camera(96, 72, 200.0)
+    tg, img = _run(gpu, scene, cam, spp=4, max_bounces=5, levels=3, seed=5, frame=2)
+    rt, ri = orc.trace(scene, cam, spp=4, max_bounces=5, levels=3, seed=5, frame=2, precision=32)
+    assert ri.max() > 0.01
+    np.testing.assert_array_equal(img, ri.astype(np.float32))
+    np.testing.assert_array_equal(tg, rt.astype(np.float32))
+
+
+def test_sphere_light_outside_the_box_is_required(gpu):
+    scene = synth.scene_tiny()
+    scene.spheres = [(np.array([0.5, 0.5, 1.05], np.float32), 0.1, np.ones(3, np.float32))]
+    with pytest.raises(gpu.GscError):
+        gpu.Scene.from_synth(scene)

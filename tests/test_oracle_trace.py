@@ -170,3 +170,44 @@ def test_seed_and_frame_select_streams(orc):
     c = orc.trace(sc, cam, spp=1, max_bounces=4, levels=2, seed=1, frame=1, precision=32)[1]
     np.testing.assert_array_equal(a, b)
     assert not np.array_equal(a, c)
+
+
+def test_single_scatter_small_far_sphere_light(orc):
+    """The same slab lit by a small spherical area light far along +x
+    (Sec. 4.3's light type): the cone estimate's expectation is L_e T
+    (1 - cos theta_max) / 2 per vertex, i.e. the directional closed form with
+    L_d = 2 pi (1 - cos theta_max) L_e (to the 1e-3 variation of theta_max
+    over the box at distance 1000)."""
+    sigma, Ld = 1.5, 3.0
+    rgb = (1.0, 0.5, 0.25)
+    D, rad = 1000.0, 20.0
+    one_minus_cos = 1.0 - math.sqrt(1.0 - (rad / D) ** 2)
+    Le = Ld / (2 * math.pi * one_minus_cos)
+    sc = _homog_scene(sigma, rgb=rgb, albedo=0.8)
+    sc.spheres = [(np.array([0.5 + D, 0.5, 0.5], np.float32), rad, np.full(3, Le, np.float32))]
+    cam = _far_cam()
+    _, img = orc.trace(sc, cam, spp=4096, max_bounces=1, levels=1, seed=19)
+    ii = np.arange(4) + 0.5
+    x = 0.5 + (ii - cam.cx) / cam.fx * 100.0
+    base = (1 - math.exp(-sigma)) * Ld / (4 * math.pi) * np.exp(-sigma * (1 - x))
+    for ch, c in enumerate(rgb):
+        r = img[ch].ravel() / np.broadcast_to(0.8 * c * base[None, :], (4, 4)).ravel()
+        se = r.std(ddof=1) / math.sqrt(r.size)
+        assert abs(r.mean() - 1.0) <= 4.5 * se + 2e-3, (r.mean(), se)
+
+
+def test_sphere_lights_add_linearly(orc):
+    """Two sphere lights together equal the sum of each alone (same streams
+    are not shared, so in expectation): NEE terms are additive."""
+    sc = synth.scene_tiny()
+    sc.light_radiance = np.zeros(3, np.float32)
+    lights = synth.two_sphere_lights()
+    cam = synth.orbit_camera(24, 24, 10.0)
+    imgs = []
+    for sph in ([lights[0]], [lights[1]], lights):
+        sc.spheres = sph
+        _, img = orc.trace(sc, cam, spp=512, max_bounces=2, levels=2, seed=23)
+        imgs.append(img)
+    both, a, b = imgs[2], imgs[0], imgs[1]
+    assert a.mean() > 0 and b.mean() > 0
+    assert abs(both.mean() - (a.mean() + b.mean())) < 0.03 * both.mean()
