@@ -492,6 +492,16 @@ def run_batched_bench(args, cfg_tuned):
     torch.cuda.synchronize()
     step.ws.status()
     graph_ms = e0.elapsed_time(e1) / reps
+    # the same batch with forward, losses and backward as separate launches (eager)
+    step.step_separate()
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        step.step_separate()
+    e1.record(s)
+    torch.cuda.synchronize()
+    step.ws.status()
+    separate_ms = e0.elapsed_time(e1) / reps
     plain_ws = gsc.Workspace(max(sizes), int(max(sizes) * 24), 1920, 1080)
     step.plain_step(plain_ws)
     torch.cuda.synchronize()
@@ -509,7 +519,8 @@ def run_batched_bench(args, cfg_tuned):
     torch.cuda.empty_cache()
     return {"workload": "32 views (256^2 / 640x480 / 1280x720 / 1920x1080, seeded) over 4 scenes of "
                         "100k/250k/500k/1M Gaussians: render + HDR loss + backward", "views": 32,
-            "pixels": px, "graph_ms_per_step": round(graph_ms, 3), "plain_ms_per_step": round(plain_ms, 3),
+            "pixels": px, "graph_ms_per_step": round(graph_ms, 3),
+            "separate_launches_ms_per_step": round(separate_ms, 3), "plain_ms_per_step": round(plain_ms, 3),
             "plain_host_ms_per_step": round(plain_wall, 3), "speedup_vs_plain": round(plain_ms / graph_ms, 3)}
 
 

@@ -3,10 +3,12 @@ captured CUDA graph, and the plain one-view-per-call path it is compared with.
 
 The paper renders and optimises every cache level separately and names a
 joint rasterisation of several Gaussian sets as future work (Sec. 5); here
-all views of all scenes go through one binning and one persistent launch per
-direction (``gsc_render_batch``), and the whole step -- both launches, the
-per-view losses and the gradient clears -- replays from a CUDA graph, so the
-host issues one call per step.
+all views of all scenes go through one binning and ONE persistent launch
+that renders every view, evaluates its HDR loss and differentiates it
+(``gsc_train_batch``), and the whole step -- gradient clears, the launch,
+the per-view loss reductions -- replays from a CUDA graph, so the host issues
+one call per step.  ``step_separate`` is the same step with the forward, the
+losses and the backward as separate launches (``gsc_render_batch``).
 """
 from __future__ import annotations
 
@@ -49,8 +51,10 @@ class BatchedStep:
             target = torch.from_numpy(synth.uniform_image(3, h, w, seed + k)).to(device)
             self.views.append(dict(params=scenes[si], cam=c, scene=si, grads=self.grads[si],
                                    image=torch.zeros((3, h, w), device=device),
-                                   dL_dimage=torch.zeros((3, h, w), device=device), target=target,
-                                   loss=torch.zeros((), device=device)))
+                                   dL_dimage=torch.zeros((3, h, w), device=device), target=target))
+        self.losses = torch.zeros(len(self.views), device=device)
+        for k, v in enumerate(self.views):
+            v["loss"] = self.losses[k]
         if max_pairs is None:
             px = sum(v["cam"].width * v["cam"].height for v in self.views) / len(self.views)
             max_pairs = int(min((1 << 31) - 1, total * max(8.0, 96.0 * px / (1920 * 1080))))
@@ -58,6 +62,11 @@ class BatchedStep:
         self.graph = None
 
     def step(self, stream=None):
+        for g in self.grads:
+            g.zero_()
+        gsc.train_batch(self.views, self.cfg, self.ws, gsc.LOSS_HDR, stream=stream)
+
+    def step_separate(self, stream=None):
         for g in self.grads:
             g.zero_()
         gsc.render_batch(self.views, gsc.BATCH_FWD, self.cfg, self.ws, stream=stream)

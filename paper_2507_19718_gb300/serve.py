@@ -89,7 +89,9 @@ class ResidentScene:
 
 class Trainer:
     """Retraining frames of one scene at a fixed training view: trace the K
-    target buffers, then render, HDR loss, backward and AdamW per level."""
+    target buffers, then one training step for all levels (render, HDR loss
+    and backward in one launch, gsc_train_batch) and AdamW per level.
+    max_gaussians: the largest scene's total over its levels."""
 
     def __init__(self, width: int, height: int, levels: int, max_gaussians: int, cfg: gsc.RasterCfg,
                  spp: int = 1, max_bounces: int = 8, lr=None, weight_decay: float = 0.01, device="cuda"):
@@ -99,12 +101,10 @@ class Trainer:
         self.lr = np.asarray(gsc.PAPER_LR if lr is None else lr, np.float32)
         self.weight_decay = weight_decay
         pairs = int(max_gaussians * max(8.0, 96.0 * width * height / (1920 * 1080)))
-        self.ws = gsc.Workspace(max_gaussians, pairs, width, height, device)
+        self.ws = gsc.Workspace(max_gaussians, pairs, width, height, device, max_views=levels)
         f32 = dict(dtype=torch.float32, device=device)
         self.targets = torch.zeros((levels, 3, height, width), **f32)
         self.image = torch.zeros((3, height, width), **f32)
-        self.render = torch.zeros((3, height, width), **f32)
-        self.dL = torch.zeros((3, height, width), **f32)
         self.loss = torch.zeros((levels,), **f32)
 
     def frame(self, sc: ResidentScene, angle: float, frame: int, seed: int, stream=None):
@@ -115,11 +115,10 @@ class Trainer:
                                lr_scale=gsc.lr_scale(sc.static_frames), step=sc.adam_step)
         gsc.trace(sc.handle, c, self.spp, self.max_bounces, self.K, seed, frame, targets=self.targets,
                   image=self.image, stream=stream)
-        for k, L in enumerate(sc.levels):
-            gsc.cache_render(L.params, c, self.cfg, self.ws, image=self.render, stream=stream)
-            gsc.loss(gsc.LOSS_HDR, self.render, self.targets[k], self.ws, dL_dpred=self.dL, loss_out=self.loss[k],
-                     stream=stream)
-            gsc.cache_backward(L.params, c, self.cfg, self.ws, self.dL, L.grads, stream=stream)
+        views = [dict(params=L.params, cam=c, target=self.targets[k], grads=L.grads, loss=self.loss[k])
+                 for k, L in enumerate(sc.levels)]
+        gsc.train_batch(views, self.cfg, self.ws, gsc.LOSS_HDR, stream=stream)
+        for L in sc.levels:
             gsc.cache_step(L.params, L.grads, L.m, L.v, adam, stream=stream)
         sc.frames_trained += 1
 
@@ -145,7 +144,7 @@ class Server:
                                       max_views=self.max_views) for _ in range(2)]
         self.plain_ws = gsc.Workspace(max(L.n for sc in scenes for L in sc.levels), pairs // 4, max_res[0],
                                       max_res[1], device)
-        self.trainer = Trainer(train_res[0], train_res[1], self.K, max(L.n for sc in scenes for L in sc.levels), cfg,
+        self.trainer = Trainer(train_res[0], train_res[1], self.K, max(sc.n_gaussians for sc in scenes), cfg,
                                device=device)
         self.fixed_bytes = (sum(sc.state_bytes() for sc in scenes) + sum(ws.nbytes for ws in self.view_ws) +
                             self.plain_ws.nbytes + self.trainer.ws.nbytes)

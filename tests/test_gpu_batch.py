@@ -183,3 +183,27 @@ def test_train_batch_rejects_non_local_losses(gpu):
                grads=torch.zeros_like(v["params"]), loss=torch.zeros((), device="cuda"))]
     with pytest.raises(gpu.GscError):
         gpu.train_batch(tv, gpu.raster_cfg(), ws, gpu.LOSS_L1_SSIM)
+
+
+def test_batched_step_graph_replays_the_training_step(gpu):
+    """BatchedStep (one training-step launch for all views under a CUDA graph)
+    gives the same losses and gradients as its separate-launch step."""
+    import torch
+    from paper_2507_19718_gb300 import batched
+    scenes = [torch.from_numpy(synth.gaussians(n, 900 + k)).cuda() for k, n in enumerate([400, 700])]
+    views = [(k % 2, synth.orbit_camera(w, h, 20.0 * k)) for k, (w, h) in enumerate(SIZES)]
+    cfg = gpu.raster_cfg(tile=(16, 16), list_capacity=256, bin_size=32, pixels_per_thread=2)
+    st = batched.BatchedStep(scenes, views, cfg, max_pairs=1 << 22)
+    st.step_separate()
+    torch.cuda.synchronize()
+    sep_g = [g.clone() for g in st.grads]
+    sep_l = st.losses.clone()
+    st.capture()
+    st.replay()
+    torch.cuda.synchronize()
+    st.ws.status()
+    np.testing.assert_allclose(st.losses.cpu().numpy(), sep_l.cpu().numpy(), rtol=2e-6)
+    for a, b in zip(st.grads, sep_g):
+        np.testing.assert_allclose(a.cpu().numpy(), b.cpu().numpy(), rtol=1e-4,
+                                   atol=1e-6 * float(b.abs().max()))
+        assert float(b.abs().max()) > 0
