@@ -247,6 +247,10 @@ size_t layout(int64_t NG, int64_t NP, int32_t W, int32_t H, int32_t NV, gsc_work
     w->pval1 = (uint32_t*)take(4 * np);
     w->hist = (uint32_t*)take(4 * kHistWords);
     w->ranges = (uint2*)take(sizeof(uint2) * (size_t)tiles);
+    w->tkey0 = (uint32_t*)take(4 * (size_t)tiles);
+    w->tkey1 = (uint32_t*)take(4 * (size_t)tiles);
+    w->tord0 = (uint32_t*)take(4 * (size_t)tiles);
+    w->tord1 = (uint32_t*)take(4 * (size_t)tiles);
     w->g2d = (float4*)take(sizeof(float4) * 3 * ng);
     w->red = (float*)take(sizeof(float) * red);
     w->red_floats = red;
@@ -550,9 +554,9 @@ gsc_status gsc_render_batch(const gsc_view* views, int32_t n_views, int32_t mode
         const gsc_view& v = views[order[k]];
         add_view(b, rc, &v.cam, v.params, v.N, v.image, v.dL_dimage, v.grads);
     }
-    if ((int64_t)b.total_bins > ws->max_tiles)
-        return fail(GSC_ERR_INVALID_ARG, "the batch has %u bins, the workspace %lld (raise max_views)", b.total_bins,
-                    (long long)ws->max_tiles);
+    if ((int64_t)b.total_bins > ws->max_tiles || (int64_t)b.total_tiles > ws->max_tiles)
+        return fail(GSC_ERR_INVALID_ARG, "the batch has %u tiles and %u bins, the workspace %lld (raise max_views)",
+                    b.total_tiles, b.total_bins, (long long)ws->max_tiles);
     if (total == 0) {
         if (mode & GSC_BATCH_FWD)
             for (int i = 0; i < n_views; ++i)
@@ -621,9 +625,9 @@ gsc_status gsc_train_batch(const gsc_train_view* views, int32_t n_views, int32_t
         b.v[k].target = v.target;
         b.v[k].loss = v.loss;
     }
-    if ((int64_t)b.total_bins > ws->max_tiles)
-        return fail(GSC_ERR_INVALID_ARG, "the batch has %u bins, the workspace %lld (raise max_views)", b.total_bins,
-                    (long long)ws->max_tiles);
+    if ((int64_t)b.total_bins > ws->max_tiles || (int64_t)b.total_tiles > ws->max_tiles)
+        return fail(GSC_ERR_INVALID_ARG, "the batch has %u tiles and %u bins, the workspace %lld (raise max_views)",
+                    b.total_tiles, b.total_bins, (long long)ws->max_tiles);
     if ((size_t)b.total_tiles > ws->red_floats)
         return fail(GSC_ERR_INVALID_ARG, "the batch has %u tiles, the loss scratch %zu", b.total_tiles,
                     ws->red_floats);

@@ -138,7 +138,9 @@ struct gsc_workspace {
     uint32_t* scan_sums;
     uint32_t *pkey0, *pkey1, *pval0, *pval1;
     uint32_t* hist;    // kHistWords
-    uint2* ranges;     // [start, end) per tile
+    uint2* ranges;     // [start, end) per bin
+    uint32_t *tkey0, *tkey1, *tord0, *tord1;  // tiles ordered by expected cost (longest bin lists first)
+    const uint32_t* order;                    // the order of the last binning (tord0 or tord1)
     float4* g2d;       // 3 x NG: 2D gradients
     float* red;        // reduction scratch for losses
     size_t red_floats;
