@@ -264,7 +264,7 @@ def run_ours(args, world, rank, local):
     tuned_top = None
     if args.no_autotune:  # the configurations the autotuner picks on a GB300
         best_f = autotune.Trial((16, 16), 128, 256, 2, float("nan"))
-        best_b = autotune.Trial((16, 16), 128, 256, 2, float("nan"))
+        best_b = autotune.Trial((16, 16), 128, 256, 4, float("nan"))
     else:
         cands = list(autotune.candidates(TUNE_TILES, TUNE_BINS, TUNE_CAPS, TUNE_PPT))
         lv = [L.params for L in loop.levels]
