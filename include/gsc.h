@@ -215,7 +215,9 @@ gsc_status gsc_workspace_status(gsc_workspace* ws, gsc_stream_t stream, int64_t*
  * forward, pairs evaluated by the backward's forward re-walk, pairs
  * evaluated back to front, the sum of the pair counts of all binnings, the
  * number of binnings, pairs composited by the re-walk, and pairs that
- * contributed gradient terms back to front.  n: entries wanted (<= 10). */
+ * contributed gradient terms back to front.  The last two are one count:
+ * the pairs composited for pixels whose dL/dimage is not zero, which are the
+ * pairs that contribute back to front.  n: entries wanted (<= 10). */
 #define GSC_COUNTER_WORDS 10
 gsc_status gsc_workspace_counters(gsc_workspace* ws, gsc_stream_t stream, int64_t* out, int32_t n);
 

@@ -558,7 +558,7 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
     float4* s1 = smem + cap;
     float4* s2 = smem + 2 * cap;
     uint32_t* hits = reinterpret_cast<uint32_t*>(smem + 3 * cap);
-    uint32_t n_eval1 = 0, n_eval2 = 0, n_comp1 = 0;
+    uint32_t n_eval1 = 0, n_eval2 = 0, n_hit2 = 0;
     __shared__ uint32_t s_tile;
     // persistent CTAs: tiles of all views are handed out by an atomic counter,
     // in the order of their expected cost (longest bin list first)
@@ -677,7 +677,6 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
                     }
                     T[q] = comp ? Tn : T[q];
                     last[q] = comp ? h0 + (uint32_t)k + 1u : last[q];
-                    n_comp1 += comp ? 1u : 0u;
                 }
             }
         }
@@ -720,11 +719,11 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
     __syncthreads();
     uint32_t mylast = 0;
 #pragma unroll
-    for (int q = 0; q < PPT; ++q)
-        if (active[q]) {
-            mylast = max(mylast, last[q]);
-            n_eval2 += last[q];  // phase 2 evaluates this pixel at entries [0, last)
-        }
+    for (int q = 0; q < PPT; ++q) {
+        if (!active[q]) last[q] = 0;  // phase 2 evaluates a pixel at entries [0, last)
+        mylast = max(mylast, last[q]);
+        n_eval2 += last[q];
+    }
     if (mylast) atomicMax(&s_end, mylast);
     __syncthreads();
     const uint32_t hend = s_end;
@@ -790,17 +789,20 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
                 const float dx = __fsub_rn(fx, r0.x);
                 float wx, xx = falloff_col(r0, dx, wx);
                 // per entry: sum w dx, sum w dy, sum w dx^2, sum w dx dy, sum w dy^2
-                // (w = dL/dalpha alpha), sum dL/dalpha G, red, green; blue apart
+                // (w = dL/dalpha alpha), sum dL/dalpha G, red, green; blue apart.
+                // The pixels of a thread share dx, so the thread sums w, w dy and
+                // w dy^2 and scales by dx (and dx^2) once per entry.
                 float v8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                float dcb = 0.f;
+                float sw = 0.f, dcb = 0.f;
                 bool any = false;
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
-                    if (!(active[q] && j < last[q])) continue;
+                    if (j >= last[q]) continue;
                     const float dy = __fsub_rn(fy[q], r0.y);
                     float p = falloff_row(xx, wx, r1.x, dy);
                     if (p < r1.z) continue;
                     any = true;
+                    ++n_hit2;
                     float e = ex2_approx(p);
                     float araw = __fmul_rn(r1.y, e);
                     float alpha = fminf(rc.alpha_max, araw);
@@ -816,14 +818,15 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
                     if (araw < rc.alpha_max) {
                         v8[5] = fmaf(dal, e, v8[5]);
                         float w = dal * alpha;
-                        float wx = w * dx, wy = w * dy;
-                        v8[0] += wx;
+                        float wy = w * dy;
+                        sw += w;
                         v8[1] += wy;
-                        v8[2] = fmaf(wx, dx, v8[2]);
-                        v8[3] = fmaf(wx, dy, v8[3]);
                         v8[4] = fmaf(wy, dy, v8[4]);
                     }
                 }
+                v8[0] = sw * dx;
+                v8[2] = v8[0] * dx;
+                v8[3] = v8[1] * dx;
                 if (__any_sync(kFull, any)) {
                     // values 0..7 -> floats 0..5, 8, 9 of the 12-float 2D gradient record
                     float tot = warp_reduce_scatter8(v8, lane);
@@ -842,8 +845,10 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
     }  // tiles
     warp_count(&stats[kStEvalRewalk], n_eval1);
     warp_count(&stats[kStEvalBack], n_eval2);
-    warp_count(&stats[kStCompRewalk], n_comp1);
-    warp_count(&stats[kStHitBack], n_comp1);  // back to front: the same composited pairs
+    // the entries a pixel meets in phase 2 before its last composited one and
+    // whose falloff passes alpha_min are exactly the pairs phase 1 composited
+    warp_count(&stats[kStCompRewalk], n_hit2);
+    warp_count(&stats[kStHitBack], n_hit2);
 }
 
 // 2D gradients -> packed parameter gradients (+=)
