@@ -139,8 +139,8 @@ struct gsc_workspace {
     uint32_t *pkey0, *pkey1, *pval0, *pval1;
     uint32_t* hist;    // kHistWords
     uint2* ranges;     // [start, end) per bin
-    uint32_t *tkey0, *tkey1, *tord0, *tord1;  // tiles ordered by expected cost (longest bin lists first)
-    const uint32_t* order;                    // the order of the last binning (tord0 or tord1)
+    uint32_t* tile_order;   // tiles ordered by expected cost (longest bin lists first)
+    const uint32_t* order;  // the order of the last binning
     float4* g2d;       // 3 x NG: 2D gradients
     float* red;        // reduction scratch for losses
     size_t red_floats;
@@ -162,6 +162,8 @@ void scan_gathered(const uint32_t* cnt, const uint32_t* idx, uint32_t n, uint32_
 int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* n_dev,
                      uint32_t n_host, int bits, int blocks, uint32_t* hist, cudaStream_t s);
 int sort_blocks_for(uint64_t n);
+// digit counts of the last pass of radix_sort_pairs (in its histogram buffer)
+inline uint32_t* radix_totals(uint32_t* hist) { return hist + (size_t)kMaxSortBlocks * kMaxDigits; }
 int radix_passes(int bits);
 
 // raster.cu (every view of the batch shares rc)

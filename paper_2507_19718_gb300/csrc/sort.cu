@@ -5,12 +5,13 @@
 //
 // Radix sort: 8- or 9-bit digits, three kernels per pass over a fixed grid of
 // `blocks` CTAs, each owning a contiguous range of the input:
-//   hist    per-CTA digit counts (warp-aggregated shared-memory atomics),
+//   hist    per-CTA digit counts (per-warp shared-memory atomics),
 //           stored digit-major so that one exclusive scan yields the stable
 //           scatter base of every (digit, CTA);
 //   scan    one CTA per digit scans its `blocks` counts;
-//   scatter each CTA ranks its keys in 2048-key tiles (warp match + per-warp
-//           digit counters), then writes keys and values to their slots.
+//   scatter each CTA ranks its keys in 2048-key tiles (equal digits found by
+//           warp ballots, per-warp digit counters), then writes keys and
+//           values to their slots.
 // The element count may live on the device (the pair count is only known
 // after the binning scan), so no host round trip is needed.
 #include "gsc_internal.cuh"
@@ -76,16 +77,23 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
     uint32_t n = read_count(n_dev, n_host);
     uint32_t lo, hi;
     block_range(n, blocks, blockIdx.x, lo, hi);
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < 8 * NDIG; i += kSortThreads) (&h[0][0])[i] = 0;
     __syncthreads();
-    // warp-uniform trip count so that __match_any_sync sees full warps
-    for (uint32_t base = lo; base < hi; base += kSortThreads) {
-        uint32_t i = base + threadIdx.x;
-        bool valid = i < hi;
-        int d = valid ? (int)((keys[i] >> shift) & (uint32_t)(NDIG - 1)) : NDIG;
-        unsigned peers = __match_any_sync(kFull, d);
-        if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[warp][d], (uint32_t)__popc(peers));
+    // 2048 keys per step, all loads issued before the first match; the trip
+    // count is uniform so that __match_any_sync sees full warps
+    for (uint32_t base = lo; base < hi; base += kSortTile) {
+        int d[kSortIPT];
+#pragma unroll
+        for (int j = 0; j < kSortIPT; ++j) {
+            uint32_t i = base + j * kSortThreads + threadIdx.x;
+            d[j] = i < hi ? (int)((keys[i] >> shift) & (uint32_t)(NDIG - 1)) : NDIG;
+        }
+        // plain shared atomics: measured 1.5x faster over the whole pass than
+        // aggregating equal digits with __match_any_sync first
+#pragma unroll
+        for (int j = 0; j < kSortIPT; ++j)
+            if (d[j] < NDIG) atomicAdd(&h[warp][d[j]], 1u);
     }
     __syncthreads();
     for (int d = threadIdx.x; d < NDIG; d += kSortThreads) {
@@ -169,14 +177,28 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
         __syncthreads();
         uint32_t kk[kSortIPT], vv[kSortIPT], rank[kSortIPT];
         int dd[kSortIPT];
+        // all loads of the tile first, then the ranking
 #pragma unroll
         for (int j = 0; j < kSortIPT; ++j) {
             uint32_t i = tile + warp * (kWarp * kSortIPT) + j * kWarp + lane;
             bool valid = i < hi;
             kk[j] = valid ? kin[i] : 0u;
             vv[j] = valid ? vin[i] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kSortIPT; ++j) {
+            uint32_t i = tile + warp * (kWarp * kSortIPT) + j * kWarp + lane;
+            bool valid = i < hi;
             int d = valid ? (int)((kk[j] >> shift) & (uint32_t)(NDIG - 1)) : NDIG;
-            unsigned peers = __match_any_sync(kFull, d);
+            // lanes with the same digit (NDIG marks an empty slot): one ballot
+            // per digit bit, cheaper here than __match_any_sync
+            unsigned peers = kFull;
+#pragma unroll
+            for (int bit = 0; bit <= DB; ++bit) {
+                const bool set = (d >> bit) & 1;
+                const unsigned m = __ballot_sync(kFull, set);
+                peers &= set ? m : ~m;
+            }
             uint32_t base = valid ? wh[warp][d] : 0u;
             __syncwarp();
             if (valid && lane == __ffs(peers) - 1) wh[warp][d] = base + (uint32_t)__popc(peers);
@@ -241,13 +263,31 @@ int sort_blocks_for(uint64_t n) {
     return (int)b;
 }
 
+// CTAs of the scatter kernel that are resident on the device at once: a pass
+// runs on at most that many, so that it ends in one wave (a second, partial
+// wave would take as long as the first)
+template <int DB>
+static int resident_scatter_blocks() {
+    static int cached = 0;
+    if (cached <= 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_radix_scatter<DB>, kSortThreads, 0);
+        cached = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+    }
+    return cached;
+}
+
 // passes = ceil(bits / 9); 8-bit digits when they cover the bits in that
 // many passes, else 9-bit digits (e.g. 9 bits: one 9-bit pass; 16: two 8-bit)
 int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* n_dev,
                      uint32_t n_host, int bits, int blocks, uint32_t* hist, cudaStream_t s) {
-    uint32_t* totals = hist + (size_t)kMaxSortBlocks * kMaxDigits;
+    uint32_t* totals = radix_totals(hist);
     const int passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
     const int db = 8 * passes >= bits ? 8 : 9;
+    const int resident = db == 8 ? resident_scatter_blocks<8>() : resident_scatter_blocks<9>();
+    if (blocks > resident) blocks = resident;
     int cur = 0;
     for (int shift = 0; shift < bits; shift += db) {
         uint32_t* ki = cur ? k1 : k0;
