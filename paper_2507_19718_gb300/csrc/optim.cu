@@ -314,14 +314,15 @@ namespace gsc {
 
 struct AdamDev {
     float lr[16];
-    float b1, b2, eps, wd, bc1, bc2;
+    float b1, b2, eps, wd;
+    float ibc1, ibc2;  // 1 / (1 - beta^t), the bias corrections
 };
 
 __device__ __forceinline__ void adam_one(float& p, float& m, float& v, float g, float lr, const AdamDev& a) {
     if (lr == 0.f) return;
     m = a.b1 * m + (1.f - a.b1) * g;
     v = a.b2 * v + (1.f - a.b2) * g * g;
-    float mh = m / a.bc1, vh = v / a.bc2;
+    float mh = m * a.ibc1, vh = v * a.ibc2;
     p = p - lr * (mh / (sqrtf(vh) + a.eps) + a.wd * p);
 }
 
@@ -350,8 +351,8 @@ cudaError_t launch_adamw(float* params, float* grads, float* m, float* v, int64_
     a.b2 = ap.beta2;
     a.eps = ap.eps;
     a.wd = ap.weight_decay;
-    a.bc1 = (float)(1.0 - pow((double)ap.beta1, (double)ap.step));
-    a.bc2 = (float)(1.0 - pow((double)ap.beta2, (double)ap.step));
+    a.ibc1 = (float)(1.0 / (1.0 - pow((double)ap.beta1, (double)ap.step)));
+    a.ibc2 = (float)(1.0 / (1.0 - pow((double)ap.beta2, (double)ap.step)));
     size_t n4 = (size_t)N * 4;
     size_t blocks = (n4 + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;

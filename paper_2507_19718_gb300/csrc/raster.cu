@@ -50,16 +50,19 @@ __device__ __forceinline__ float view_depth(const CamDev& c, float x, float y, f
 }
 
 // log2 of the Gaussian falloff at pixel-centre offset (dx, dy), fixed rounding:
-// p = fma(qc dy, dy, fma(qb dx, dy, (qa dx) dx)).  The dx terms are shared by
-// the pixels of one column, so they are split off.
+// p = fma(fma(qc, dy, qb dx), dy, (qa dx) dx), Horner in dy.  The dx terms are
+// shared by the pixels of one column, so they are split off.
 __device__ __forceinline__ float falloff_col(float4 r0, float dx, float& wx) {
     wx = __fmul_rn(r0.w, dx);
     return __fmul_rn(__fmul_rn(r0.z, dx), dx);
 }
 __device__ __forceinline__ float falloff_row(float xx, float wx, float qc, float dy) {
-    float p = __fmaf_rn(wx, dy, xx);
-    return __fmaf_rn(__fmul_rn(qc, dy), dy, p);
+    return __fmaf_rn(__fmaf_rn(qc, dy, wx), dy, xx);
 }
+
+// transmittance behind a composited entry, T (1 - alpha) as T - T alpha with
+// one rounding
+__device__ __forceinline__ float transmit(float T, float alpha) { return __fmaf_rn(-T, alpha, T); }
 
 struct Proj {
     float qn[4], qinv;
@@ -375,8 +378,10 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render(const __grid_constant__
     int px = tx * TW + (threadIdx.x % TW), py0 = ty * TH + (threadIdx.x / TW);
     float fx = (float)px + 0.5f;
     float fy[PPT], T[PPT], Cr[PPT], Cg[PPT], Cb[PPT];
-    bool inside[PPT], done[PPT];
-    uint32_t ev[PPT];  // entries a pixel evaluated, set when it reaches T_min
+    bool inside[PPT];
+    // entries a pixel evaluated, set when it reaches T_min; all ones while it
+    // has not (a pixel outside the image starts at 0: nothing to evaluate)
+    uint32_t ev[PPT];
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
         int py = py0 + q * ROWS;
@@ -384,7 +389,6 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render(const __grid_constant__
         fy[q] = (float)py + 0.5f;
         T[q] = 1.f;
         Cr[q] = Cg[q] = Cb[q] = 0.f;
-        done[q] = !inside[q];
         ev[q] = inside[q] ? 0xffffffffu : 0u;
     }
     uint2 rg = ranges[vw.bin_off + (ty / rc.spt_y) * vw.bins_x + tx / rc.spt_x];
@@ -393,7 +397,7 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render(const __grid_constant__
     for (;;) {
         bool tdone = true;
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) tdone = tdone && done[q];
+        for (int q = 0; q < PPT; ++q) tdone = tdone && ev[q] != 0xffffffffu;
         if (__syncthreads_count(tdone) == NT || pos >= rg.y) break;
         int staged = 0;
         while (pos < rg.y && staged + NT <= cap) {
@@ -432,19 +436,15 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render(const __grid_constant__
                 // select (adding a zero weight leaves a colour unchanged)
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
-                    if (done[q]) continue;
+                    if (ev[q] != 0xffffffffu) continue;
                     const float p = falloff_row(xx, wx, r1.x, __fsub_rn(fy[q], r0.y));
                     const bool hit = !(p < r1.z);
                     const float alpha = fminf(rc.alpha_max, __fmul_rn(r1.y, ex2_approx(p)));
-                    const float Tn = __fmul_rn(T[q], __fsub_rn(1.f, alpha));
+                    const float Tn = transmit(T[q], alpha);
                     const bool stop = hit && Tn < rc.T_min;
                     const bool comp = hit && !stop;
-                    if (stop) {
-                        done[q] = true;
-                        ev[q] = hbase + (uint32_t)k + 1u;
-                    } else {
-                        all = false;
-                    }
+                    ev[q] = stop ? hbase + (uint32_t)k + 1u : ev[q];
+                    all = all && stop;
                     n_comp += comp ? 1u : 0u;
                     const float wgt = comp ? alpha * T[q] : 0.f;
                     Cr[q] = fmaf(c.x, wgt, Cr[q]);
@@ -452,12 +452,7 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render(const __grid_constant__
                     Cb[q] = fmaf(c.z, wgt, Cb[q]);
                     T[q] = comp ? Tn : T[q];
                 }
-                if (all) {
-                    bool alld = true;
-#pragma unroll
-                    for (int q = 0; q < PPT; ++q) alld = alld && done[q];
-                    if (alld) break;
-                }
+                if (all) break;  // every pixel of the thread has stopped
             }
         }
         hbase += (uint32_t)staged;
@@ -518,7 +513,8 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float (&a)[8], int l
 // their Gaussian ids go to a shared-memory ring of kHitRing slots, and the
 // list position of every kHitRing-th hit is recorded, so that phase 2 can
 // rebuild any chunk of hits without scanning from the start.  Each pixel
-// keeps its final T and the number of hits up to its last composited entry.
+// keeps its final T and the hit number of the entry that stopped it (none if
+// it never stopped: it then saw every hit).
 // Phase 2 walks the hits back to front, chunk by chunk (the last chunk is
 // still in the ring; earlier ones are re-filtered from their recorded
 // position), stages their records, and per entry sums the nine 2D gradient
@@ -582,7 +578,7 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
     float fx = (float)px + 0.5f;
     size_t HW = (size_t)cam.W * cam.H;
     float fy[PPT], gr[PPT], gg[PPT], gb[PPT], T[PPT];
-    bool active[PPT], done[PPT];
+    bool active[PPT];
     uint32_t last[PPT], ev[PPT];
     float Cr[PPT], Cg[PPT], Cb[PPT];  // composited colour (training step only)
 #pragma unroll
@@ -603,9 +599,7 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
         } else {
             active[q] = inside;  // the gradient is known after phase 1
         }
-        done[q] = !active[q];
         T[q] = 1.f;
-        last[q] = 0;
         ev[q] = active[q] ? 0xffffffffu : 0u;
     }
     uint2 rg = ranges[vw.bin_off + (ty / rc.spt_y) * vw.bins_x + tx / rc.spt_x];
@@ -616,7 +610,7 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
     for (;;) {
         bool tdone = true;
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) tdone = tdone && done[q];
+        for (int q = 0; q < PPT; ++q) tdone = tdone && ev[q] != 0xffffffffu;
         if (__syncthreads_count(tdone) == NT || pos >= rg.y) break;
         int staged = 0;
         uint32_t h0 = nhit;
@@ -660,17 +654,14 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
                 // select (measured 2.5-3% faster than branching on all three)
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
-                    if (done[q]) continue;
+                    if (ev[q] != 0xffffffffu) continue;  // stopped (or inactive)
                     const float p = falloff_row(xx, wx, r1.x, __fsub_rn(fy[q], r0.y));
                     const bool hit = !(p < r1.z);
                     const float alpha = fminf(rc.alpha_max, __fmul_rn(r1.y, ex2_approx(p)));
-                    const float Tn = __fmul_rn(T[q], __fsub_rn(1.f, alpha));
+                    const float Tn = transmit(T[q], alpha);
                     const bool stop = hit && Tn < rc.T_min;
                     const bool comp = hit && !stop;
-                    if (stop) {
-                        done[q] = true;
-                        ev[q] = h0 + (uint32_t)k + 1u;
-                    }
+                    ev[q] = stop ? h0 + (uint32_t)k + 1u : ev[q];
                     if (LOSS != kLossNone) {  // the forward's colour arithmetic
                         const float wgt = comp ? alpha * T[q] : 0.f;
                         Cr[q] = fmaf(c.x, wgt, Cr[q]);
@@ -678,7 +669,6 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
                         Cb[q] = fmaf(c.z, wgt, Cb[q]);
                     }
                     T[q] = comp ? Tn : T[q];
-                    last[q] = comp ? h0 + (uint32_t)k + 1u : last[q];
                 }
             }
         }
@@ -719,10 +709,13 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
     }
     if (threadIdx.x == 0) s_end = 0;
     __syncthreads();
+    // Phase 2 evaluates a pixel at the entries [0, last): up to the one that
+    // stopped it, else to the end of the list (the entries after its last
+    // composited one are then non-hits, skipped by the alpha_min test).
     uint32_t mylast = 0;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
-        if (!active[q]) last[q] = 0;  // phase 2 evaluates a pixel at entries [0, last)
+        last[q] = !active[q] ? 0u : (ev[q] == 0xffffffffu ? nhit : ev[q] - 1u);
         mylast = max(mylast, last[q]);
         n_eval2 += last[q];
     }
