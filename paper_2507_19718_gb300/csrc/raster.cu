@@ -970,35 +970,37 @@ static int bits_for(uint32_t n) {
 
 // Order in which the persistent CTAs take the tiles: by the length of the
 // tile's bin list, longest first (a longest-processing-time-first schedule,
-// so that the cheap tiles fill the end of the launch).  Class of a tile =
-// 255 - 8 log2(length + 1); the order within a class is whatever the atomics
-// give, since it only decides which CTA renders a tile, never a result.
+// so that the cheap tiles fill the end of the launch).  Class of a bin (and
+// of its tiles) = 255 - 8 log2(length + 1).  The tiles of a bin are placed
+// together in row-major order; the order of the bins within a class is
+// whatever the atomics give, since it only decides which CTA renders a tile,
+// never a result.
 constexpr int kOrderThreads = 1024;
 constexpr int kOrderClasses = 256;
+constexpr int kOrderCachedBins = 4096;  // bins whose start is kept in shared memory
 
-__device__ __forceinline__ uint32_t tile_class(const BatchDev& b, const uint2* ranges, const RasterDev& rc,
-                                               uint32_t t) {
-    const ViewDev& vw = b.v[view_of_tile(b, t)];
-    const uint32_t lt = t - vw.tile_off;
-    const int tx = (int)(lt % (uint32_t)vw.tiles_x), ty = (int)(lt / (uint32_t)vw.tiles_x);
-    uint2 rg = ranges[vw.bin_off + (ty / rc.spt_y) * vw.bins_x + tx / rc.spt_x];
-    float l = log2f((float)(rg.y - rg.x) + 1.0f) * 8.0f;
-    return (uint32_t)(kOrderClasses - 1) - (uint32_t)fminf(l, (float)(kOrderClasses - 1));
+__device__ __forceinline__ int view_of_bin(const BatchDev& b, uint32_t bin) {
+    int v = 0;
+    while (v + 1 < b.nviews && bin >= b.v[v + 1].bin_off) ++v;
+    return v;
 }
 
 // One CTA.  With `totals` (the digit counts of a one-pass pair sort, where
 // the digit is the whole bin id) it first writes every bin's range as the
-// exclusive scan of the counts; then it counts the tiles per class, scans the
-// counts and places every tile.
+// exclusive scan of the counts.  Then per bin: its class and tile count; the
+// tile counts are summed per class and scanned, every bin takes its start in
+// its class, and every tile goes to its bin's start plus its row-major
+// position in the bin.
 __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_constant__ BatchDev b,
                                                               const uint32_t* __restrict__ totals,
                                                               uint2* __restrict__ ranges, RasterDev rc,
+                                                              uint32_t* __restrict__ bin_start,
                                                               uint32_t* __restrict__ order) {
     __shared__ uint32_t cls[kOrderClasses];
     __shared__ uint32_t wsum[kOrderThreads / 32];
+    __shared__ uint32_t s_start[kOrderCachedBins];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // exclusive scan of one value per thread (values beyond the first
-    // kOrderThreads entries are not needed: callers guarantee the count)
+    // exclusive scan of one value per thread
     auto block_scan = [&](uint32_t v) -> uint32_t {
         uint32_t x = v;
 #pragma unroll
@@ -1013,24 +1015,53 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_const
         __syncthreads();
         return before + x - v;
     };
-    if (totals) {
-        const uint32_t nb = b.total_bins;
+    const uint32_t nb = b.total_bins;
+    if (totals) {  // the caller guarantees nb <= kOrderThreads here
         uint32_t c = threadIdx.x < nb ? totals[threadIdx.x] : 0u;
         uint32_t s = block_scan(c);
         if (threadIdx.x < nb) ranges[threadIdx.x] = make_uint2(s, s + c);
-        __syncthreads();  // the ranges are read back below by other threads
     }
     if (threadIdx.x < kOrderClasses) cls[threadIdx.x] = 0;
-    __syncthreads();
-    for (uint32_t t = threadIdx.x; t < b.total_tiles; t += kOrderThreads)
-        atomicAdd(&cls[tile_class(b, ranges, rc, t)], 1u);
+    __syncthreads();  // also makes the ranges written above visible to the CTA
+    auto bin_info = [&](uint32_t bin, uint32_t& klass, uint32_t& ntiles) {
+        const ViewDev& vw = b.v[view_of_bin(b, bin)];
+        const uint32_t lb = bin - vw.bin_off;
+        const int bx = (int)(lb % (uint32_t)vw.bins_x), by = (int)(lb / (uint32_t)vw.bins_x);
+        const int w = min(rc.spt_x, vw.tiles_x - bx * rc.spt_x), h = min(rc.spt_y, vw.tiles_y - by * rc.spt_y);
+        ntiles = (uint32_t)(w * h);
+        const uint2 rg = ranges[bin];
+        const float l = log2f((float)(rg.y - rg.x) + 1.0f) * 8.0f;
+        klass = (uint32_t)(kOrderClasses - 1) - (uint32_t)fminf(l, (float)(kOrderClasses - 1));
+    };
+    for (uint32_t bin = threadIdx.x; bin < nb; bin += kOrderThreads) {
+        uint32_t k, nt;
+        bin_info(bin, k, nt);
+        atomicAdd(&cls[k], nt);
+    }
     __syncthreads();
     uint32_t c = threadIdx.x < kOrderClasses ? cls[threadIdx.x] : 0u;
     uint32_t s = block_scan(c);
     if (threadIdx.x < kOrderClasses) cls[threadIdx.x] = s;
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < b.total_tiles; t += kOrderThreads)
-        order[atomicAdd(&cls[tile_class(b, ranges, rc, t)], 1u)] = t;
+    for (uint32_t bin = threadIdx.x; bin < nb; bin += kOrderThreads) {
+        uint32_t k, nt;
+        bin_info(bin, k, nt);
+        const uint32_t st = atomicAdd(&cls[k], nt);
+        if (bin < (uint32_t)kOrderCachedBins) s_start[bin] = st;
+        else bin_start[bin] = st;
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < b.total_tiles; t += kOrderThreads) {
+        const ViewDev& vw = b.v[view_of_tile(b, t)];
+        const uint32_t lt = t - vw.tile_off;
+        const int tx = (int)(lt % (uint32_t)vw.tiles_x), ty = (int)(lt / (uint32_t)vw.tiles_x);
+        const int bx = tx / rc.spt_x, by = ty / rc.spt_y;
+        const uint32_t bin = vw.bin_off + (uint32_t)(by * vw.bins_x + bx);
+        const int w = min(rc.spt_x, vw.tiles_x - bx * rc.spt_x);
+        const uint32_t local = (uint32_t)((ty - by * rc.spt_y) * w + (tx - bx * rc.spt_x));
+        const uint32_t st = bin < (uint32_t)kOrderCachedBins ? s_start[bin] : bin_start[bin];
+        order[st + local] = t;
+    }
 }
 
 cudaError_t bin_gaussians(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t** sorted_vals,
@@ -1078,7 +1109,7 @@ cudaError_t bin_gaussians(const BatchDev& b, const RasterDev& rc, gsc_workspace*
             k_ranges<<<152 * 8, 256, 0, s>>>(keys, ws->counters, ws->ranges);
         }
         k_tile_order<<<1, kOrderThreads, 0, s>>>(b, one_pass ? radix_totals(ws->hist) : nullptr, ws->ranges, rc,
-                                                 ws->tile_order);
+                                                 ws->bin_start, ws->tile_order);
         ws->order = ws->tile_order;
     }
     return cudaGetLastError();
@@ -1196,8 +1227,10 @@ cudaError_t launch_render(const BatchDev& b, const RasterDev& rc, gsc_workspace*
     GSC_TILE_DISPATCH(render_t, b, rc, ws, vals, s)
 }
 
-// per view: the sum of its tiles' loss partials (in order, FP64) / k
-__global__ void k_view_loss(const __grid_constant__ BatchDev b, const float* __restrict__ tile_loss) {
+// per view: the sum of its tiles' loss partials (in a fixed order, FP64) / k
+constexpr int kViewLossThreads = 1024;
+__global__ void __launch_bounds__(kViewLossThreads) k_view_loss(const __grid_constant__ BatchDev b,
+                                                                const float* __restrict__ tile_loss) {
     __shared__ double sm[32];
     const ViewDev& vw = b.v[blockIdx.x];
     const uint32_t n = (uint32_t)vw.tiles_x * (uint32_t)vw.tiles_y;
@@ -1250,7 +1283,7 @@ cudaError_t launch_train(const BatchDev& b, const RasterDev& rc, gsc_workspace* 
     }
     if (e == cudaSuccess) {
         PhaseScope ph(kPhLoss, s, 1);
-        k_view_loss<<<b.nviews, 256, 0, s>>>(b, ws->red);
+        k_view_loss<<<b.nviews, kViewLossThreads, 0, s>>>(b, ws->red);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return e;
