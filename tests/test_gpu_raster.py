@@ -237,3 +237,43 @@ def test_nine_bit_pair_sort_gives_the_same_bits(gpu, orc):
     for (x0, y0) in [(300, 220), (0, 0), (624, 464)]:
         ref, marg, _, _ = orc.render(p, cam, window=(x0, y0, 16, 16))
         _compare_forward(nine[:, y0:y0 + 16, x0:x0 + 16], ref, marg)
+
+
+def _deep_stack(n=4000, w=32, h=32, seed=71):
+    """n faint Gaussians spread over a small image in front of the camera:
+    every 16x16 tile keeps about 2,900 of them, its pixels composite 400 to
+    1,000 each, so the backward's hit ring wraps (earlier chunks are rebuilt
+    from their recorded list positions)."""
+    rng = np.random.default_rng(seed)
+    p = synth.gaussians(n, seed)
+    cam = synth.orbit_camera(w, h, 40.0)
+    R = cam.R.astype(np.float64)
+    depth = 2.2 + rng.uniform(-0.3, 0.3, n)
+    xy = rng.uniform(-0.9, 0.9, (n, 2))
+    p[:, 0:3] = (cam.pos + depth[:, None] * R[2] + xy[:, :1] * R[0] + xy[:, 1:] * R[1]).astype(np.float32)
+    p[:, 4:7] = np.float32(-1.08) + rng.normal(0, 0.05, (n, 3)).astype(np.float32)
+    p[:, 3] = np.float32(np.log(0.02 / 0.98))
+    return p, cam
+
+
+def test_deep_lists_wrap_the_hit_ring(gpu, orc):
+    torch = _torch()
+    p, cam = _deep_stack()
+    ref_img, marg, ncon, _ = orc.render(p, cam, grad_margins=True)
+    assert ncon.max() > 900 and ncon.min() > 300  # per-pixel composited terms
+    ws = _ws(gpu, len(p), 1 << 20, cam.width, cam.height)
+    params = torch.from_numpy(p).cuda()
+    dL = np.random.default_rng(8).uniform(-1, 1, (3, cam.height, cam.width))
+    dL[:, marg] = 0.0
+    dL = dL.astype(np.float32)
+    ref, _ = orc.render_backward(p, cam, dL.astype(np.float64))
+    for tile, ppt in [((16, 16), 4), ((8, 8), 1), ((32, 8), 2)]:
+        cfg = gpu.raster_cfg(tile=tile, pixels_per_thread=ppt)
+        img = gpu.cache_render(params, cam, cfg, ws)
+        _, m2, _, _ = orc.render(p, cam)
+        # a pixel tests thousands of alphas: a fifth of them have one within
+        # the margin of a threshold, the rest are compared
+        _compare_forward(img.cpu().numpy().astype(np.float64), ref_img, m2, max_marginal=0.3)
+        g = gpu.cache_backward(params, cam, cfg, ws, torch.from_numpy(dL).cuda())
+        ws.status()
+        _grad_compare(g.cpu().numpy().astype(np.float64), ref, floor_rel=1e-2)
