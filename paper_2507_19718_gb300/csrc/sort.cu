@@ -80,20 +80,30 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
     int warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < 8 * NDIG; i += kSortThreads) (&h[0][0])[i] = 0;
     __syncthreads();
-    // 2048 keys per step, all loads issued before the first match; the trip
-    // count is uniform so that __match_any_sync sees full warps
+    // 2048 keys per step; the next step's keys are loaded before this
+    // step's counts, so one load latency overlaps one step of atomics
+    uint32_t kc[kSortIPT];
+#pragma unroll
+    for (int j = 0; j < kSortIPT; ++j) {
+        uint32_t i = lo + j * kSortThreads + threadIdx.x;
+        kc[j] = i < hi ? keys[i] : 0u;
+    }
     for (uint32_t base = lo; base < hi; base += kSortTile) {
-        int d[kSortIPT];
+        uint32_t kn[kSortIPT];
+        const uint32_t nb = base + kSortTile;
 #pragma unroll
         for (int j = 0; j < kSortIPT; ++j) {
-            uint32_t i = base + j * kSortThreads + threadIdx.x;
-            d[j] = i < hi ? (int)((keys[i] >> shift) & (uint32_t)(NDIG - 1)) : NDIG;
+            uint32_t i = nb + j * kSortThreads + threadIdx.x;
+            kn[j] = i < hi ? keys[i] : 0u;
         }
         // plain shared atomics: measured 1.5x faster over the whole pass than
         // aggregating equal digits with __match_any_sync first
 #pragma unroll
-        for (int j = 0; j < kSortIPT; ++j)
-            if (d[j] < NDIG) atomicAdd(&h[warp][d[j]], 1u);
+        for (int j = 0; j < kSortIPT; ++j) {
+            uint32_t i = base + j * kSortThreads + threadIdx.x;
+            if (i < hi) atomicAdd(&h[warp][(kc[j] >> shift) & (uint32_t)(NDIG - 1)], 1u);
+            kc[j] = kn[j];
+        }
     }
     __syncthreads();
     for (int d = threadIdx.x; d < NDIG; d += kSortThreads) {
@@ -172,19 +182,22 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
         }
     }
     unsigned lt = lanemask_lt();
+    // keys and values of a tile are loaded one tile ahead: the next tile's
+    // loads are issued once this tile sits in shared memory, before its
+    // write-out
+    uint32_t kk[kSortIPT], vv[kSortIPT];
+#pragma unroll
+    for (int j = 0; j < kSortIPT; ++j) {
+        uint32_t i = lo + warp * (kWarp * kSortIPT) + j * kWarp + lane;
+        bool valid = i < hi;
+        kk[j] = valid ? kin[i] : 0u;
+        vv[j] = valid ? vin[i] : 0u;
+    }
     for (uint32_t tile = lo; tile < hi; tile += kSortTile) {
         for (int i = threadIdx.x; i < 8 * NDIG; i += kSortThreads) (&wh[0][0])[i] = 0;
         __syncthreads();
-        uint32_t kk[kSortIPT], vv[kSortIPT], rank[kSortIPT];
+        uint32_t rank[kSortIPT];
         int dd[kSortIPT];
-        // all loads of the tile first, then the ranking
-#pragma unroll
-        for (int j = 0; j < kSortIPT; ++j) {
-            uint32_t i = tile + warp * (kWarp * kSortIPT) + j * kWarp + lane;
-            bool valid = i < hi;
-            kk[j] = valid ? kin[i] : 0u;
-            vv[j] = valid ? vin[i] : 0u;
-        }
 #pragma unroll
         for (int j = 0; j < kSortIPT; ++j) {
             uint32_t i = tile + warp * (kWarp * kSortIPT) + j * kWarp + lane;
@@ -242,6 +255,14 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
                 skey[lp] = kk[j];
                 sval[lp] = vv[j];
             }
+        }
+        const uint32_t nt = tile + kSortTile;
+#pragma unroll
+        for (int j = 0; j < kSortIPT; ++j) {
+            uint32_t i = nt + warp * (kWarp * kSortIPT) + j * kWarp + lane;
+            bool valid = i < hi;
+            kk[j] = valid ? kin[i] : 0u;
+            vv[j] = valid ? vin[i] : 0u;
         }
         __syncthreads();
         // runs of equal digits are contiguous in the output: coalesced stores
