@@ -786,8 +786,8 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
                 const float dx = __fsub_rn(fx, r0.x);
                 float wx, xx = falloff_col(r0, dx, wx);
                 // per entry: sum w dx, sum w dy, sum w dx^2, sum w dx dy, sum w dy^2
-                // (w = dL/dalpha alpha), sum dL/dalpha G, red, green; blue apart.
-                // The pixels of a thread share dx, so the thread sums w, w dy and
+                // (w = dL/dalpha alpha), sum w, red, green; blue apart.  The
+                // pixels of a thread share dx, so the thread sums w, w dy and
                 // w dy^2 and scales by dx (and dx^2) once per entry.
                 float v8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 float sw = 0.f, dcb = 0.f;
@@ -822,7 +822,6 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
                     float dal = fmaf(T[q], dc, -inv * DS[q]);
                     DS[q] = fmaf(wgt, dc, DS[q]);
                     if (araw < rc.alpha_max) {
-                        v8[5] = fmaf(dal, e, v8[5]);
                         float w = dal * alpha;
                         float wy = w * dy;
                         sw += w;
@@ -833,6 +832,7 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
                 v8[0] = sw * dx;
                 v8[2] = v8[0] * dx;
                 v8[3] = v8[1] * dx;
+                v8[5] = sw;
                 if (__any_sync(kFull, any)) {
                     // values 0..7 -> floats 0..5, 8, 9 of the 12-float 2D gradient record
                     float tot = warp_reduce_scatter8(v8, lane);
@@ -879,7 +879,8 @@ __global__ void __launch_bounds__(128) k_project_bwd(const __grid_constant__ Bat
     const float* R = cam.R;
     // The record holds, summed over pixels, w dx, w dy, w dx^2, w dx dy,
     // w dy^2 with w = dL/dalpha alpha = dL/dpower (power = -d^T Q d / 2,
-    // d = pixel - mean), then dL/dalpha G and the colour terms.
+    // d = pixel - mean), then sum w and the colour terms.  Where alpha =
+    // o G is not clamped, dL/do = sum dL/dalpha G = sum w / o.
     float qa = x.a, qb = x.b, qc = x.c;
     float gmx = qa * a0.x + qb * a0.y, gmy = qb * a0.x + qc * a0.y;
     float ga = -0.5f * a0.z, gb = -a0.w, gc = -0.5f * a1.x;
@@ -917,7 +918,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(const __grid_constant__ Bat
     o0.y += R[1] * dtx + R[4] * dty + R[7] * dtz;
     o0.z += R[2] * dtx + R[5] * dty + R[8] * dtz;
     float op = 1.f / (1.f + expf(-p0.w));
-    o0.w += a1.y * op * (1.f - op);  // alpha = sigmoid(logit) G
+    o0.w += a1.y * (1.f - op);  // (sum w / o) do/dlogit, do/dlogit = o (1 - o)
     // Sigma = M M^T: dL/dM = (G + G^T) M with G = dA T0 T0^T + dB T0 T1^T + dC T1 T1^T
     float Gs[9];
 #pragma unroll

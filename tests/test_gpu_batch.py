@@ -207,3 +207,42 @@ def test_batched_step_graph_replays_the_training_step(gpu):
         np.testing.assert_allclose(a.cpu().numpy(), b.cpu().numpy(), rtol=1e-4,
                                    atol=1e-6 * float(b.abs().max()))
         assert float(b.abs().max()) > 0
+
+
+def test_batch_with_many_bins_matches_views_alone(gpu):
+    """Six 1280x720 views with 32-pixel bins: 5,520 bins, so the pair sort
+    takes two radix passes (the bin ranges come from the sorted keys) and
+    the tile order keeps the starts of the bins past the 4,096th in global
+    memory; every image is still the single-view render bit for bit."""
+    import torch
+    scenes = [torch.from_numpy(synth.gaussians(n, 700 + k)).cuda() for k, n in enumerate([1500, 2500])]
+    views = []
+    for i in range(6):
+        cam = gpu.camera(synth.orbit_camera(1280, 720, 23.0 * i))
+        views.append(dict(params=scenes[i % 2], cam=cam, scene=i % 2,
+                          image=torch.zeros((3, 720, 1280), device="cuda"),
+                          dL_dimage=torch.from_numpy(
+                              np.random.default_rng(40 + i).uniform(-1, 1, (3, 720, 1280)).astype(np.float32)).cuda()))
+    cfg = gpu.raster_cfg(tile=(8, 8), list_capacity=256, bin_size=32, pixels_per_thread=1)
+    ws = gpu.Workspace(4000 * 6, 1 << 23, 1280, 720, max_views=6)
+    grads = [torch.zeros_like(s) for s in scenes]
+    for v in views:
+        v["grads"] = grads[v["scene"]]
+    gpu.render_batch(views, gpu.BATCH_FWD | gpu.BATCH_BWD, cfg, ws)
+    ws.status()
+    alone_ws = gpu.Workspace(2500, 1 << 23, 1280, 720)
+    ref_grads = [torch.zeros_like(s) for s in scenes]
+    for v in views:
+        img = gpu.cache_render(v["params"], v["cam"], cfg, alone_ws)
+        gpu.cache_backward(v["params"], v["cam"], cfg, alone_ws, v["dL_dimage"], ref_grads[v["scene"]])
+        alone_ws.status()
+        assert torch.equal(img, v["image"])
+        assert float(img.abs().max()) > 0
+    # a Gaussian near the camera sums 10^5 pixel terms of random sign per
+    # view (three views per scene): the FP32 atomics of the batch and of the
+    # single views add them in different orders, which moves such a sum by up
+    # to a few 1e-4 of itself
+    for g, r in zip(grads, ref_grads):
+        g, r = g.cpu().numpy(), r.cpu().numpy()
+        np.testing.assert_allclose(g, r, rtol=2e-3, atol=1e-5 * np.abs(r).max())
+        assert np.abs(r).max() > 0
