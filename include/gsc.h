@@ -385,6 +385,25 @@ typedef struct gsc_adam_params {
 gsc_status gsc_cache_step(float* params, float* grads, float* m, float* v, int64_t N, const gsc_adam_params* adam,
                           gsc_stream_t stream);
 
+/* gsc_train_batch and gsc_cache_step of every view in one call: the training
+ * step of Sec. 3.6 (render, HDR loss, backward) whose per-Gaussian gradient
+ * kernel also takes the AdamW step, so the parameter gradients never go
+ * through memory.  Views must not share parameters or gradients (each view
+ * is its own cache level); params of every view are updated IN PLACE
+ * (the const in gsc_train_view does not apply here), m[i] and v[i] are view
+ * i's first and second moments (N x 16 FP32 device arrays, 16-B aligned),
+ * and a view's grads, if not NULL, is read as an accumulated gradient (added
+ * to this step's) and zeroed; NULL means none, and saves its traffic.  Every
+ * Gaussian of every view takes the step, whether its view saw it or not,
+ * exactly as gsc_cache_step over the same records would.  Equals
+ * gsc_train_batch followed by gsc_cache_step per view up to the order of
+ * floating-point atomics.  GSC_ERR_INVALID_ARG: adam, m or v NULL, a view's
+ * m or v NULL or misaligned, views sharing parameters, or any condition of
+ * gsc_train_batch.  Graph-capturable. */
+gsc_status gsc_train_step(const gsc_train_view* views, float* const* m, float* const* v, int32_t n_views,
+                          int32_t loss_kind, const gsc_adam_params* adam, const gsc_raster_cfg* cfg,
+                          gsc_workspace* ws, gsc_stream_t stream);
+
 /* Eq. 4: the learning-rate factor 1 / (1 + ln t) after t >= 1 frames of an
  * unchanged viewport (t = 1 on the first frame after a change). */
 float gsc_lr_scale(int32_t t);

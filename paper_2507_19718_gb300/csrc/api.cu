@@ -576,8 +576,10 @@ gsc_status gsc_render_batch(const gsc_view* views, int32_t n_views, int32_t mode
     return GSC_OK;
 }
 
-gsc_status gsc_train_batch(const gsc_train_view* views, int32_t n_views, int32_t loss_kind,
-                           const gsc_raster_cfg* cfg, gsc_workspace* ws, gsc_stream_t stream) {
+// gsc_train_batch, and with adam (m, v: per-view moment arrays) gsc_train_step
+static gsc_status train_views(const gsc_train_view* views, float* const* m, float* const* v_, int32_t n_views,
+                              int32_t loss_kind, const gsc_adam_params* adam, const gsc_raster_cfg* cfg,
+                              gsc_workspace* ws, gsc_stream_t stream) {
     if (!views || n_views < 1 || n_views > kMaxViews)
         return fail(GSC_ERR_INVALID_ARG, "n_views must be in [1, %d]", kMaxViews);
     if (loss_kind != GSC_LOSS_HDR && loss_kind != GSC_LOSS_HDR_FULLGRAD)
@@ -603,12 +605,20 @@ gsc_status gsc_train_batch(const gsc_train_view* views, int32_t n_views, int32_t
         const gsc_train_view& v = views[i];
         if ((st = check_cam(&v.cam))) return st;
         if ((st = check_ws(ws, v.N, &v.cam))) return st;
-        if (v.N > 0 && (!v.params || !aligned(v.params, 16) || !v.grads || !aligned(v.grads, 16)))
+        // the fused step may go without an accumulated gradient (grads NULL)
+        if (v.N > 0 && (!v.params || !aligned(v.params, 16) || (!v.grads && !adam) || !aligned(v.grads, 16)))
             return fail(GSC_ERR_INVALID_ARG, "view %d: params/grads NULL or not 16-B aligned", i);
         if (!v.target || !v.loss) return fail(GSC_ERR_INVALID_ARG, "view %d: target or loss is NULL", i);
+        if (adam && v.N > 0 && (!m[i] || !v_[i] || !aligned(m[i], 16) || !aligned(v_[i], 16)))
+            return fail(GSC_ERR_INVALID_ARG, "view %d: m/v NULL or not 16-B aligned", i);
         total += v.N;
-        for (int j = 0; j < i; ++j)
+        for (int j = 0; j < i; ++j) {
             if (v.grads && v.grads == views[j].grads) shared = true;
+            if (adam && v.N > 0 && views[j].N > 0 &&
+                (v.params == views[j].params || (v.grads && v.grads == views[j].grads)))
+                return fail(GSC_ERR_INVALID_ARG, "views %d and %d share parameters: the fused step needs them apart",
+                            j, i);
+        }
     }
     if (total > ws->max_gaussians)
         return fail(GSC_ERR_INVALID_ARG, "the batch holds %lld Gaussians, the workspace %lld", (long long)total,
@@ -622,6 +632,10 @@ gsc_status gsc_train_batch(const gsc_train_view* views, int32_t n_views, int32_t
         add_view(b, rc, &v.cam, v.params, v.N, v.image, nullptr, v.grads);
         b.v[k].target = v.target;
         b.v[k].loss = v.loss;
+        if (adam) {
+            b.v[k].m = reinterpret_cast<float4*>(m[order[k]]);
+            b.v[k].v = reinterpret_cast<float4*>(v_[order[k]]);
+        }
     }
     if ((int64_t)b.total_bins > ws->max_tiles || (int64_t)b.total_tiles > ws->max_tiles)
         return fail(GSC_ERR_INVALID_ARG, "the batch has %u tiles and %u bins, the workspace %lld (raise max_views)",
@@ -629,12 +643,27 @@ gsc_status gsc_train_batch(const gsc_train_view* views, int32_t n_views, int32_t
     if ((size_t)b.total_tiles > ws->red_floats)
         return fail(GSC_ERR_INVALID_ARG, "the batch has %u tiles, the loss scratch %zu", b.total_tiles,
                     ws->red_floats);
+    AdamDev ad;
+    if (adam) ad = adam_dev(*adam);
     const uint32_t* vals = nullptr;
     cudaError_t e = bin_gaussians(b, rc, ws, &vals, s);
     if (e == cudaSuccess)
-        e = launch_train(b, rc, ws, vals, loss_kind == GSC_LOSS_HDR_FULLGRAD ? 1 : 0, shared, s);
-    if (e != cudaSuccess) return cuda_fail(e, "gsc_train_batch launch");
+        e = launch_train(b, rc, ws, vals, loss_kind == GSC_LOSS_HDR_FULLGRAD ? 1 : 0, shared, adam ? &ad : nullptr,
+                         s);
+    if (e != cudaSuccess) return cuda_fail(e, adam ? "gsc_train_step launch" : "gsc_train_batch launch");
     return GSC_OK;
+}
+
+gsc_status gsc_train_batch(const gsc_train_view* views, int32_t n_views, int32_t loss_kind,
+                           const gsc_raster_cfg* cfg, gsc_workspace* ws, gsc_stream_t stream) {
+    return train_views(views, nullptr, nullptr, n_views, loss_kind, nullptr, cfg, ws, stream);
+}
+
+gsc_status gsc_train_step(const gsc_train_view* views, float* const* m, float* const* v, int32_t n_views,
+                          int32_t loss_kind, const gsc_adam_params* adam, const gsc_raster_cfg* cfg,
+                          gsc_workspace* ws, gsc_stream_t stream) {
+    if (!adam || !m || !v) return fail(GSC_ERR_INVALID_ARG, "adam, m or v is NULL");
+    return train_views(views, m, v, n_views, loss_kind, adam, cfg, ws, stream);
 }
 
 // ------------------------------------------------------------------ cache initialisation

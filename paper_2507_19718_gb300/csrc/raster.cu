@@ -857,25 +857,16 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
     warp_count(&stats[kStHitBack], n_hit2);
 }
 
-// 2D gradients -> packed parameter gradients (+=)
-// (vector atomics when two views of the batch share a parameter set)
-__global__ void __launch_bounds__(128) k_project_bwd(const __grid_constant__ BatchDev b, RasterDev rc,
-                                                     const uint32_t* __restrict__ cnt,
-                                                     const float4* __restrict__ g2d, int shared_params) {
-    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= b.total_g || cnt[g] == 0) return;
-    const ViewDev& vw = b.v[view_of_gaussian(b, g)];
-    const CamDev& cam = vw.cam;
-    const size_t l = g - vw.g_off;
-    const float4* prm = vw.params + 4 * l;
-    float4* grd = vw.grads + 4 * l;
-    float4 a0 = g2d[3 * (size_t)g], a1 = g2d[3 * (size_t)g + 1], a2 = g2d[3 * (size_t)g + 2];
+// The parameter gradient of one Gaussian from its 2D gradient record a0..a2
+// (zero record or not projected: false, o untouched).
+__device__ __forceinline__ bool project_grad(const float4& a0, const float4& a1, const float4& a2, const float4& p0,
+                                             const float4& p1, const float4& p2, const float4& p3, const CamDev& cam,
+                                             const RasterDev& rc, float4& o0, float4& o1, float4& o2, float4& o3) {
     if (a0.x == 0.f && a0.y == 0.f && a0.z == 0.f && a0.w == 0.f && a1.x == 0.f && a1.y == 0.f && a2.x == 0.f &&
         a2.y == 0.f && a2.z == 0.f)
-        return;
-    float4 p0 = prm[0], p1 = prm[1], p2 = prm[2], p3 = prm[3];
+        return false;
     Proj x;
-    if (!project_core(p0, p1, p2, cam, rc, x)) return;
+    if (!project_core(p0, p1, p2, cam, rc, x)) return false;
     const float* R = cam.R;
     // The record holds, summed over pixels, w dx, w dy, w dx^2, w dx dy,
     // w dy^2 with w = dL/dalpha alpha = dL/dpower (power = -d^T Q d / 2,
@@ -913,7 +904,6 @@ __global__ void __launch_bounds__(128) k_project_bwd(const __grid_constant__ Bat
     float dty = dJ12 * (-cam.fy * iz2) + gmy * cam.fy * iz;
     float dtz = dJ00 * (-cam.fx * iz2) + dJ02 * (2.f * cam.fx * tx * iz3) + dJ11 * (-cam.fy * iz2) +
                 dJ12 * (2.f * cam.fy * ty * iz3) - gmx * cam.fx * tx * iz2 - gmy * cam.fy * ty * iz2;
-    float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0, o2 = o0, o3 = o0;
     o0.x += R[0] * dtx + R[3] * dty + R[6] * dtz;
     o0.y += R[1] * dtx + R[4] * dty + R[7] * dtz;
     o0.z += R[2] * dtx + R[5] * dty + R[8] * dtz;
@@ -958,6 +948,24 @@ __global__ void __launch_bounds__(128) k_project_bwd(const __grid_constant__ Bat
     if (p3.x > 0.f) o3.x += a2.x;
     if (p3.y > 0.f) o3.y += a2.y;
     if (p3.z > 0.f) o3.z += a2.z;
+    return true;
+}
+
+// 2D gradients -> packed parameter gradients (+=), with vector atomics when
+// two views of the batch share a parameter set.
+__global__ void __launch_bounds__(128) k_project_bwd(const __grid_constant__ BatchDev b, RasterDev rc,
+                                                     const uint32_t* __restrict__ cnt,
+                                                     const float4* __restrict__ g2d, int shared_params) {
+    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= b.total_g || cnt[g] == 0) return;
+    const ViewDev& vw = b.v[view_of_gaussian(b, g)];
+    const size_t l = g - vw.g_off;
+    const float4* prm = vw.params + 4 * l;
+    float4* grd = vw.grads + 4 * l;
+    float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0, o2 = o0, o3 = o0;
+    if (!project_grad(g2d[3 * (size_t)g], g2d[3 * (size_t)g + 1], g2d[3 * (size_t)g + 2], prm[0], prm[1], prm[2],
+                      prm[3], vw.cam, rc, o0, o1, o2, o3))
+        return;
     if (shared_params) {
         atomicAdd(&grd[0], o0);
         atomicAdd(&grd[1], o1);
@@ -969,6 +977,46 @@ __global__ void __launch_bounds__(128) k_project_bwd(const __grid_constant__ Bat
         grd[1] = make_float4(c1.x + o1.x, c1.y + o1.y, c1.z + o1.z, c1.w + o1.w);
         grd[2] = make_float4(c2.x + o2.x, c2.y + o2.y, c2.z + o2.z, c2.w + o2.w);
         grd[3] = make_float4(c3.x + o3.x, c3.y + o3.y, c3.z + o3.z, c3.w + o3.w);
+    }
+}
+
+// The fused training step's per-Gaussian kernel: the parameter gradient of
+// every Gaussian of the batch (zero where no tile saw it), plus the
+// accumulated one when the view has a gradient array (which is then zeroed),
+// and the AdamW step of its record, exactly as gsc_cache_step would take it.
+// One thread per Gaussian: the projection gradient is computed once (four
+// threads per Gaussian, each owning one float4 of the record, were measured
+// 1.6x slower: the projection arithmetic then runs four times).
+__global__ void __launch_bounds__(128) k_project_bwd_step(const __grid_constant__ BatchDev b, RasterDev rc,
+                                                          const uint32_t* __restrict__ cnt,
+                                                          const float4* __restrict__ g2d,
+                                                          const __grid_constant__ AdamDev adam) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= b.total_g) return;
+    const ViewDev& vw = b.v[view_of_gaussian(b, g)];
+    const size_t l = g - vw.g_off;
+    float4* prm = const_cast<float4*>(vw.params) + 4 * l;
+    float4 P[4] = {prm[0], prm[1], prm[2], prm[3]};
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 G[4] = {z, z, z, z};
+    if (cnt[g] != 0)
+        project_grad(g2d[3 * (size_t)g], g2d[3 * (size_t)g + 1], g2d[3 * (size_t)g + 2], P[0], P[1], P[2], P[3],
+                     vw.cam, rc, G[0], G[1], G[2], G[3]);
+    float4* grd = vw.grads ? vw.grads + 4 * l : nullptr;
+    float4* mp = vw.m + 4 * l;
+    float4* vp = vw.v + 4 * l;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (grd) {
+            const float4 c = grd[q];
+            G[q] = make_float4(c.x + G[q].x, c.y + G[q].y, c.z + G[q].z, c.w + G[q].w);
+            grd[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float4 m = mp[q], v = vp[q];
+        adam_four(P[q], m, v, G[q], q, adam);
+        prm[q] = P[q];
+        mp[q] = m;
+        vp[q] = v;
     }
 }
 
@@ -1260,11 +1308,16 @@ __global__ void __launch_bounds__(kViewLossThreads) k_view_loss(const __grid_con
 }
 
 static cudaError_t project_backward(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, bool shared_params,
-                                    cudaStream_t s) {
+                                    const AdamDev* adam, cudaStream_t s) {
     uint32_t nblk = (b.total_g + 127) / 128;
     if (nblk == 0) nblk = 1;
-    PhaseScope ph(kPhProjectBwd, s, 1);
-    k_project_bwd<<<nblk, 128, 0, s>>>(b, rc, ws->cnt, ws->g2d, shared_params ? 1 : 0);
+    if (adam) {
+        PhaseScope ph(kPhAdam, s, 1);
+        k_project_bwd_step<<<nblk, 128, 0, s>>>(b, rc, ws->cnt, ws->g2d, *adam);
+    } else {
+        PhaseScope ph(kPhProjectBwd, s, 1);
+        k_project_bwd<<<nblk, 128, 0, s>>>(b, rc, ws->cnt, ws->g2d, shared_params ? 1 : 0);
+    }
     return cudaGetLastError();
 }
 
@@ -1278,11 +1331,11 @@ cudaError_t launch_render_backward(const BatchDev& b, const RasterDev& rc, gsc_w
         e = launch();
     }
     if (e != cudaSuccess) return e;
-    return project_backward(b, rc, ws, shared_params, s);
+    return project_backward(b, rc, ws, shared_params, nullptr, s);
 }
 
 cudaError_t launch_train(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
-                         int full_grad, bool shared_params, cudaStream_t s) {
+                         int full_grad, bool shared_params, const AdamDev* adam, cudaStream_t s) {
     cudaError_t e;
     {
         PhaseScope ph(kPhTrain, s, 1);
@@ -1299,7 +1352,7 @@ cudaError_t launch_train(const BatchDev& b, const RasterDev& rc, gsc_workspace* 
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return e;
-    return project_backward(b, rc, ws, shared_params, s);
+    return project_backward(b, rc, ws, shared_params, adam, s);
 }
 
 }  // namespace gsc

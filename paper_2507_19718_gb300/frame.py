@@ -50,8 +50,10 @@ class FrameLoop:
     ``fused_train`` (default, with ``fused``): when the tracer does not read
     the cache images (C <= 0), a frame is trace -> one training step that
     renders every level, evaluates the HDR loss against its buffer and
-    differentiates in the same launch (gsc_train_batch) -> AdamW.  The
-    rendered images are the same bits as a separate forward."""
+    differentiates in the same launch, then turns the 2D gradients into
+    parameter gradients and takes the AdamW step in one more kernel
+    (gsc_train_step).  The rendered images are the same bits as a separate
+    forward."""
 
     def __init__(self, scene: synth.Scene, level_sizes, width: int, height: int, spp: int = 1,
                  max_bounces: int = 8, seed: int = synth.BASE_SEED, tile=(16, 16), list_capacity: int = 256,
@@ -149,13 +151,14 @@ class FrameLoop:
             gsc.cache_step(L.params, L.grads, L.m, L.v, adam, stream=stream)
 
     def train_step(self, c: gsc.Camera, lr_scale: float, stream=None):
-        """Render + HDR loss + backward of all levels in one launch, then AdamW."""
+        """Render + HDR loss + backward of all levels in one launch, the
+        per-Gaussian gradients and the AdamW step in one more (gsc_train_step)."""
         self.adam_step += 1
         adam = gsc.adam_params(self.lr, weight_decay=self.weight_decay, lr_scale=lr_scale, step=self.adam_step)
-        views = [dict(params=L.params, cam=c, target=self.targets[k], image=self.renders[k], grads=L.grads,
-                      loss=self.losses[k]) for k, L in enumerate(self.levels)]
-        gsc.train_batch(views, self.cfg_bwd or self.cfg, self.ws, gsc.LOSS_HDR, stream=stream)
-        gsc.cache_step(*self.store, adam, stream=stream)
+        # no gradient is accumulated between frames, so none is passed
+        views = [dict(params=L.params, cam=c, target=self.targets[k], image=self.renders[k], loss=self.losses[k],
+                      m=L.m, v=L.v) for k, L in enumerate(self.levels)]
+        gsc.train_step(views, adam, self.cfg_bwd or self.cfg, self.ws, gsc.LOSS_HDR, stream=stream)
 
     def frame(self, cam, frame: int, stream=None):
         """One frame: render the cache (its images feed the tracer when C > 0),

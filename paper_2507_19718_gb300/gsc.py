@@ -106,6 +106,8 @@ SIGNATURES = {
     "gsc_cache_backward": (_i32, [_vp, _i64, C.POINTER(Camera), C.POINTER(RasterCfg), _vp, _vp, _vp, _vp]),
     "gsc_render_batch": (_i32, [C.POINTER(View), _i32, _i32, C.POINTER(RasterCfg), _vp, _vp]),
     "gsc_train_batch": (_i32, [C.POINTER(TrainView), _i32, _i32, C.POINTER(RasterCfg), _vp, _vp]),
+    "gsc_train_step": (_i32, [C.POINTER(TrainView), C.POINTER(_vp), C.POINTER(_vp), _i32, _i32,
+                              C.POINTER(AdamParams), C.POINTER(RasterCfg), _vp, _vp]),
     "gsc_loss": (_i32, [_i32, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
     "gsc_loss_noalloc": (_i32, [_i32, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp]),
     "gsc_cache_step": (_i32, [_vp, _vp, _vp, _vp, _i64, C.POINTER(AdamParams), _vp]),
@@ -406,10 +408,7 @@ def render_batch(views, mode: int, cfg: RasterCfg, ws: Workspace, stream=None):
     _check(lib().gsc_render_batch(arr, len(views), mode, C.byref(cfg), ws.handle, _stream(stream)))
 
 
-def train_batch(views, cfg: RasterCfg, ws: Workspace, loss_kind: int = 0, stream=None):
-    """gsc_train_batch: render + HDR loss + backward of every view in one
-    launch.  views: dicts with params (N x 16), cam, target (3 x H x W),
-    grads (N x 16, +=), loss (device scalar) and optionally image."""
+def _train_views(views):
     arr = (TrainView * len(views))()
     for i, v in enumerate(views):
         p = v["params"]
@@ -417,18 +416,45 @@ def train_batch(views, cfg: RasterCfg, ws: Workspace, loss_kind: int = 0, stream
         c = v["cam"] if isinstance(v["cam"], Camera) else camera(v["cam"])
         npx = 3 * c.width * c.height
         _need(v["target"], "target", npx)
-        _need(v["grads"], "grads", p.numel())
         arr[i].params = p.data_ptr()
         arr[i].N = p.numel() // 16
         arr[i].cam = c
         arr[i].target = v["target"].data_ptr()
-        arr[i].grads = v["grads"].data_ptr()
+        if v.get("grads") is not None:  # train_step: optional (no accumulated gradient)
+            _need(v["grads"], "grads", p.numel())
+            arr[i].grads = v["grads"].data_ptr()
         _need(v["loss"], "loss", 1)
         arr[i].loss = v["loss"].data_ptr()
         if v.get("image") is not None:
             _need(v["image"], "image", npx)
             arr[i].image = v["image"].data_ptr()
+    return arr
+
+
+def train_batch(views, cfg: RasterCfg, ws: Workspace, loss_kind: int = 0, stream=None):
+    """gsc_train_batch: render + HDR loss + backward of every view in one
+    launch.  views: dicts with params (N x 16), cam, target (3 x H x W),
+    grads (N x 16, +=), loss (device scalar) and optionally image."""
+    arr = _train_views(views)
     _check(lib().gsc_train_batch(arr, len(views), loss_kind, C.byref(cfg), ws.handle, _stream(stream)))
+
+
+def train_step(views, adam: AdamParams, cfg: RasterCfg, ws: Workspace, loss_kind: int = 0, stream=None):
+    """gsc_train_step: train_batch with the AdamW step of every view's
+    parameters fused into the gradient kernel.  views: as train_batch plus m
+    and v (N x 16 each); params are updated in place; grads (optional) is an
+    accumulated gradient, read and zeroed; views must not share parameters."""
+    arr = _train_views(views)
+    M = (_vp * len(views))()
+    V = (_vp * len(views))()
+    for i, v in enumerate(views):
+        n = v["params"].numel()
+        _need(v["m"], "m", n)
+        _need(v["v"], "v", n)
+        M[i] = v["m"].data_ptr()
+        V[i] = v["v"].data_ptr()
+    _check(lib().gsc_train_step(arr, M, V, len(views), loss_kind, C.byref(adam), C.byref(cfg), ws.handle,
+                                _stream(stream)))
 
 
 def loss(kind: int, pred: torch.Tensor, target: torch.Tensor, ws: Workspace, crop=None,

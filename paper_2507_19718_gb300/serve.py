@@ -90,8 +90,9 @@ class ResidentScene:
 class Trainer:
     """Retraining frames of one scene at a fixed training view: trace the K
     target buffers, then one training step for all levels (render, HDR loss
-    and backward in one launch, gsc_train_batch) and AdamW per level.
-    max_gaussians: the largest scene's total over its levels."""
+    and backward in one launch, the per-Gaussian gradients and AdamW in one
+    more: gsc_train_step).  max_gaussians: the largest scene's total over its
+    levels."""
 
     def __init__(self, width: int, height: int, levels: int, max_gaussians: int, cfg: gsc.RasterCfg,
                  spp: int = 1, max_bounces: int = 8, lr=None, weight_decay: float = 0.01, device="cuda"):
@@ -115,11 +116,9 @@ class Trainer:
                                lr_scale=gsc.lr_scale(sc.static_frames), step=sc.adam_step)
         gsc.trace(sc.handle, c, self.spp, self.max_bounces, self.K, seed, frame, targets=self.targets,
                   image=self.image, stream=stream)
-        views = [dict(params=L.params, cam=c, target=self.targets[k], grads=L.grads, loss=self.loss[k])
+        views = [dict(params=L.params, cam=c, target=self.targets[k], loss=self.loss[k], m=L.m, v=L.v)
                  for k, L in enumerate(sc.levels)]
-        gsc.train_batch(views, self.cfg, self.ws, gsc.LOSS_HDR, stream=stream)
-        for L in sc.levels:
-            gsc.cache_step(L.params, L.grads, L.m, L.v, adam, stream=stream)
+        gsc.train_step(views, adam, self.cfg, self.ws, gsc.LOSS_HDR, stream=stream)
         sc.frames_trained += 1
 
 

@@ -93,6 +93,15 @@ def test_host_side_validation(L):
     tviews = (gsc.TrainView * 2)()
     assert L.gsc_train_batch(tviews, 0, 0, C.byref(cfg0), None, None) == gsc.GSC_ERR_INVALID_ARG
     assert L.gsc_train_batch(tviews, 2, gsc.LOSS_L1_SSIM, C.byref(cfg0), None, None) == gsc.GSC_ERR_INVALID_ARG
+    # fused training step: adam, m and v are required
+    mv = (C.c_void_p * 2)(256, 256)
+    a1 = gsc.adam_params([0.01] * 16)
+    assert L.gsc_train_step(tviews, mv, mv, 2, gsc.LOSS_HDR, None, C.byref(cfg0), None, None) == \
+        gsc.GSC_ERR_INVALID_ARG
+    assert L.gsc_train_step(tviews, None, mv, 2, gsc.LOSS_HDR, C.byref(a1), C.byref(cfg0), None, None) == \
+        gsc.GSC_ERR_INVALID_ARG
+    assert L.gsc_train_step(tviews, mv, mv, 0, gsc.LOSS_HDR, C.byref(a1), C.byref(cfg0), None, None) == \
+        gsc.GSC_ERR_INVALID_ARG
     # render: bad tile shape, then NULL workspace
     cam = gsc.Camera()
     cam.fx = cam.fy = 100.0

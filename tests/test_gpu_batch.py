@@ -246,3 +246,104 @@ def test_batch_with_many_bins_matches_views_alone(gpu):
         g, r = g.cpu().numpy(), r.cpu().numpy()
         np.testing.assert_allclose(g, r, rtol=2e-3, atol=1e-5 * np.abs(r).max())
         assert np.abs(r).max() > 0
+
+
+def test_train_step_equals_train_batch_then_cache_step(gpu):
+    """gsc_train_step (the AdamW step fused into the per-Gaussian gradient
+    kernel) against gsc_train_batch followed by gsc_cache_step per level, on
+    three levels with gradients already accumulated and moments from earlier
+    steps: images bit for bit, losses to summation order, parameters and
+    moments to the order of the gradient atomics; Gaussians no tile saw
+    (behind the camera) take exactly the step of their accumulated
+    gradient."""
+    import torch
+    rng = np.random.default_rng(91)
+    cam = synth.orbit_camera(96, 80, 25.0)
+    fwd = cam.R[2].astype(np.float64)
+    levels = []
+    for k, n in enumerate([700, 350, 175]):
+        p = synth.gaussians(n, 900 + k)
+        p[:5, 0:3] = (cam.pos - 0.5 * fwd).astype(np.float32)  # behind the camera: never seen
+        g = rng.normal(0, 1e-3, (n, 16)).astype(np.float32)
+        m = rng.normal(0, 1e-3, (n, 16)).astype(np.float32)
+        v = rng.uniform(1e-6, 1e-5, (n, 16)).astype(np.float32)
+        levels.append((p, g, m, v))
+    target = torch.from_numpy(rng.uniform(0, 1, (3, 80, 96)).astype(np.float32)).cuda()
+    cfg = gpu.raster_cfg(tile=(16, 16), list_capacity=256, bin_size=32, pixels_per_thread=4)
+    ws = gpu.Workspace(1225, 1 << 22, 96, 80, max_views=3)
+    adam = gpu.adam_params(gpu.PAPER_LR, lr_scale=0.7, step=6)
+
+    def state():
+        return [tuple(torch.from_numpy(a.copy()).cuda() for a in L) for L in levels]
+
+    def views(st, losses, imgs):
+        return [dict(params=P, cam=cam, target=target, image=imgs[k], grads=G, loss=losses[k], m=M, v=V)
+                for k, (P, G, M, V) in enumerate(st)]
+
+    sa, la, ia = state(), torch.zeros(3, device="cuda"), [torch.zeros(3, 80, 96, device="cuda") for _ in range(3)]
+    gpu.train_batch(views(sa, la, ia), cfg, ws, gpu.LOSS_HDR)
+    for P, G, M, V in sa:
+        gpu.cache_step(P, G, M, V, adam)
+    ws.status()
+    sb, lb, ib = state(), torch.zeros(3, device="cuda"), [torch.zeros(3, 80, 96, device="cuda") for _ in range(3)]
+    gpu.train_step(views(sb, lb, ib), adam, cfg, ws, gpu.LOSS_HDR)
+    ws.status()
+    for a, b in zip(ia, ib):
+        assert torch.equal(a, b)
+    np.testing.assert_allclose(la.cpu().numpy(), lb.cpu().numpy(), rtol=2e-6)
+    for (Pa, Ga, Ma, Va), (Pb, Gb, Mb, Vb), (p0, _, _, _) in zip(sa, sb, levels):
+        Pa, Ma, Va, Pb, Mb, Vb = (x.cpu().numpy().astype(np.float64) for x in (Pa, Ma, Va, Pb, Mb, Vb))
+        assert float(Gb.abs().max()) == 0.0 and float(Ga.abs().max()) == 0.0
+        dp = np.abs(Pa - p0)
+        assert dp.max() > 0
+        assert np.all(np.abs(Pb - Pa) <= 1e-6 * np.abs(Pa) + 1e-3 * dp + 1e-9)
+        np.testing.assert_allclose(Mb, Ma, rtol=1e-4, atol=1e-6 * np.abs(Ma).max())
+        np.testing.assert_allclose(Vb, Va, rtol=1e-4, atol=1e-6 * np.abs(Va).max())
+        # the unseen Gaussians: the same arithmetic on the same gradient
+        np.testing.assert_array_equal(Pb[:5], Pa[:5])
+        np.testing.assert_array_equal(Mb[:5], Ma[:5])
+        np.testing.assert_array_equal(Vb[:5], Va[:5])
+
+
+def test_train_step_rejects_shared_parameters(gpu):
+    import torch
+    p = torch.from_numpy(synth.gaussians(100, 5)).cuda()
+    g, m, v = torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p)
+    cam = synth.orbit_camera(32, 32, 0.0)
+    t = torch.zeros(3, 32, 32, device="cuda")
+    loss = torch.zeros(2, device="cuda")
+    ws = gpu.Workspace(200, 1 << 20, 32, 32, max_views=2)
+    views = [dict(params=p, cam=cam, target=t, grads=g, loss=loss[k], m=m, v=v) for k in range(2)]
+    with pytest.raises(gpu.GscError) as e:
+        gpu.train_step(views, gpu.adam_params(gpu.PAPER_LR), gpu.raster_cfg(), ws, gpu.LOSS_HDR)
+    assert e.value.status == gpu.GSC_ERR_INVALID_ARG
+
+
+def test_train_step_without_accumulated_gradient(gpu):
+    """grads = None in gsc_train_step means no accumulated gradient: the
+    same step as passing zeros (to the order of the gradient atomics;
+    Gaussians no tile saw bit for bit)."""
+    import torch
+    cam = synth.orbit_camera(64, 48, 10.0)
+    p = synth.gaussians(400, 31)
+    p[:3, 0:3] = (cam.pos - 0.5 * cam.R[2].astype(np.float64)).astype(np.float32)
+    rng = np.random.default_rng(4)
+    m0 = rng.normal(0, 1e-3, p.shape).astype(np.float32)
+    v0 = rng.uniform(1e-6, 1e-5, p.shape).astype(np.float32)
+    target = torch.from_numpy(rng.uniform(0, 1, (3, 48, 64)).astype(np.float32)).cuda()
+    ws = gpu.Workspace(400, 1 << 20, 64, 48)
+    cfg = gpu.raster_cfg()
+    adam = gpu.adam_params(gpu.PAPER_LR, step=3)
+    out = []
+    for with_grads in (True, False):
+        P, M, V = (torch.from_numpy(a.copy()).cuda() for a in (p, m0, v0))
+        view = dict(params=P, cam=cam, target=target, loss=torch.zeros((), device="cuda"), m=M, v=V)
+        if with_grads:
+            view["grads"] = torch.zeros_like(P)
+        gpu.train_step([view], adam, cfg, ws, gpu.LOSS_HDR)
+        ws.status()
+        out.append([x.cpu().numpy() for x in (P, M, V)])
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_allclose(b, a, rtol=1e-4, atol=1e-6 * np.abs(a).max())
+        np.testing.assert_array_equal(b[:3], a[:3])
+    assert np.abs(out[1][0] - p).max() > 0
