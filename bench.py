@@ -670,6 +670,10 @@ def main():
     res, cfg = run_ours(args, world, rank, local)
     import torch
     torch.cuda.empty_cache()
+    # mixed resolutions: the tuned tile, capacity and pixels per thread, the
+    # bin size chosen per view (bin_size 0)
+    cfg = type(cfg).from_buffer_copy(cfg)
+    cfg.bin_size = 0
     if not args.no_batched:
         res["batched"] = run_batched_bench(args, cfg)
     if not args.no_served:

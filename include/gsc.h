@@ -78,8 +78,9 @@ typedef struct gsc_camera {
 /* Rasterizer configuration.  Tiles (one CTA each, one thread per pixel):
  * 16x16, 8x8, 32x8, 16x8, 8x16, 8x32 or 32x4.  Gaussians are binned into
  * coarse square bins of bin_size pixels (a multiple of tile_w and tile_h,
- * 32..512; 0 = 64); every tile walks its bin's depth-ordered list and keeps
- * the Gaussians whose support reaches the tile.  list_capacity: entries
+ * 32..512; 0 = per view, the largest of 256, 128, 64 and 32 px at most a
+ * twelfth of the view's longer side); every tile walks its bin's
+ * depth-ordered list and keeps the Gaussians whose support reaches the tile.  list_capacity: entries
  * staged in shared memory per batch (32..2048, multiple of 32; raised to the
  * tile's thread count if smaller).  alpha_max (0.99), alpha_min (1/255),
  * T_min (1e-4), near_plane (0.2) and dilation (0.3 px^2) are the compositing

@@ -166,10 +166,20 @@ RasterDev raster_dev(const gsc_raster_cfg* c) {
     r.ppt = c->pixels_per_thread ? c->pixels_per_thread : 1;
     int nt = c->tile_w * c->tile_h / r.ppt;
     r.cap = c->list_capacity < nt ? nt : c->list_capacity;
-    r.bin = c->bin_size ? c->bin_size : 64;
-    r.spt_x = r.bin / c->tile_w;
-    r.spt_y = r.bin / c->tile_h;
+    r.bin = c->bin_size;
     return r;
+}
+
+// Bin size of a view when the configuration leaves it open: the largest of
+// 256, 128, 64 and 32 px at most a twelfth of the longer image side (32 at
+// least), so that a tile's bin list stays a small part of the image
+// whatever its resolution (1080p: 128, the size tuned for it; 720p: 64;
+// 640x480 and below: 32).  Every candidate is a multiple of every tile side.
+static int auto_bin(int w, int h) {
+    const int side = w > h ? w : h;
+    int bin = 256;
+    while (bin > 32 && bin * 12 > side) bin /= 2;
+    return bin;
 }
 
 // Append one view to a batch table (tiles and bins numbered after the
@@ -189,8 +199,11 @@ void add_view(BatchDev& b, const RasterDev& rc, const gsc_camera* cam, const flo
     v.N = (uint32_t)N;
     v.tiles_x = (cam->width + rc.tile_w - 1) / rc.tile_w;
     v.tiles_y = (cam->height + rc.tile_h - 1) / rc.tile_h;
-    v.bins_x = (cam->width + rc.bin - 1) / rc.bin;
-    v.bins_y = (cam->height + rc.bin - 1) / rc.bin;
+    v.bin = rc.bin ? rc.bin : auto_bin(cam->width, cam->height);
+    v.spt_x = v.bin / rc.tile_w;
+    v.spt_y = v.bin / rc.tile_h;
+    v.bins_x = (cam->width + v.bin - 1) / v.bin;
+    v.bins_y = (cam->height + v.bin - 1) / v.bin;
     v.tile_off = b.total_tiles;
     v.bin_off = b.total_bins;
     b.total_g += (uint32_t)N;

@@ -36,8 +36,8 @@ struct CamDev {
 struct RasterDev {
     float alpha_max, alpha_min, T_min, near_plane, dilation;
     int tile_w, tile_h, cap;
-    int bin, spt_x, spt_y;  // bin size (px), tiles per bin side
-    int ppt;                // pixels per thread (1, 2, 4 or 8)
+    int bin;  // bin size (px) of every view; 0: each view picks its own (auto_bin)
+    int ppt;  // pixels per thread (1, 2, 4 or 8)
 };
 
 // One view of a (possibly batched) render: its camera, its Gaussians (global
@@ -57,6 +57,7 @@ struct ViewDev {
     float4* v;
     uint32_t g_off, N, tile_off, bin_off;
     int tiles_x, tiles_y, bins_x, bins_y;
+    int bin, spt_x, spt_y;  // the view's bin size (px) and tiles per bin side
 };
 struct BatchDev {
     int nviews;

@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchDe
     uint32_t tx0 = ilo / rc.tile_w, tx1 = ihi / rc.tile_w + 1;
     uint32_t ty0 = jlo / rc.tile_h, ty1 = jhi / rc.tile_h + 1;
     rect[g] = make_uint2(tx0 | (tx1 << 16), ty0 | (ty1 << 16));
-    uint32_t bx0 = ilo / rc.bin, bx1 = ihi / rc.bin + 1;
-    uint32_t by0 = jlo / rc.bin, by1 = jhi / rc.bin + 1;
+    uint32_t bx0 = ilo / vw.bin, bx1 = ihi / vw.bin + 1;
+    uint32_t by0 = jlo / vw.bin, by1 = jhi / vw.bin + 1;
     cnt[g] = (bx1 - bx0) * (by1 - by0);
     key[g] = __float_as_uint(x.t[2]);
     float h = -0.5f * kLog2e;
@@ -221,11 +221,11 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ BatchDev b
     uint32_t bx0 = 0, by0 = 0, wx = 1, boff = 0, bins_x = 0;
     if (c) {
         uint2 rr = rect[g];
-        bx0 = (rr.x & 0xffffu) / rc.spt_x;
-        uint32_t bx1 = ((rr.x >> 16) - 1) / rc.spt_x + 1;
-        by0 = (rr.y & 0xffffu) / rc.spt_y;
-        wx = bx1 - bx0;
         const ViewDev& vw = b.v[view_of_gaussian(b, g)];
+        bx0 = (rr.x & 0xffffu) / vw.spt_x;
+        uint32_t bx1 = ((rr.x >> 16) - 1) / vw.spt_x + 1;
+        by0 = (rr.y & 0xffffu) / vw.spt_y;
+        wx = bx1 - bx0;
         boff = vw.bin_off;
         bins_x = (uint32_t)vw.bins_x;
     }
@@ -243,7 +243,13 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ BatchDev b
         const uint32_t x0 = __shfl_sync(kFull, bx0, j), y0 = __shfl_sync(kFull, by0, j);
         const uint32_t bo = __shfl_sync(kFull, boff, j), bxn = __shfl_sync(kFull, bins_x, j);
         if (e < end) {
-            const uint32_t ky = k / wj, kx = k - ky * wj;
+            // row of pair k in a rectangle wj bins wide, floor((k + 1/2) / wj)
+            // in FP32: the quotient stays 1 / (2 wj) away from an integer and
+            // its two roundings move it by at most (k + 1/2) 2^-23 / wj, which
+            // is less while k < 2^22 - 1/2 (a view has at most 2048 x 2048
+            // bins of 32 px, so k < 2^22)
+            const uint32_t ky = (uint32_t)(((float)k + 0.5f) * __frcp_rn((float)wj));
+            const uint32_t kx = k - ky * wj;
             pkey[e] = bo + (y0 + ky) * bxn + x0 + kx;
             pval[e] = gj;
         }
@@ -391,7 +397,7 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render(const __grid_constant__
         Cr[q] = Cg[q] = Cb[q] = 0.f;
         ev[q] = inside[q] ? 0xffffffffu : 0u;
     }
-    uint2 rg = ranges[vw.bin_off + (ty / rc.spt_y) * vw.bins_x + tx / rc.spt_x];
+    uint2 rg = ranges[vw.bin_off + (ty / vw.spt_y) * vw.bins_x + tx / vw.spt_x];
     uint32_t pos = rg.x;
     uint32_t hbase = 0;  // entries staged by earlier batches of this tile
     for (;;) {
@@ -604,7 +610,7 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
         T[q] = 1.f;
         ev[q] = active[q] ? 0xffffffffu : 0u;
     }
-    uint2 rg = ranges[vw.bin_off + (ty / rc.spt_y) * vw.bins_x + tx / rc.spt_x];
+    uint2 rg = ranges[vw.bin_off + (ty / vw.spt_y) * vw.bins_x + tx / vw.spt_x];
 
     // ---- phase 1
     uint32_t nhit = 0;  // hits found so far (uniform)
@@ -1087,7 +1093,7 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_const
         const ViewDev& vw = b.v[view_of_bin(b, bin)];
         const uint32_t lb = bin - vw.bin_off;
         const int bx = (int)(lb % (uint32_t)vw.bins_x), by = (int)(lb / (uint32_t)vw.bins_x);
-        const int w = min(rc.spt_x, vw.tiles_x - bx * rc.spt_x), h = min(rc.spt_y, vw.tiles_y - by * rc.spt_y);
+        const int w = min(vw.spt_x, vw.tiles_x - bx * vw.spt_x), h = min(vw.spt_y, vw.tiles_y - by * vw.spt_y);
         ntiles = (uint32_t)(w * h);
         const uint2 rg = ranges[bin];
         const float l = log2f((float)(rg.y - rg.x) + 1.0f) * 8.0f;
@@ -1115,10 +1121,10 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_const
         const ViewDev& vw = b.v[view_of_tile(b, t)];
         const uint32_t lt = t - vw.tile_off;
         const int tx = (int)(lt % (uint32_t)vw.tiles_x), ty = (int)(lt / (uint32_t)vw.tiles_x);
-        const int bx = tx / rc.spt_x, by = ty / rc.spt_y;
+        const int bx = tx / vw.spt_x, by = ty / vw.spt_y;
         const uint32_t bin = vw.bin_off + (uint32_t)(by * vw.bins_x + bx);
-        const int w = min(rc.spt_x, vw.tiles_x - bx * rc.spt_x);
-        const uint32_t local = (uint32_t)((ty - by * rc.spt_y) * w + (tx - bx * rc.spt_x));
+        const int w = min(vw.spt_x, vw.tiles_x - bx * vw.spt_x);
+        const uint32_t local = (uint32_t)((ty - by * vw.spt_y) * w + (tx - bx * vw.spt_x));
         const uint32_t st = bin < (uint32_t)kOrderCachedBins ? s_start[bin] : bin_start[bin];
         order[st + local] = t;
     }

@@ -101,7 +101,9 @@ class Trainer:
         self.spp, self.max_bounces = spp, max_bounces
         self.lr = np.asarray(gsc.PAPER_LR if lr is None else lr, np.float32)
         self.weight_decay = weight_decay
-        pairs = int(max_gaussians * max(8.0, 96.0 * width * height / (1920 * 1080)))
+        # bins chosen per view (bin_size 0) go down to 32 px, so a Gaussian
+        # can reach a dozen bins even at training resolution
+        pairs = int(max_gaussians * max(24.0, 96.0 * width * height / (1920 * 1080)))
         self.ws = gsc.Workspace(max_gaussians, pairs, width, height, device, max_views=levels)
         f32 = dict(dtype=torch.float32, device=device)
         self.targets = torch.zeros((levels, 3, height, width), **f32)
@@ -169,7 +171,9 @@ class Server:
         queue = collections.deque()
         inflight = collections.deque()        # (event, requests, workspace index, bytes)
         free_ws = list(range(len(self.view_ws)))
-        rs, ts = torch.cuda.Stream(), torch.cuda.Stream()
+        # views on a higher-priority stream: when a CTA of the retraining
+        # frame retires, the block scheduler hands the SM to a view's CTA first
+        rs, ts = torch.cuda.Stream(priority=-1), torch.cuda.Stream(priority=0)
         tf_waiting = collections.defaultdict(list)   # scene -> TF requests completed by its retraining
         last_train_ev = {}                    # scene -> event of its last enqueued training frame
         last_render_ev = {}                   # scene -> event of its last enqueued render batch
