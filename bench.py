@@ -549,6 +549,10 @@ def run_served_bench(args, cfg_tuned):
         torch.cuda.synchronize()
 
     srv = serve.Server(scenes, cfg_tuned)
+    # the retraining frames run at 320x240: their launch configuration is
+    # tuned there, on the largest scene
+    trials = srv.trainer.tune(max(scenes, key=lambda s: s.n_gaussians))
+    best_train = min(trials, key=lambda t: t.ms)
     warm = serve.poisson_trace(200.0, 0.5, 8, seed=synth.BASE_SEED + 70)
     srv.run_batched(copy.deepcopy(warm))
     srv.run_plain(copy.deepcopy(warm))
@@ -556,7 +560,8 @@ def run_served_bench(args, cfg_tuned):
     out = {"workload": f"8 resident scenes (256^3, 200k..1M Gaussians x 3 levels), Poisson 200 req/s for "
                        f"{args.serve_seconds:g} s, 90% views (256^2..1080p), 10% TF changes (16 retraining "
                        f"frames at 320x240)", "requests": len(trace),
-           "hbm_budget_gb": round(srv.budget / 1e9, 1)}
+           "hbm_budget_gb": round(srv.budget / 1e9, 1),
+           "retrain_launch": dict(_launch_cfg(best_train), ms=round(best_train.ms, 3))}
     for mode in ("batched", "plain"):
         reset()
         tr = copy.deepcopy(trace)

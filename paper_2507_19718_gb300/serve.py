@@ -110,6 +110,19 @@ class Trainer:
         self.image = torch.zeros((3, height, width), **f32)
         self.loss = torch.zeros((levels,), **f32)
 
+    def tune(self, sc: "ResidentScene", tiles=((16, 16), (8, 8), (32, 8), (8, 32), (16, 8)), bins=(0, 64),
+             caps=(256,), ppts=(1, 2, 4)):
+        """Pick the fastest launch configuration of the training step at this
+        resolution on scene sc (its levels trained from the training view);
+        results do not depend on it.  Returns the trials."""
+        from . import autotune
+        cam = synth.orbit_camera(self.w, self.h, 30.0)
+        cands = list(autotune.candidates(tiles, bins, caps, ppts))
+        best, trials = autotune.autotune([L.params for L in sc.levels], cam, self.ws, cands=cands, reps=2,
+                                         train=True)
+        self.cfg = best.cfg()
+        return trials
+
     def frame(self, sc: ResidentScene, angle: float, frame: int, seed: int, stream=None):
         c = gsc.camera(synth.orbit_camera(self.w, self.h, angle))
         sc.static_frames += 1   # the training view stays put: Eq. 4 decays
@@ -130,7 +143,8 @@ class Server:
 
     def __init__(self, scenes, cfg: gsc.RasterCfg, hbm_budget: int | None = None, max_views: int = 32,
                  train_res=(320, 240), retrain_frames: int = 16, max_batch_gaussians: int | None = None,
-                 max_res=(1920, 1080), seed: int = 99, device: str = "cuda", keep_images: bool = False):
+                 max_res=(1920, 1080), seed: int = 99, device: str = "cuda", keep_images: bool = False,
+                 train_cfg: gsc.RasterCfg | None = None):
         self.scenes = scenes
         self.keep_images = keep_images   # completed requests keep their images (tests)
         self.cfg = cfg
@@ -145,7 +159,8 @@ class Server:
                                       max_views=self.max_views) for _ in range(2)]
         self.plain_ws = gsc.Workspace(max(L.n for sc in scenes for L in sc.levels), pairs // 4, max_res[0],
                                       max_res[1], device)
-        self.trainer = Trainer(train_res[0], train_res[1], self.K, max(sc.n_gaussians for sc in scenes), cfg,
+        self.trainer = Trainer(train_res[0], train_res[1], self.K, max(sc.n_gaussians for sc in scenes),
+                               train_cfg or cfg,
                                device=device)
         self.fixed_bytes = (sum(sc.state_bytes() for sc in scenes) + sum(ws.nbytes for ws in self.view_ws) +
                             self.plain_ws.nbytes + self.trainer.ws.nbytes)
