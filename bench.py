@@ -502,7 +502,7 @@ def run_batched_bench(args, cfg_tuned):
     torch.cuda.synchronize()
     step.ws.status()
     separate_ms = e0.elapsed_time(e1) / reps
-    plain_ws = gsc.Workspace(max(sizes), int(max(sizes) * 24), 1920, 1080)
+    plain_ws = gsc.Workspace(max(sizes), int(max(sizes) * 48), 1920, 1080)
     step.plain_step(plain_ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()

@@ -57,7 +57,8 @@ class BatchedStep:
             v["loss"] = self.losses[k]
         if max_pairs is None:
             px = sum(v["cam"].width * v["cam"].height for v in self.views) / len(self.views)
-            max_pairs = int(min((1 << 31) - 1, total * max(8.0, 96.0 * px / (1920 * 1080))))
+            # per-view bins (bin_size 0) go down to 32 px on the small views
+            max_pairs = int(min((1 << 31) - 1, total * max(24.0, 96.0 * px / (1920 * 1080))))
         self.ws = gsc.Workspace(total, max_pairs, max_w, max_h, device, max_views=len(self.views))
         self.graph = None
 
