@@ -857,7 +857,7 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
     }  // tiles
     warp_count(&stats[kStEvalRewalk], n_eval1);
     warp_count(&stats[kStEvalBack], n_eval2);
-    // the entries a pixel meets in phase 2 before its last composited one and
+    // the entries a pixel meets in phase 2 (before the one that stopped it)
     // whose falloff passes alpha_min are exactly the pairs phase 1 composited
     warp_count(&stats[kStCompRewalk], n_hit2);
     warp_count(&stats[kStHitBack], n_hit2);
