@@ -261,7 +261,6 @@ size_t layout(int64_t NG, int64_t NP, int32_t W, int32_t H, int32_t NV, gsc_work
     w->hist = (uint32_t*)take(4 * kHistWords);
     w->ranges = (uint2*)take(sizeof(uint2) * (size_t)tiles);
     w->tile_order = (uint32_t*)take(4 * (size_t)tiles);
-    w->bin_start = (uint32_t*)take(4 * (size_t)tiles);
     w->g2d = (float4*)take(sizeof(float4) * 3 * ng);
     w->red = (float*)take(sizeof(float) * red);
     w->red_floats = red;

@@ -143,7 +143,6 @@ struct gsc_workspace {
     uint32_t* hist;    // kHistWords
     uint2* ranges;     // [start, end) per bin
     uint32_t* tile_order;   // tiles ordered by expected cost (longest bin lists first)
-    uint32_t* bin_start;    // first slot of every bin's tiles in tile_order
     const uint32_t* order;  // the order of the last binning
     float4* g2d;       // 3 x NG: 2D gradients
     float* red;        // reduction scratch for losses

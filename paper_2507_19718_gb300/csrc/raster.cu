@@ -1043,7 +1043,6 @@ static int bits_for(uint32_t n) {
 // never a result.
 constexpr int kOrderThreads = 1024;
 constexpr int kOrderClasses = 256;
-constexpr int kOrderCachedBins = 4096;  // bins whose start is kept in shared memory
 
 __device__ __forceinline__ int view_of_bin(const BatchDev& b, uint32_t bin) {
     int v = 0;
@@ -1054,17 +1053,14 @@ __device__ __forceinline__ int view_of_bin(const BatchDev& b, uint32_t bin) {
 // One CTA.  With `totals` (the digit counts of a one-pass pair sort, where
 // the digit is the whole bin id) it first writes every bin's range as the
 // exclusive scan of the counts.  Then per bin: its class and tile count; the
-// tile counts are summed per class and scanned, every bin takes its start in
-// its class, and every tile goes to its bin's start plus its row-major
-// position in the bin.
+// tile counts are summed per class and scanned, and every bin takes its start
+// in its class and writes its tiles there in row-major order.
 __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_constant__ BatchDev b,
                                                               const uint32_t* __restrict__ totals,
                                                               uint2* __restrict__ ranges, RasterDev rc,
-                                                              uint32_t* __restrict__ bin_start,
                                                               uint32_t* __restrict__ order) {
     __shared__ uint32_t cls[kOrderClasses];
     __shared__ uint32_t wsum[kOrderThreads / 32];
-    __shared__ uint32_t s_start[kOrderCachedBins];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // exclusive scan of one value per thread
     auto block_scan = [&](uint32_t v) -> uint32_t {
@@ -1109,24 +1105,22 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_const
     uint32_t s = block_scan(c);
     if (threadIdx.x < kOrderClasses) cls[threadIdx.x] = s;
     __syncthreads();
-    for (uint32_t bin = threadIdx.x; bin < nb; bin += kOrderThreads) {
+    // one warp per bin: it takes the bin's start in its class and writes
+    // the bin's tiles, row-major, 32 at a time
+    for (uint32_t bin = warp; bin < nb; bin += kOrderThreads / 32) {
         uint32_t k, nt;
         bin_info(bin, k, nt);
-        const uint32_t st = atomicAdd(&cls[k], nt);
-        if (bin < (uint32_t)kOrderCachedBins) s_start[bin] = st;
-        else bin_start[bin] = st;
-    }
-    __syncthreads();
-    for (uint32_t t = threadIdx.x; t < b.total_tiles; t += kOrderThreads) {
-        const ViewDev& vw = b.v[view_of_tile(b, t)];
-        const uint32_t lt = t - vw.tile_off;
-        const int tx = (int)(lt % (uint32_t)vw.tiles_x), ty = (int)(lt / (uint32_t)vw.tiles_x);
-        const int bx = tx / vw.spt_x, by = ty / vw.spt_y;
-        const uint32_t bin = vw.bin_off + (uint32_t)(by * vw.bins_x + bx);
+        uint32_t st = 0;
+        if (lane == 0) st = atomicAdd(&cls[k], nt);
+        st = __shfl_sync(kFull, st, 0);
+        const ViewDev& vw = b.v[view_of_bin(b, bin)];
+        const uint32_t lb = bin - vw.bin_off;
+        const int bx = (int)(lb % (uint32_t)vw.bins_x), by = (int)(lb / (uint32_t)vw.bins_x);
         const int w = min(vw.spt_x, vw.tiles_x - bx * vw.spt_x);
-        const uint32_t local = (uint32_t)((ty - by * vw.spt_y) * w + (tx - bx * vw.spt_x));
-        const uint32_t st = bin < (uint32_t)kOrderCachedBins ? s_start[bin] : bin_start[bin];
-        order[st + local] = t;
+        for (uint32_t li = (uint32_t)lane; li < nt; li += 32) {
+            const int ry = (int)li / w, rx = (int)li - ry * w;
+            order[st + li] = vw.tile_off + (uint32_t)((by * vw.spt_y + ry) * vw.tiles_x + bx * vw.spt_x + rx);
+        }
     }
 }
 
@@ -1175,7 +1169,7 @@ cudaError_t bin_gaussians(const BatchDev& b, const RasterDev& rc, gsc_workspace*
             k_ranges<<<152 * 8, 256, 0, s>>>(keys, ws->counters, ws->ranges);
         }
         k_tile_order<<<1, kOrderThreads, 0, s>>>(b, one_pass ? radix_totals(ws->hist) : nullptr, ws->ranges, rc,
-                                                 ws->bin_start, ws->tile_order);
+                                                 ws->tile_order);
         ws->order = ws->tile_order;
     }
     return cudaGetLastError();

@@ -212,8 +212,8 @@ def test_batched_step_graph_replays_the_training_step(gpu):
 def test_batch_with_many_bins_matches_views_alone(gpu):
     """Six 1280x720 views with 32-pixel bins: 5,520 bins, so the pair sort
     takes two radix passes (the bin ranges come from the sorted keys) and
-    the tile order keeps the starts of the bins past the 4,096th in global
-    memory; every image is still the single-view render bit for bit."""
+    the tile order handles thousands of bins; every image is still the
+    single-view render bit for bit."""
     import torch
     scenes = [torch.from_numpy(synth.gaussians(n, 700 + k)).cuda() for k, n in enumerate([1500, 2500])]
     views = []
