@@ -76,6 +76,30 @@ class BatchedStep:
                      stream=stream)
         gsc.render_batch(self.views, gsc.BATCH_BWD, self.cfg, self.ws, stream=stream)
 
+    def tune(self, tiles=((16, 16), (8, 8), (32, 8), (8, 32), (16, 8)), ppts=(1, 2, 4), caps=(256,), bins=(0,),
+             reps: int = 2):
+        """Pick the fastest launch configuration for this batch (results do not
+        depend on it); returns [(config dict, ms)]."""
+        from . import autotune
+        trials = []
+        for tile, b, cap, q in autotune.candidates(tiles, bins, caps, ppts):
+            self.cfg = gsc.raster_cfg(tile=tile, list_capacity=cap, bin_size=b, pixels_per_thread=q)
+            self.step()
+            self.ws.status()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                self.step()
+            e1.record()
+            e1.synchronize()
+            self.ws.status()
+            trials.append((dict(tile=list(tile), bin=b, list_capacity=cap, pixels_per_thread=q),
+                           e0.elapsed_time(e1) / reps))
+        best = min(trials, key=lambda t: t[1])[0]
+        self.cfg = gsc.raster_cfg(tile=best["tile"], list_capacity=best["list_capacity"], bin_size=best["bin"],
+                                  pixels_per_thread=best["pixels_per_thread"])
+        return trials
+
     def capture(self):
         """Warm up eagerly on a side stream, then capture one step."""
         s = torch.cuda.Stream()
