@@ -38,7 +38,7 @@ LEVELS = 3
 SPP, BOUNCES = 1, 8
 ORBIT_DEG_PER_FRAME = 0.5
 # candidates of the start-up autotuner (tile shape x bin size x staging capacity)
-TUNE_TILES, TUNE_BINS, TUNE_CAPS, TUNE_PPT = ((16, 16), (32, 8), (8, 32)), (64, 128, 256), (256, 512), (1, 2, 4, 8)
+TUNE_TILES, TUNE_BINS, TUNE_CAPS, TUNE_PPT = ((16, 16), (32, 8), (8, 32)), (64, 128, 256), (96, 128, 256), (1, 2, 4, 8)
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # FP32 FMA lanes: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (maximum SM clock)
@@ -263,8 +263,8 @@ def run_ours(args, world, rank, local):
     # and the backward batch (results do not depend on them)
     tuned_top = None
     if args.no_autotune:  # the configurations the autotuner picks on a GB300
-        best_f = autotune.Trial((16, 16), 128, 256, 2, float("nan"))
-        best_b = autotune.Trial((16, 16), 128, 256, 4, float("nan"))
+        best_f = autotune.Trial((16, 16), 128, 128, 4, float("nan"))
+        best_b = autotune.Trial((16, 16), 128, 96, 4, float("nan"))
     else:
         cands = list(autotune.candidates(TUNE_TILES, TUNE_BINS, TUNE_CAPS, TUNE_PPT))
         lv = [L.params for L in loop.levels]

@@ -17,7 +17,7 @@ from . import gsc
 
 TILES = ((16, 16), (8, 8), (32, 8), (16, 8), (8, 16))
 BINS = (32, 64, 128)
-CAPS = (256, 512, 1024)
+CAPS = (96, 128, 256, 512)
 PPTS = (1, 2, 4, 8)
 # (tile, pixels per thread) pairs the library is compiled for
 COMPILED = {1: {(16, 16), (8, 8), (32, 8), (16, 8), (8, 16), (8, 32), (32, 4)},

@@ -76,7 +76,7 @@ class BatchedStep:
                      stream=stream)
         gsc.render_batch(self.views, gsc.BATCH_BWD, self.cfg, self.ws, stream=stream)
 
-    def tune(self, tiles=((16, 16), (8, 8), (32, 8), (8, 32), (16, 8)), ppts=(1, 2, 4), caps=(256,), bins=(0,),
+    def tune(self, tiles=((16, 16), (8, 8), (32, 8), (8, 32), (16, 8)), ppts=(1, 2, 4), caps=(128, 256), bins=(0,),
              reps: int = 2):
         """Pick the fastest launch configuration for this batch (results do not
         depend on it); returns [(config dict, ms)]."""

@@ -111,7 +111,7 @@ class Trainer:
         self.loss = torch.zeros((levels,), **f32)
 
     def tune(self, sc: "ResidentScene", tiles=((16, 16), (8, 8), (32, 8), (8, 32), (16, 8)), bins=(0, 64),
-             caps=(256,), ppts=(1, 2, 4)):
+             caps=(128, 256), ppts=(1, 2, 4)):
         """Pick the fastest launch configuration of the training step at this
         resolution on scene sc (its levels trained from the training view);
         results do not depend on it.  Returns the trials."""
