@@ -263,12 +263,15 @@ __device__ float sphere_nee(const TraceDev& v, Philox& r, const float* x, const 
     return T * ((1.0f - cmax) * 0.5f);
 }
 
-// 16 CTAs of 128 threads per SM, i.e. every warp slot of the SM, at 32
-// registers: the tracer waits mostly on dependent volume loads, and the extra
-// warps hide that better than registers would (measured 1.69 -> 1.39 ms per
-// 1080p frame against 96 registers and 5 CTAs, despite the spills)
-__global__ void __launch_bounds__(128, 16) k_trace(TraceDev v, CamDev cam, const float* __restrict__ cache,
-                                               float* __restrict__ targets, float* __restrict__ image) {
+// Two register budgets for the same code.  MINB = 16 (every warp slot of the
+// SM, 32 registers, with spills): on a frame of many waves the tracer waits
+// mostly on dependent volume loads, and the extra warps hide that better than
+// registers (1080p: 1.40 ms against 1.54 ms at MINB = 5).  MINB = 5 (no
+// spills): on a frame of a few waves or less the warps are there anyway and
+// the spills only cost (256^2 to 640x480: 17-19% faster than MINB = 16).
+template <int MINB>
+__global__ void __launch_bounds__(128, MINB) k_trace(TraceDev v, CamDev cam, const float* __restrict__ cache,
+                                                     float* __restrict__ targets, float* __restrict__ image) {
     int i = blockIdx.x * 16 + (threadIdx.x & 15);
     int j = blockIdx.y * 8 + (threadIdx.x >> 4);
     if (i >= cam.W || j >= cam.H) return;
@@ -442,6 +445,18 @@ cudaError_t launch_init_sample(const gsc_scene* sc, uint32_t n, uint64_t seed, i
     return cudaGetLastError();
 }
 
+// SMs of the current device (queried once)
+static int sm_count() {
+    static int cached = 0;
+    if (cached <= 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cached = sms > 0 ? sms : 1;
+    }
+    return cached;
+}
+
 cudaError_t launch_trace(const gsc_scene* sc, const CamDev& cam, const gsc_trace_params& p, const float* cache,
                          float* targets, float* image, cudaStream_t s) {
     TraceDev v = trace_dev(sc);
@@ -452,7 +467,11 @@ cudaError_t launch_trace(const gsc_scene* sc, const CamDev& cam, const gsc_trace
     v.C = p.C; v.eps = p.eps;
     dim3 grid((cam.W + 15) / 16, (cam.H + 7) / 8);
     PhaseScope ph(kPhTrace, s, 1);
-    k_trace<<<grid, 128, 0, s>>>(v, cam, cache, targets, image);
+    // two full waves at 16 CTAs per SM: below that, the spill-free budget
+    if ((size_t)grid.x * grid.y >= (size_t)2 * 16 * sm_count())
+        k_trace<16><<<grid, 128, 0, s>>>(v, cam, cache, targets, image);
+    else
+        k_trace<5><<<grid, 128, 0, s>>>(v, cam, cache, targets, image);
     return cudaGetLastError();
 }
 

@@ -45,7 +45,9 @@ def test_trace_bit_exact_with_cache_and_termination(gpu, orc):
 
 def test_trace_bit_exact_frame_scene_1080p_windows(gpu, orc):
     """The 1080p frame workload (256^3 blobs + fBm, 8-point TF, directional +
-    environment light, 1 spp, 8 bounces, 3 levels) on sampled windows."""
+    environment light, 1 spp, 8 bounces, 3 levels) on sampled windows.  A frame
+    of this size runs the many-wave register budget of the tracer (16 CTAs per
+    SM); the small frames of the other tests run the spill-free one."""
     scene = synth.scene_frame()
     cam = synth.orbit_camera(1920, 1080, 45.0)
     tg, img = _run(gpu, scene, cam, spp=1, max_bounces=8, levels=3, seed=5, frame=11)
