@@ -277,6 +277,22 @@ def run_ours(args, world, rank, local):
     cfg = workload_config(best_f, best_b)
     if tuned_top:
         cfg["autotune_fastest"] = tuned_top
+    # the fastest training configuration drifts as the cache trains (the
+    # pixels of a tile stop at more different depths, and fewer pixels per
+    # thread win): the frame loop keeps choosing between the tuned one and
+    # the fastest ones at the next two lower pixels-per-thread values, timing
+    # every frame's training step
+    sel = adapt = None
+    if not args.no_adapt:
+        if args.no_autotune:
+            adapt = [best_b, autotune.Trial((16, 16), 128, 128, 2, float("nan")),
+                     autotune.Trial((16, 16), 128, 256, 1, float("nan"))]
+        else:
+            lower = sorted({t.ppt for t in trials_b if t.ppt < best_b.ppt}, reverse=True)[:2]
+            if not lower:
+                lower = sorted({t.ppt for t in trials_b if t.ppt > best_b.ppt})[:1]
+            adapt = [best_b] + [min((t for t in trials_b if t.ppt == q), key=lambda t: t.ms) for q in lower]
+        sel = loop.adapt_train_launch([t.cfg() for t in adapt])
     stream = torch.cuda.current_stream()
 
     # warm-up (also sizes nothing: the pair capacity is fixed)
@@ -319,7 +335,8 @@ def run_ours(args, world, rank, local):
     # ---- end-to-end through the public API with host I/O: per frame the
     # camera pose goes in (a gsc_camera struct, read by the calls), and the
     # path-traced display image and the level losses come back to pinned host
-    # memory.
+    # memory (FrameLoop.frame_to_host: the image copy runs beside the
+    # training step); the host waits for every frame's results.
     host_img = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, pin_memory=True)
     host_loss = torch.empty((LEVELS,), dtype=torch.float32, pin_memory=True)
     loop.restore(snap)
@@ -331,9 +348,7 @@ def run_ours(args, world, rank, local):
     for f in range(args.warmup, args.warmup + K):
         pose = bytes(cams[f])                     # the caller's pose, host memory
         c = gsc.Camera.from_buffer_copy(pose)
-        loop.frame(c, f)
-        host_img.copy_(loop.image, non_blocking=True)
-        host_loss.copy_(loop.losses, non_blocking=True)
+        loop.frame_to_host(c, f, host_img, host_loss, stream)
         stream.synchronize()
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t_host0) * 1e3
@@ -411,6 +426,9 @@ def run_ours(args, world, rank, local):
     counts = {k: (v if k in ("pairs_last", "pairs_max", "pair_sort_passes") else round(v / K))
               for k, v in counters.items()}
 
+    if sel is not None:
+        cfg["train_launch_adaptive"] = {"candidates": [_launch_cfg(t) for t in adapt], "steps_per_candidate": sel.runs,
+                                        "switches": sel.switches, "choice_at_end": sel.current}
     result = {
         "metric": METRIC, "value": round(tr_max / (K * world), 3), "unit": "ms/frame", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": round(total_max / K, 3), "higher_is_better": False,
@@ -661,6 +679,8 @@ def main():
     ap.add_argument("--no-init", action="store_true")
     ap.add_argument("--no-coupled", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--no-adapt", action="store_true",
+                    help="keep the training step's launch configuration fixed instead of choosing it frame by frame")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the launch autotuner (for profiler runs with few launches)")
     args = ap.parse_args()

@@ -106,3 +106,75 @@ def autotune(levels, cam, ws: gsc.Workspace, backward=True, cands=None, reps=2, 
             print(f"tile {tile[0]}x{tile[1]} bin {b} cap {cap} ppt {q}: {ms:.3f} ms", flush=True)
     best = min(trials, key=lambda t: t.ms)
     return best, trials
+
+
+class OnlineSelector:
+    """Launch configuration of a step that repeats while its best choice
+    drifts with the data.  In the training step of a cache the pixels of a
+    tile stop at more and more different depths as the cache trains, and
+    fewer pixels per thread start to win (at 1080p with 1M Gaussians: 4 per
+    thread fastest on the first frames, 2 per thread 27% faster than 4 after
+    25 frames of an orbiting camera).
+
+    Every step runs exactly once with one configuration, so nothing is added
+    to the work: the current choice runs on most steps and every
+    ``explore_every``-th step runs the next other candidate in turn.  The
+    current choice's time is a running mean (weight ``alpha`` on the newest
+    step), another candidate's time is its newest measurement; the selector
+    moves to a candidate that is faster by more than ``margin``.  When the
+    current choice's time rises more than ``drift`` above its lowest since it
+    was chosen (the data changed), the next steps explore every other
+    candidate at once.  Times
+    come back through ``report`` whenever they are known (a step's device
+    time is read without waiting for it)."""
+
+    def __init__(self, n: int, explore_every: int = 4, alpha: float = 0.25, margin: float = 0.03,
+                 drift: float = 0.05):
+        if n < 1 or explore_every < 2:
+            raise ValueError("need at least one candidate and explore_every >= 2")
+        self.n, self.explore_every, self.alpha, self.margin, self.drift = n, explore_every, alpha, margin, drift
+        self.current = 0
+        self.est = [None] * n
+        self.runs = [0] * n
+        self.switches = 0
+        self._step = 0
+        self._next = 0
+        self._low = None          # lowest time of the current choice since it was chosen
+        self._burst = 0           # steps left that explore at once
+
+    def choose(self) -> int:
+        """Index of the candidate for the next step."""
+        self._step += 1
+        if self.n > 1 and (self._burst > 0 or self._step % self.explore_every == 0):
+            self._burst = max(0, self._burst - 1)
+            self._step = 0            # the next regular exploration counts from here
+            for _ in range(self.n):
+                self._next = (self._next + 1) % self.n
+                if self._next != self.current:
+                    break
+            i = self._next
+        else:
+            i = self.current
+        self.runs[i] += 1
+        return i
+
+    def report(self, i: int, ms: float):
+        """Device time of a step that ran candidate ``i``."""
+        if i == self.current and self.est[i] is not None:
+            self.est[i] += self.alpha * (ms - self.est[i])
+        else:
+            self.est[i] = ms
+        cur = self.est[self.current]
+        if cur is None:
+            return
+        if i == self.current:
+            if self._low is None or cur < self._low:
+                self._low = cur
+            elif cur > self._low * (1.0 + self.drift):
+                self._burst = self.n - 1
+                self._low = cur
+        best = min((j for j in range(self.n) if self.est[j] is not None), key=lambda j: self.est[j])
+        if best != self.current and self.est[best] < cur * (1.0 - self.margin):
+            self.current = best
+            self.switches += 1
+            self._low = self.est[best]

@@ -8,6 +8,7 @@ calls and owns the device tensors.
 """
 from __future__ import annotations
 
+import copy
 import ctypes as C
 
 import numpy as np
@@ -98,19 +99,27 @@ class FrameLoop:
         self.adam_step = 0
         self.static_frames = 0
         self._last_pose = None
+        self._copy_stream = None
+        self._adapt = None
 
     def snapshot(self):
-        """Copy of the training state (parameters, moments, step, schedule)."""
+        """Copy of the training state (parameters, moments, step, schedule,
+        and the state of the adaptive launch choice)."""
         P, _, M, V = self.store
-        return (P.clone(), M.clone(), V.clone()), self.adam_step, self.static_frames, self._last_pose
+        sel = copy.deepcopy(self._adapt["sel"]) if self._adapt is not None else None
+        return (P.clone(), M.clone(), V.clone()), self.adam_step, self.static_frames, self._last_pose, sel
 
     def restore(self, snap):
-        (p, m, v), self.adam_step, self.static_frames, self._last_pose = snap
+        (p, m, v), self.adam_step, self.static_frames, self._last_pose, sel = snap
         P, G, M, V = self.store
         P.copy_(p)
         M.copy_(m)
         V.copy_(v)
         G.zero_()
+        if self._adapt is not None and sel is not None:
+            self._adapt["pending"] = []          # times of steps from before the snapshot's state
+            self._adapt["sel"] = copy.deepcopy(sel)
+            self.cfg_bwd = self._adapt["cfgs"][sel.current]
 
     def _schedule(self, c: gsc.Camera) -> float:
         """Eq. 4: frames the viewport has been unchanged (pose compared bit for bit)."""
@@ -150,6 +159,33 @@ class FrameLoop:
             gsc.cache_backward(L.params, c, cfg_b, self.ws, self.dL[k], L.grads, stream=stream)
             gsc.cache_step(L.params, L.grads, L.m, L.v, adam, stream=stream)
 
+    def adapt_train_launch(self, cfgs, explore_every: int = 6):
+        """Choose the training step's launch configuration among ``cfgs``
+        while the cache trains (``autotune.OnlineSelector``; the first is the
+        starting choice): every frame's training step is timed on the device
+        and every ``explore_every``-th frame runs another candidate.  The
+        configuration changes no result beyond the order of the FP32 sums."""
+        from .autotune import OnlineSelector
+        cfgs = list(cfgs)
+        self._adapt = dict(cfgs=cfgs, sel=OnlineSelector(len(cfgs), explore_every), pending=[],
+                           pool=[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                                 for _ in range(3)], slot=0)
+        self.cfg_bwd = cfgs[0]
+        return self._adapt["sel"]
+
+    def _adapt_collect(self, lag: int):
+        """Report the timed training steps that have finished; wait for the
+        oldest ones until at most ``lag`` remain in flight (the frames queued
+        behind them keep the device busy meanwhile)."""
+        a = self._adapt
+        while len(a["pending"]) > lag:
+            i, e0, e1 = a["pending"].pop(0)
+            e1.synchronize()
+            a["sel"].report(i, e0.elapsed_time(e1))
+        while a["pending"] and a["pending"][0][2].query():
+            i, e0, e1 = a["pending"].pop(0)
+            a["sel"].report(i, e0.elapsed_time(e1))
+
     def train_step(self, c: gsc.Camera, lr_scale: float, stream=None):
         """Render + HDR loss + backward of all levels in one launch, the
         per-Gaussian gradients and the AdamW step in one more (gsc_train_step)."""
@@ -158,7 +194,23 @@ class FrameLoop:
         # no gradient is accumulated between frames, so none is passed
         views = [dict(params=L.params, cam=c, target=self.targets[k], image=self.renders[k], loss=self.losses[k],
                       m=L.m, v=L.v) for k, L in enumerate(self.levels)]
-        gsc.train_step(views, adam, self.cfg_bwd or self.cfg, self.ws, gsc.LOSS_HDR, stream=stream)
+        a = self._adapt
+        if a is None:
+            gsc.train_step(views, adam, self.cfg_bwd or self.cfg, self.ws, gsc.LOSS_HDR, stream=stream)
+            return
+        # the choice for this frame sees the times of the frames before the
+        # previous one; the previous frame's work keeps the device busy while
+        # the host waits for them
+        self._adapt_collect(lag=1)
+        i = a["sel"].choose()
+        self.cfg_bwd = a["cfgs"][a["sel"].current]
+        e0, e1 = a["pool"][a["slot"]]
+        a["slot"] = (a["slot"] + 1) % len(a["pool"])
+        s = torch.cuda.current_stream() if stream is None else stream
+        e0.record(s)
+        gsc.train_step(views, adam, a["cfgs"][i], self.ws, gsc.LOSS_HDR, stream=stream)
+        e1.record(s)
+        a["pending"].append((i, e0, e1))
 
     def frame(self, cam, frame: int, stream=None):
         """One frame: render the cache (its images feed the tracer when C > 0),
@@ -173,3 +225,37 @@ class FrameLoop:
         self.trace(c, frame, stream)
         self.train_levels(c, lr_scale, stream)
         return self.losses
+
+    def frame_to_host(self, cam, frame: int, host_image: torch.Tensor, host_losses: torch.Tensor, stream=None):
+        """``frame`` with its results read back to host memory (pinned, for the
+        copies to be asynchronous): the display image is final once the tracer
+        has run, so it is copied on a side stream while the levels train; the
+        level losses follow the step.  Both host tensors are complete once
+        ``stream`` (default: the current stream) is synchronised, and the next
+        frame's tracer, which rewrites the image, runs after the copy."""
+        s = torch.cuda.current_stream() if stream is None else stream
+        if not (self.fused_train and self.C_term <= 0):
+            # the image depends on this frame's cache render: nothing to overlap
+            self.frame(cam, frame, s)
+            with torch.cuda.stream(s):
+                host_image.copy_(self.image, non_blocking=True)
+                host_losses.copy_(self.losses, non_blocking=True)
+            return host_losses
+        if self._copy_stream is None:
+            self._copy_stream = torch.cuda.Stream(device=self.image.device)
+        c = cam if isinstance(cam, gsc.Camera) else gsc.camera(cam)
+        lr_scale = self._schedule(c)
+        self.trace(c, frame, s)
+        traced = torch.cuda.Event()
+        traced.record(s)
+        cs = self._copy_stream
+        cs.wait_event(traced)
+        with torch.cuda.stream(cs):
+            host_image.copy_(self.image, non_blocking=True)
+        read = torch.cuda.Event()
+        read.record(cs)
+        self.train_step(c, lr_scale, s)
+        with torch.cuda.stream(s):
+            host_losses.copy_(self.losses, non_blocking=True)
+        s.wait_event(read)
+        return host_losses

@@ -1,0 +1,70 @@
+"""Host logic of the adaptive launch choice of the frame loop's training step
+(autotune.OnlineSelector), driven by synthetic step times; no GPU."""
+import pytest
+
+from paper_2507_19718_gb300.autotune import OnlineSelector
+
+
+def _run(sel, cost, frames, lag=0):
+    """Choose, 'run' and report like the frame loop: the time of a step comes
+    back ``lag`` steps later."""
+    seq, pending = [], []
+    for f in range(frames):
+        while len(pending) > lag:
+            sel.report(*pending.pop(0))
+        i = sel.choose()
+        seq.append(i)
+        pending.append((i, cost(i, f)))
+    return seq
+
+
+def test_keeps_the_fastest_and_explores_the_others_in_turn():
+    sel = OnlineSelector(3, explore_every=4)
+    seq = _run(sel, lambda i, f: (2.9, 3.3, 3.5)[i], 24)
+    assert seq == [0, 0, 0, 1, 0, 0, 0, 2] * 3
+    assert sel.current == 0 and sel.switches == 0
+    assert sel.runs == [18, 3, 3]
+
+
+def test_follows_a_drift_of_the_fastest_candidate():
+    # the first candidate is fastest on the first 12 steps, the second after
+    sel = OnlineSelector(3, explore_every=4)
+    cost = lambda i, f: (2.9, 3.3, 3.5)[i] if f < 12 else (3.4, 2.5, 2.9)[i]
+    seq = _run(sel, cost, 48, lag=2)
+    assert sel.current == 1
+    # after the drift the second candidate carries most steps
+    assert seq[32:].count(1) >= 12
+
+
+def test_a_drift_of_the_current_choice_explores_at_once():
+    # the current choice slows down by 30% at step 10, right after the
+    # regular exploration: every other candidate runs within the next steps
+    # instead of waiting for the next regular round
+    sel = OnlineSelector(3, explore_every=8)
+    cost = lambda i, f: (2.5, 3.0, 3.2)[i] if f < 10 else (3.25, 2.4, 2.7)[i]
+    seq = _run(sel, cost, 20, lag=2)
+    assert seq[:8] == [0] * 7 + [1]
+    assert 1 in seq[10:15] and 2 in seq[10:15]
+    assert sel.current == 1 and seq[-3:] == [1, 1, 1]
+    # a steady choice never triggers an exploration between regular rounds
+    sel = OnlineSelector(3, explore_every=8)
+    assert _run(sel, lambda i, f: (2.5, 3.0, 3.2)[i] * (1 + 0.01 * (f % 3)), 32, lag=2) == \
+        ([0] * 7 + [1] + [0] * 7 + [2]) * 2
+
+
+def test_margin_keeps_the_choice_between_near_ties():
+    sel = OnlineSelector(2, explore_every=2, margin=0.03)
+    _run(sel, lambda i, f: (3.00, 2.95)[i], 40)
+    assert sel.current == 0 and sel.switches == 0
+    sel = OnlineSelector(2, explore_every=2, margin=0.03)
+    _run(sel, lambda i, f: (3.00, 2.80)[i], 40)
+    assert sel.current == 1 and sel.switches == 1
+
+
+def test_single_candidate_and_arguments():
+    sel = OnlineSelector(1)
+    assert _run(sel, lambda i, f: 1.0, 10) == [0] * 10
+    with pytest.raises(ValueError):
+        OnlineSelector(0)
+    with pytest.raises(ValueError):
+        OnlineSelector(2, explore_every=1)
