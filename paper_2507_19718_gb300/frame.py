@@ -164,7 +164,9 @@ class FrameLoop:
         while the cache trains (``autotune.OnlineSelector``; the first is the
         starting choice): every frame's training step is timed on the device
         and every ``explore_every``-th frame runs another candidate.  The
-        configuration changes no result beyond the order of the FP32 sums."""
+        configuration changes no result beyond the order of the FP32 sums.
+        It applies to the one-launch training step (C <= 0); the separate
+        launches of a cache-reading frame keep ``cfg_bwd``."""
         from .autotune import OnlineSelector
         cfgs = list(cfgs)
         self._adapt = dict(cfgs=cfgs, sel=OnlineSelector(len(cfgs), explore_every), pending=[],
