@@ -288,10 +288,7 @@ def run_ours(args, world, rank, local):
             adapt = [best_b, autotune.Trial((16, 16), 128, 128, 2, float("nan")),
                      autotune.Trial((16, 16), 128, 256, 1, float("nan"))]
         else:
-            lower = sorted({t.ppt for t in trials_b if t.ppt < best_b.ppt}, reverse=True)[:2]
-            if not lower:
-                lower = sorted({t.ppt for t in trials_b if t.ppt > best_b.ppt})[:1]
-            adapt = [best_b] + [min((t for t in trials_b if t.ppt == q), key=lambda t: t.ms) for q in lower]
+            adapt = autotune.drift_candidates(best_b, trials_b)
         sel = loop.adapt_train_launch([t.cfg() for t in adapt])
     stream = torch.cuda.current_stream()
 

@@ -108,6 +108,17 @@ def autotune(levels, cam, ws: gsc.Workspace, backward=True, cands=None, reps=2, 
     return best, trials
 
 
+
+def drift_candidates(best: Trial, trials, k: int = 2):
+    """Candidates of an online choice for a training step tuned as ``best``:
+    ``best`` first, then the fastest trial at each of the ``k`` next lower
+    pixels-per-thread values (the direction the choice drifts as a cache
+    trains); with no lower value, the fastest at the next higher one."""
+    lower = sorted({t.ppt for t in trials if t.ppt < best.ppt}, reverse=True)[:k]
+    if not lower:
+        lower = sorted({t.ppt for t in trials if t.ppt > best.ppt})[:1]
+    return [best] + [min((t for t in trials if t.ppt == q), key=lambda t: t.ms) for q in lower]
+
 class OnlineSelector:
     """Launch configuration of a step that repeats while its best choice
     drifts with the data.  In the training step of a cache the pixels of a

@@ -2,7 +2,7 @@
 (autotune.OnlineSelector), driven by synthetic step times; no GPU."""
 import pytest
 
-from paper_2507_19718_gb300.autotune import OnlineSelector
+from paper_2507_19718_gb300.autotune import OnlineSelector, Trial, drift_candidates
 
 
 def _run(sel, cost, frames, lag=0):
@@ -68,3 +68,16 @@ def test_single_candidate_and_arguments():
         OnlineSelector(0)
     with pytest.raises(ValueError):
         OnlineSelector(2, explore_every=1)
+
+
+def test_drift_candidates_take_the_next_lower_pixels_per_thread():
+    T = lambda tile, cap, q, ms: Trial(tile, 128, cap, q, ms)
+    trials = [T((16, 16), 96, 4, 2.88), T((16, 16), 96, 8, 3.21), T((16, 16), 256, 2, 3.30),
+              T((8, 32), 128, 2, 3.25), T((16, 16), 256, 1, 3.60), T((8, 8), 512, 1, 3.90)]
+    best = trials[0]
+    got = drift_candidates(best, trials)
+    assert got == [best, trials[3], trials[4]]
+    # tuned at one pixel per thread: the only alternative is the next higher
+    got = drift_candidates(trials[4], trials)
+    assert got == [trials[4], trials[3]]
+    assert drift_candidates(best, [best]) == [best]
