@@ -20,8 +20,12 @@ Passages followed (Bauer et al., "GSCache"):
   cache_bytes        Table 3
   loss_l1ssim        not in the paper (the 1M-Gaussian gradient workload)
 
-Parity unpinned: the cache-coupled tracer branch (Algorithm 1 with C > 0 and
-cache images) beyond the C -> infinity identity.
+The cache-coupled tracer branch (Algorithm 1 with C > 0 and cache images) is
+pinned by the C -> infinity identity and by three closed forms in a
+homogeneous medium with constant cache images: C -> 0+ (every collision ends
+in the first cache level), one survival with weight 1/Tr followed by an escape
+into the cache from a dense half-space (escape probability (1 - ln 2) / 2),
+and no roulette from Tr = 0.9 up.
 """
 from __future__ import annotations
 

@@ -36,9 +36,11 @@
  *   orc_adamw           Sec. 3.6 "Regularization" (AdamW, Loshchilov & Hutter)
  *   orc_lr_scale        Eq. 4
  *
- * Parity unpinned: the cache-coupled branch of the tracer (Algorithm 1 with
- * C > 0 and cache images) has no closed form; only the C -> infinity identity
- * pins it.
+ * The cache-coupled branch of the tracer (Algorithm 1 with C > 0 and cache
+ * images) is pinned by the C -> infinity identity and by closed forms in a
+ * homogeneous medium with constant cache images: C -> 0+, one roulette
+ * survival then an escape from a dense half-space, and no roulette from
+ * Tr = 0.9 up.
  */
 #include <math.h>
 #include <stdint.h>

@@ -8,7 +8,9 @@ directional light.  Invariants: the white furnace (albedo 1, environment
 only, unbounded bounces => every pixel's expectation is L_env); delta and
 ratio tracking agree with exp(-integral sigma) by quadrature; the target
 buffers and the primary-escape term sum to the image; Algorithm 1 with
-C -> infinity is the identity.
+C -> infinity is the identity.  Algorithm 1's termination into the cache:
+closed forms at C -> 0+, after one roulette survival (the escape probability
+of a dense half-space), and without roulette from Tr = 0.9 up.
 """
 import math
 
@@ -148,6 +150,75 @@ def test_algorithm1_with_infinite_C_is_identity(orc):
     c = orc.trace(sc, cam, spp=2, max_bounces=4, levels=4, seed=11, C=0.5, cache=cache, precision=32)
     assert not np.array_equal(a[1], c[1])
     assert np.all(np.isfinite(c[0])) and np.all(np.isfinite(c[1]))
+
+
+def _const_cache(levels, h, w, per_level):
+    """Cache images: level k holds the constant colour per_level[k]."""
+    c = np.zeros((levels, 3, h, w), np.float32)
+    for k, rgb in enumerate(per_level):
+        c[k] = np.asarray(rgb, np.float32)[:, None, None]
+    return c
+
+
+# escape probability of a path scattered isotropically at the exponentially
+# distributed depth of a beam entering a half-space at normal incidence:
+# 1/2 int_0^1 mu / (1 + mu) dmu
+P_ESC_HALF_SPACE = 0.5 * (1.0 - math.log(2.0))
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_algorithm1_with_vanishing_C_terminates_at_the_first_vertex(orc, precision):
+    """C -> 0+: Tr = 0 at the first vertex, so every path that collides ends
+    there in the cache's level 1 (index 0, not divided: no earlier survival)
+    and every primary escape shows the environment:
+    E[pixel] = e^{-sigma} L_env + (1 - e^{-sigma}) cache_1."""
+    sigma, env = 1.0, 0.7
+    sc = _homog_scene(sigma, albedo=0.8, env=(env, env, env))
+    cam = _far_cam()
+    c1, c2 = (0.3, 0.5, 0.9), (5.0, 6.0, 7.0)
+    cache = _const_cache(2, 4, 4, [c1, c2])
+    _, img = orc.trace(sc, cam, spp=4096, max_bounces=4, levels=2, seed=21, C=1e-30, cache=cache,
+                       precision=precision)
+    pe = math.exp(-sigma)
+    for ch in range(3):
+        _ratio_check(img[ch], np.full((4, 4), pe * env + (1 - pe) * c1[ch]))
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_algorithm1_survival_weight_and_escape_into_the_cache(orc, precision):
+    """A dense half-space (sigma = 200 in the unit box), no lights, B = 2, and
+    Tr = C lum(albedo) = 0.3 at the first vertex: a path ends there in the
+    cache with probability 1 - Tr (value cache_1); it survives with
+    probability Tr, beta = Tr, and then either escapes with no radiance
+    (value cache_1 / beta) or collides at the bounce limit (value 0):
+    E[pixel] = cache_1 (1 - Tr + P_esc), P_esc = (1 - ln 2) / 2.  The TF colour
+    is not grey, so Tr also pins the Rec. 709 luminance of the throughput."""
+    rgb = (1.0, 0.5, 0.25)
+    sc = _homog_scene(200.0, rgb=rgb, albedo=0.8)
+    cam = _far_cam()
+    c1, c2 = (0.3, 0.5, 0.9), (5.0, 6.0, 7.0)
+    cache = _const_cache(2, 4, 4, [c1, c2])
+    Tr = 0.3
+    lum = 0.8 * (0.2126 * rgb[0] + 0.7152 * rgb[1] + 0.0722 * rgb[2])
+    _, img = orc.trace(sc, cam, spp=4096, max_bounces=2, levels=2, seed=22, C=Tr / lum, cache=cache,
+                       precision=precision)
+    for ch in range(3):
+        _ratio_check(img[ch], np.full((4, 4), c1[ch] * (1 - Tr + P_ESC_HALF_SPACE)))
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_algorithm1_no_roulette_from_tr_09(orc, precision):
+    """As above with Tr = 0.95 >= 0.9: no roulette at the first vertex, so
+    only the escaped paths end in the cache, undivided:
+    E[pixel] = cache_1 P_esc."""
+    sc = _homog_scene(200.0, albedo=0.8)
+    cam = _far_cam()
+    c1, c2 = (0.3, 0.5, 0.9), (5.0, 6.0, 7.0)
+    cache = _const_cache(2, 4, 4, [c1, c2])
+    _, img = orc.trace(sc, cam, spp=4096, max_bounces=2, levels=2, seed=23, C=0.95 / 0.8, cache=cache,
+                       precision=precision)
+    for ch in range(3):
+        _ratio_check(img[ch], np.full((4, 4), c1[ch] * P_ESC_HALF_SPACE))
 
 
 def test_fp32_mirror_tracks_fp64(orc):
