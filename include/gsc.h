@@ -365,6 +365,9 @@ gsc_status gsc_train_batch(const gsc_train_view* views, int32_t n_views, int32_t
  * 3 x 1920 x 1080 fits); larger crops return GSC_ERR_CAPACITY.  The first
  * call on each device looks up the array's device address (with that device
  * current), so make that first call before capturing a stream into a graph.
+ * That address is kept for the life of the process: a cudaDeviceReset (or
+ * anything else that replaces the device's primary context) after the first
+ * call is not supported, since later calls would write through the old address.
  * Every call uses the same array: calls that can run at the same time on the
  * GPU (different streams without ordering) race and give wrong losses.
  * Nothing in the array needs clearing between calls.  Allocates nothing. */

@@ -62,14 +62,18 @@ class BatchedStep:
         self.ws = gsc.Workspace(total, max_pairs, max_w, max_h, device, max_views=len(self.views))
         self.graph = None
 
+    def _zero_grads(self, stream):
+        # the clears run on the stream the batch runs on, so they are ordered before its atomics
+        with torch.cuda.stream(stream if stream is not None else torch.cuda.current_stream()):
+            for g in self.grads:
+                g.zero_()
+
     def step(self, stream=None):
-        for g in self.grads:
-            g.zero_()
+        self._zero_grads(stream)
         gsc.train_batch(self.views, self.cfg, self.ws, gsc.LOSS_HDR, stream=stream)
 
     def step_separate(self, stream=None):
-        for g in self.grads:
-            g.zero_()
+        self._zero_grads(stream)
         gsc.render_batch(self.views, gsc.BATCH_FWD, self.cfg, self.ws, stream=stream)
         for v in self.views:
             gsc.loss(gsc.LOSS_HDR, v["image"], v["target"], self.ws, dL_dpred=v["dL_dimage"], loss_out=v["loss"],

@@ -719,7 +719,8 @@ gsc_status gsc_loss(int32_t kind, const float* pred, const float* target, int32_
     int x0 = 0, y0 = 0, w = W, h = H;
     if (crop) {
         x0 = crop[0]; y0 = crop[1]; w = crop[2]; h = crop[3];
-        if (x0 < 0 || y0 < 0 || w < 1 || h < 1 || x0 + w > W || y0 + h > H)
+        // 64-bit sums: a crop such as (INT_MAX, 0, 1, H) must not wrap around into range
+        if (x0 < 0 || y0 < 0 || w < 1 || h < 1 || (int64_t)x0 + w > W || (int64_t)y0 + h > H)
             return fail(GSC_ERR_INVALID_ARG, "crop outside the image");
     }
     if (kind == GSC_LOSS_L1_SSIM && (size_t)65536 + 3 * (size_t)C * w * h > ws->red_floats)

@@ -198,8 +198,10 @@ cudaError_t launch_loss(int kind, const float* pred, const float* target, int C,
                         int w, int h, float* dL_dpred, float* loss_out, float* red, size_t red_floats,
                         cudaStream_t s) {
     size_t n = (size_t)C * w * h;
-    if (dL_dpred && (x0 != 0 || y0 != 0 || w != W || h != H))
-        cudaMemsetAsync(dL_dpred, 0, sizeof(float) * (size_t)C * H * W, s);
+    if (dL_dpred && (x0 != 0 || y0 != 0 || w != W || h != H)) {
+        cudaError_t e = cudaMemsetAsync(dL_dpred, 0, sizeof(float) * (size_t)C * H * W, s);
+        if (e != cudaSuccess) return e;
+    }
     if (kind == GSC_LOSS_HDR || kind == GSC_LOSS_HDR_FULLGRAD) {
         int blocks = (int)((n + kRedThreads - 1) / kRedThreads);
         if (blocks > kRedBlocks) blocks = kRedBlocks;
@@ -269,7 +271,7 @@ extern "C" gsc_status gsc_loss_noalloc(int32_t kind, const float* pred, const fl
     int x0 = 0, y0 = 0, w = W, h = H;
     if (crop) {
         x0 = crop[0]; y0 = crop[1]; w = crop[2]; h = crop[3];
-        if (x0 < 0 || y0 < 0 || w < 1 || h < 1 || x0 + w > W || y0 + h > H)
+        if (x0 < 0 || y0 < 0 || w < 1 || h < 1 || (int64_t)x0 + w > W || (int64_t)y0 + h > H)
             return set_error(GSC_ERR_INVALID_ARG, "gsc_loss_noalloc: crop outside the image");
     }
     size_t n = (size_t)C * w * h;

@@ -127,3 +127,13 @@ def test_host_side_validation(L):
     # loss: kind not available / crop outside
     assert L.gsc_loss(7, C.c_void_p(256), C.c_void_p(256), 3, 8, 8, None, None, C.c_void_p(256), C.c_void_p(256),
                       None) == gsc.GSC_ERR_INVALID_ARG
+    # a crop whose end overflows 32-bit int is rejected before any launch, with and without a workspace
+    big = (C.c_int32 * 4)(2 ** 31 - 1, 0, 1, 8)
+    tall = (C.c_int32 * 4)(0, 2 ** 31 - 4, 8, 8)
+    for crop in (big, tall):
+        assert L.gsc_loss(0, C.c_void_p(256), C.c_void_p(256), 3, 8, 8, crop, C.c_void_p(256), C.c_void_p(256),
+                          C.c_void_p(256), None) == gsc.GSC_ERR_INVALID_ARG
+        assert L.gsc_loss_noalloc(0, C.c_void_p(256), C.c_void_p(256), 3, 8, 8, crop, C.c_void_p(256),
+                                  C.c_void_p(256), None) == gsc.GSC_ERR_INVALID_ARG
+        L.gsc_last_error(msg, 256)
+        assert b"crop" in msg.value
