@@ -420,7 +420,7 @@ def run_ours(args, world, rank, local):
     roof["avg_launch_ms"] = round(dom_ms / max(dom_launches, 1), 4)
     stages = {k: round(v[0] / K, 3) for k, v in phases.items()}
     # cumulative counters per frame; the pair counts of a binning as they are
-    counts = {k: (v if k in ("pairs_last", "pairs_max", "pair_sort_passes") else round(v / K))
+    counts = {k: (v if k in ("pairs_last", "pairs_max", "pair_sort_passes", "items_last") else round(v / K))
               for k, v in counters.items()}
 
     if sel is not None:

@@ -218,8 +218,10 @@ gsc_status gsc_workspace_status(gsc_workspace* ws, gsc_stream_t stream, int64_t*
  * number of binnings, pairs composited by the re-walk, and pairs that
  * contributed gradient terms back to front.  The last two are one count:
  * the pairs composited for pixels whose dL/dimage is not zero, which are the
- * pairs that contribute back to front.  n: entries wanted (<= 10). */
-#define GSC_COUNTER_WORDS 10
+ * pairs that contribute back to front.  out[10]: work items of the last
+ * binning's order (its tiles, plus one for every extra part a gradient
+ * launch split a heavy tile into; not reset).  n: entries wanted (<= 11). */
+#define GSC_COUNTER_WORDS 11
 gsc_status gsc_workspace_counters(gsc_workspace* ws, gsc_stream_t stream, int64_t* out, int32_t n);
 
 /* ------------------------------------------------------------------ */

@@ -80,6 +80,9 @@ def lib():
             L.orc_render.restype = i32
             L.orc_render_backward.argtypes = [i64, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, i32]
             L.orc_render_backward.restype = i32
+            L.orc_render_backward_ex.argtypes = [i64, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, vp, i32]
+            L.orc_render_backward_ex.restype = i32
+            L.orc_grad_abs_map.argtypes = [i64, vp, vp, vp, vp, vp, i32]
             L.orc_render_lists.argtypes = [i64, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, i32]
             L.orc_render_lists.restype = i32
             L.orc_frozen_fd.argtypes = [i64, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, i32, vp, vp, f64, vp,
@@ -303,6 +306,38 @@ def render_backward(params, cam, dL_dimage, cfg=None, window=None, nthreads: int
     if rc:
         raise MemoryError("orc_render_backward")
     return grads, g2d
+
+
+def render_backward_terms(params, cam, dL_dimage, cfg=None, window=None, nthreads: int = 0):
+    """render_backward plus, per Gaussian, the sum of the absolute values of
+    the (pixel, term) contributions to each 2D gradient component (N, 9) and
+    the number of contributions (N,): the conditioning of each gradient sum,
+    which bounds the rounding error of a low-precision implementation."""
+    params = _c(params, np.float32)
+    x0, y0, w, h = window if window is not None else (0, 0, cam.width, cam.height)
+    g = _c(dL_dimage, np.float64)
+    assert g.shape == (3, h, w)
+    grads = np.zeros((len(params), 16), np.float64)
+    g2d = np.zeros((len(params), 9), np.float64)
+    a2d = np.zeros((len(params), 9), np.float64)
+    nterm = np.zeros(len(params), np.int64)
+    rc = lib().orc_render_backward_ex(len(params), _p(params), _p(cam.packed()), _p(_cfg(cfg)), x0, y0, w, h,
+                                      _p(g), _p(grads), _p(g2d), _p(a2d), _p(nterm), _threads(nthreads))
+    if rc:
+        raise MemoryError("orc_render_backward_ex")
+    return grads, g2d, a2d, nterm
+
+
+def grad_abs_map(params, cam, abs2d, cfg=None, nthreads: int = 0) -> np.ndarray:
+    """|J| m per Gaussian (N, 16): J the Jacobian of the packed parameter
+    gradient with respect to the 2D gradient record, m = abs2d (N, 9)."""
+    params = _c(params, np.float32)
+    m = _c(abs2d, np.float64)
+    assert m.shape == (len(params), 9)
+    out = np.zeros((len(params), 16), np.float64)
+    lib().orc_grad_abs_map(len(params), _p(params), _p(cam.packed()), _p(_cfg(cfg)), _p(m), _p(out),
+                           _threads(nthreads))
+    return out
 
 
 class FrozenLists:

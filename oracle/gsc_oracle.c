@@ -682,9 +682,24 @@ static void project_backward_one(const float* p, const rcam_t* c, const double* 
  * Gradient of the window render w.r.t. the packed parameters, given
  * dL/dimage (3 x h x w).  grads: N x 16 (+=).  g2d (optional): N x 9 2D
  * gradients dL/d{mx, my, a, b, c, opacity logit, r, g, b} (+=).
+ *
+ * The 2D gradient of a Gaussian is a sum over (pixel, term) contributions.
+ * For the error analysis of an FP32 implementation, abs2d (optional, N x 9)
+ * receives the sum of their absolute values and nterm (optional, N) their
+ * number; neither changes the gradient.
  */
+int orc_render_backward_ex(int64_t N, const float* params, const float* cam, const double* cfg, int x0, int y0,
+                           int w, int h, const double* dL_dimage, double* grads, double* g2d, double* abs2d,
+                           int64_t* nterm, int nthreads);
+
 int orc_render_backward(int64_t N, const float* params, const float* cam, const double* cfg, int x0, int y0, int w,
                         int h, const double* dL_dimage, double* grads, double* g2d, int nthreads) {
+    return orc_render_backward_ex(N, params, cam, cfg, x0, y0, w, h, dL_dimage, grads, g2d, NULL, NULL, nthreads);
+}
+
+int orc_render_backward_ex(int64_t N, const float* params, const float* cam, const double* cfg, int x0, int y0,
+                           int w, int h, const double* dL_dimage, double* grads, double* g2d, double* abs2d,
+                           int64_t* nterm, int nthreads) {
     rcam_t c;
     rcam_setup(&c, cam);
     proj_t* pr = (proj_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(proj_t));
@@ -718,10 +733,18 @@ int orc_render_backward(int64_t N, const float* params, const float* cam, const 
                     const float* pp = params + 16 * t->g;
                     double* a9 = acc + 9 * t->g;
                     double dalpha = 0;
+                    if (nterm) {
+#pragma omp atomic
+                        nterm[t->g] += 1;
+                    }
                     for (int ch = 0; ch < 3; ++ch) {
                         if (pp[12 + ch] > 0.0f) {
 #pragma omp atomic
                             a9[6 + ch] += t->alpha * t->T * gC[ch];
+                            if (abs2d) {
+#pragma omp atomic
+                                abs2d[9 * t->g + 6 + ch] += fabs(t->alpha * t->T * gC[ch]);
+                            }
                         }
                         dalpha += gC[ch] * (q->col[ch] * t->T - S[ch] / (1.0 - t->alpha));
                         S[ch] += q->col[ch] * t->alpha * t->T;
@@ -738,9 +761,17 @@ int orc_render_backward(int64_t N, const float* params, const float* cam, const 
                     for (int k5 = 0; k5 < 5; ++k5) {
 #pragma omp atomic
                         a9[k5] += v[k5];
+                        if (abs2d) {
+#pragma omp atomic
+                            abs2d[9 * t->g + k5] += fabs(v[k5]);
+                        }
                     }
 #pragma omp atomic
                     a9[5] += dop;
+                    if (abs2d) {
+#pragma omp atomic
+                        abs2d[9 * t->g + 5] += fabs(dop);
+                    }
                 }
             }
         }
@@ -759,6 +790,36 @@ int orc_render_backward(int64_t N, const float* params, const float* cam, const 
     free(order);
     free(acc);
     return 0;
+}
+
+/*
+ * |J| m per Gaussian, with J the 16 x 9 Jacobian of the packed parameter
+ * gradient with respect to the 2D gradient record (project_backward_one is
+ * linear in the record; column k is its image of the k-th unit record) and
+ * m = abs2d: an upper bound on the parameter-gradient magnitude that record
+ * errors of relative size e (per component) can cause, e |J| m.  out: N x 16
+ * (overwritten); Gaussians with a zero m row get zeros.
+ */
+void orc_grad_abs_map(int64_t N, const float* params, const float* cam, const double* cfg, const double* abs2d,
+                      double* out, int nthreads) {
+    rcam_t c;
+    rcam_setup(&c, cam);
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int64_t g = 0; g < N; ++g) {
+        double* o = out + 16 * g;
+        for (int k = 0; k < 16; ++k) o[k] = 0.0;
+        const double* m = abs2d + 9 * g;
+        int any = 0;
+        for (int k = 0; k < 9; ++k) any |= m[k] != 0.0;
+        if (!any) continue;
+        for (int k = 0; k < 9; ++k) {
+            if (m[k] == 0.0) continue;
+            double e[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, col[16] = {0};
+            e[k] = 1.0;
+            project_backward_one(params + 16 * g, &c, cfg, e, col);
+            for (int j = 0; j < 16; ++j) o[j] += fabs(col[j]) * m[k];
+        }
+    }
 }
 
 /* ------------------------------------------------------------------------ */

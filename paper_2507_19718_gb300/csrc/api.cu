@@ -167,6 +167,11 @@ RasterDev raster_dev(const gsc_raster_cfg* c) {
     int nt = c->tile_w * c->tile_h / r.ppt;
     r.cap = c->list_capacity < nt ? nt : c->list_capacity;
     r.bin = c->bin_size;
+    // the gradient kernels' hit ring: 2048 entries beside a small staging
+    // (the shared memory of 12 CTAs per SM still fits), so that the long
+    // lists of sparse tiles are walked back to front without rebuilding
+    // chunks; 1024 beside a large one
+    r.ring_log2 = r.cap <= 128 ? 11 : 10;
     return r;
 }
 
@@ -260,7 +265,9 @@ size_t layout(int64_t NG, int64_t NP, int32_t W, int32_t H, int32_t NV, gsc_work
     w->pval1 = (uint32_t*)take(4 * np);
     w->hist = (uint32_t*)take(4 * kHistWords);
     w->ranges = (uint2*)take(sizeof(uint2) * (size_t)tiles);
-    w->tile_order = (uint32_t*)take(4 * (size_t)tiles);
+    w->tile_order = (uint32_t*)take(4 * 4 * (size_t)tiles);  // up to 4 parts per tile
+    w->fb = (uint32_t*)take(4 * 5 * (size_t)tiles);
+    w->fb_state = (uint32_t*)take(4 * kFbWords);
     w->g2d = (float4*)take(sizeof(float4) * 3 * ng);
     w->red = (float*)take(sizeof(float) * red);
     w->red_floats = red;
@@ -418,6 +425,7 @@ gsc_status gsc_workspace_create(void* device_buffer, size_t bytes, int64_t max_g
     cudaError_t e = cudaMemset(ws->status, 0, sizeof(int32_t) * kStatusWords);
     if (e == cudaSuccess) e = cudaMemset(ws->counters, 0, sizeof(uint32_t) * kCounterWords);
     if (e == cudaSuccess) e = cudaMemset(ws->stats, 0, sizeof(unsigned long long) * kStatWords);
+    if (e == cudaSuccess) e = cudaMemset(ws->fb_state, 0, sizeof(uint32_t) * kFbWords);
     if (e != cudaSuccess) {
         delete ws;
         return cuda_fail(e, "workspace init");
@@ -457,10 +465,12 @@ gsc_status gsc_workspace_counters(gsc_workspace* ws, gsc_stream_t stream, int64_
     GSC_CUDA(cudaMemcpy(counters, ws->counters, sizeof counters, cudaMemcpyDeviceToHost));
     GSC_CUDA(cudaMemcpy(st, ws->stats, sizeof st, cudaMemcpyDeviceToHost));
     GSC_CUDA(cudaMemset(ws->stats, 0, sizeof st));
+    uint32_t fb[kFbWords];
+    GSC_CUDA(cudaMemcpy(fb, ws->fb_state, sizeof fb, cudaMemcpyDeviceToHost));
     int64_t all[GSC_COUNTER_WORDS] = {counters[kCntPairs], counters[kCntPairsMax], (int64_t)st[kStEvalFwd],
                                       (int64_t)st[kStCompFwd], (int64_t)st[kStEvalRewalk], (int64_t)st[kStEvalBack],
                                       (int64_t)st[kStPairsSum], (int64_t)st[kStBinnings],
-                                      (int64_t)st[kStCompRewalk], (int64_t)st[kStHitBack]};
+                                      (int64_t)st[kStCompRewalk], (int64_t)st[kStHitBack], (int64_t)fb[kFbItems]};
     for (int k = 0; k < n; ++k) out[k] = all[k];
     return GSC_OK;
 }
@@ -511,7 +521,7 @@ gsc_status gsc_cache_backward(const float* params, int64_t N, const gsc_camera* 
     batch_init(b);
     add_view(b, rc, cam, params, N, nullptr, dL_dimage, grads);
     const uint32_t* vals = nullptr;
-    cudaError_t e = bin_gaussians(b, rc, ws, &vals, s);
+    cudaError_t e = bin_gaussians(b, rc, ws, &vals, s, kOrderFeedback);
     if (e == cudaSuccess) e = launch_render_backward(b, rc, ws, vals, false, s);
     if (e != cudaSuccess) return cuda_fail(e, "gsc_cache_backward launch");
     return GSC_OK;
@@ -581,7 +591,7 @@ gsc_status gsc_render_batch(const gsc_view* views, int32_t n_views, int32_t mode
         if (e == cudaSuccess) e = launch_render(b, rc, ws, vals, s);
     }
     if (e == cudaSuccess && (mode & GSC_BATCH_BWD)) {
-        e = bin_gaussians(b, rc, ws, &vals, s);
+        e = bin_gaussians(b, rc, ws, &vals, s, kOrderFeedback);
         if (e == cudaSuccess) e = launch_render_backward(b, rc, ws, vals, shared, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "gsc_render_batch launch");
@@ -652,13 +662,13 @@ static gsc_status train_views(const gsc_train_view* views, float* const* m, floa
     if ((int64_t)b.total_bins > ws->max_tiles || (int64_t)b.total_tiles > ws->max_tiles)
         return fail(GSC_ERR_INVALID_ARG, "the batch has %u tiles and %u bins, the workspace %lld (raise max_views)",
                     b.total_tiles, b.total_bins, (long long)ws->max_tiles);
-    if ((size_t)b.total_tiles > ws->red_floats)
+    if ((size_t)b.total_tiles * 4 > ws->red_floats)  // four loss partials per tile
         return fail(GSC_ERR_INVALID_ARG, "the batch has %u tiles, the loss scratch %zu", b.total_tiles,
                     ws->red_floats);
     AdamDev ad;
     if (adam) ad = adam_dev(*adam);
     const uint32_t* vals = nullptr;
-    cudaError_t e = bin_gaussians(b, rc, ws, &vals, s);
+    cudaError_t e = bin_gaussians(b, rc, ws, &vals, s, kOrderFeedback);
     if (e == cudaSuccess)
         e = launch_train(b, rc, ws, vals, loss_kind == GSC_LOSS_HDR_FULLGRAD ? 1 : 0, shared, adam ? &ad : nullptr,
                          s);

@@ -38,6 +38,7 @@ struct RasterDev {
     int tile_w, tile_h, cap;
     int bin;  // bin size (px) of every view; 0: each view picks its own (auto_bin)
     int ppt;  // pixels per thread (1, 2, 4 or 8)
+    int ring_log2;  // hit ring of the gradient kernels: 1 << ring_log2 entries
 };
 
 // One view of a (possibly batched) render: its camera, its Gaussians (global
@@ -117,6 +118,22 @@ struct PhaseScope {
 enum : int { kStatusCode = 0, kStatusWords = 4 };
 // counters in the workspace
 enum : int { kCntPairs = 0, kCntPairsMax = 1, kCntTilesFwd = 2, kCntTilesBwd = 3, kCounterWords = 8 };
+// feedback state: launches so far (its parity picks the buffer the next
+// gradient kernel writes), signature of the batch geometry the last
+// feedback belongs to (0: none), number of work items of the current order
+// and (words 4-5, 64-bit) the summed per-tile cost of the coming order
+enum : int { kFbParity = 0, kFbSignature = 1, kFbItems = 2, kFbTotal = 4, kFbWords = 8 };
+// A work item of the persistent render kernels: a tile, or part `part` of
+// `1 << lp` parts of a tile (the part owns the tile's pixel rows whose slot
+// q of the thread has q mod (1 << lp) == part).  A whole tile is its id.
+constexpr uint32_t kItemNone = 0xffffffffu;
+__host__ __device__ __forceinline__ uint32_t make_item(uint32_t tile, uint32_t part, uint32_t lp) {
+    return tile | (part << 24) | (lp << 28);
+}
+// order of a binning: kOrderPlain (by bin-list length, whole tiles) or
+// kOrderFeedback (by the last gradient launch's per-tile work when the
+// geometry is the same, splitting the heaviest tiles)
+enum : int { kOrderPlain = 0, kOrderFeedback = 1 };
 // 64-bit work statistics in the workspace
 enum : int { kStEvalFwd = 0, kStCompFwd = 1, kStEvalRewalk = 2, kStEvalBack = 3, kStPairsSum = 4, kStBinnings = 5,
              kStCompRewalk = 6, kStHitBack = 7, kStatWords = 8 };
@@ -142,8 +159,13 @@ struct gsc_workspace {
     uint32_t *pkey0, *pkey1, *pval0, *pval1;
     uint32_t* hist;    // kHistWords
     uint2* ranges;     // [start, end) per bin
-    uint32_t* tile_order;   // tiles ordered by expected cost (longest bin lists first)
+    uint32_t* tile_order;   // work items (tiles or parts of tiles) by expected cost, longest first
     const uint32_t* order;  // the order of the last binning
+    // per-tile feedback of the gradient kernels (hits of the front-to-back
+    // walk and length of the back-to-front walk) in two buffers that swap
+    // every gradient launch, and a scratch of per-tile costs: 5 x max_tiles
+    uint32_t* fb;
+    uint32_t* fb_state;     // kFbWords: launch parity, geometry of the feedback, item count
     float4* g2d;       // 3 x NG: 2D gradients
     float* red;        // reduction scratch for losses
     size_t red_floats;
@@ -173,7 +195,7 @@ struct AdamDev;  // below, with the AdamW arithmetic
 
 // raster.cu (every view of the batch shares rc)
 cudaError_t bin_gaussians(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t** sorted_vals,
-                          cudaStream_t s);
+                          cudaStream_t s, int order_mode = kOrderPlain);
 cudaError_t launch_render(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
                           cudaStream_t s);
 // shared_params: two views write the same parameter gradients (atomics needed)

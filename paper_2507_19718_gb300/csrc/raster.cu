@@ -267,31 +267,6 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* __re
 }
 
 
-__device__ __forceinline__ unsigned lanemask_lt32() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
-// Block-wide stream compaction: rank of this thread among the threads whose
-// flag is set (in thread order) and their total.  Two barriers.
-template <int NT>
-__device__ __forceinline__ int block_rank(bool flag, int* s_warp, int& total) {
-    unsigned b = __ballot_sync(kFull, flag);
-    int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) s_warp[w] = __popc(b);
-    __syncthreads();
-    int off = 0, tot = 0;
-#pragma unroll
-    for (int k = 0; k < NT / 32; ++k) {
-        int c = s_warp[k];
-        off += k < w ? c : 0;
-        tot += c;
-    }
-    __syncthreads();
-    total = tot;
-    return off + __popc(b & lanemask_lt32());
-}
 
 __device__ __forceinline__ bool tile_in(uint2 r, int tx, int ty) {
     return tx >= (int)(r.x & 0xffffu) && tx < (int)(r.x >> 16) && ty >= (int)(r.y & 0xffffu) &&
@@ -331,6 +306,81 @@ __device__ __forceinline__ bool tile_hit(uint2 rect, float4 r0, float4 r1, int t
     return m >= r1.z - kCullMargin * (1.f + fabsf(r1.z));
 }
 
+// Block-wide exclusive scan of small per-thread counts (in thread order) and
+// their total.  Two barriers.
+template <int NT>
+__device__ __forceinline__ uint32_t block_scan_count(uint32_t v, int* s_warp, uint32_t& total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = (int)x;
+    __syncthreads();
+    uint32_t off = 0, tot = 0;
+#pragma unroll
+    for (int k = 0; k < NT / 32; ++k) {
+        const uint32_t c = (uint32_t)s_warp[k];
+        off += k < w ? c : 0u;
+        tot += c;
+    }
+    __syncthreads();
+    total = tot;
+    return off + x - v;
+}
+
+// Candidates a thread tests per filter round: one while a tile keeps most of
+// its bin list, up to kMaxRound while it keeps few (a tile of a long list of
+// large bins may keep 2% of it), so that long sparse lists cost few rounds
+// of barriers.
+constexpr int kMaxRound = 4;
+
+// One filter round of a tile over its bin list [pos, end): thread t tests
+// the kc candidates pos + t kc + k (k < kc), so that thread order is list
+// order.  Returns the thread's hit bits (bit k: candidate pos + t kc + k);
+// rank0 is the rank of its first hit among the round's hits, total their
+// number.
+template <int NT>
+__device__ __forceinline__ uint32_t filter_round(uint32_t pos, uint32_t end, int kc,
+                                                 const uint32_t* __restrict__ vals, const uint2* __restrict__ rect,
+                                                 const float4* __restrict__ rec, int tx, int ty, int TW, int TH,
+                                                 int* s_warp, uint32_t& rank0, uint32_t& total) {
+    uint32_t mask = 0;
+    if (kc == 1) {  // dense lists: one candidate per thread
+        const uint32_t c = pos + threadIdx.x;
+        if (c < end) {
+            const uint32_t g = vals[c];
+            const uint2 rr = rect[g];
+            if (tile_in(rr, tx, ty) && tile_hit(rr, rec[3 * (size_t)g], rec[3 * (size_t)g + 1], tx, ty, TW, TH))
+                mask = 1u;
+        }
+    } else {
+        const uint32_t base = pos + threadIdx.x * (uint32_t)kc;
+        uint32_t g[kMaxRound];
+#pragma unroll
+        for (int k = 0; k < kMaxRound; ++k) {
+            const uint32_t c = base + (uint32_t)k;
+            g[k] = (k < kc && c < end) ? vals[c] : 0xffffffffu;
+        }
+        // all gathers of the round before any test, so that their latencies overlap
+        uint2 rr[kMaxRound];
+#pragma unroll
+        for (int k = 0; k < kMaxRound; ++k) rr[k] = g[k] != 0xffffffffu ? rect[g[k]] : make_uint2(0u, 0u);
+        uint32_t in = 0;
+#pragma unroll
+        for (int k = 0; k < kMaxRound; ++k) in |= (g[k] != 0xffffffffu && tile_in(rr[k], tx, ty)) ? 1u << k : 0u;
+        for (uint32_t m = in; m; m &= m - 1) {  // few candidates reach the exact test
+            const int k = __ffs(m) - 1;
+            const uint32_t gk = vals[base + (uint32_t)k];  // both loads hit L1 now
+            if (tile_hit(rect[gk], rec[3 * (size_t)gk], rec[3 * (size_t)gk + 1], tx, ty, TW, TH)) mask |= 1u << k;
+        }
+    }
+    rank0 = block_scan_count<NT>((uint32_t)__popc(mask), s_warp, total);
+    return mask;
+}
+
 // one warp of the block counts its pixels' evaluated pairs with one atomic
 __device__ __forceinline__ void warp_count(unsigned long long* dst, uint32_t v) {
 #pragma unroll
@@ -365,7 +415,7 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render(const __grid_constant__
     float4* s1 = smem + cap;
     float4* s2 = smem + 2 * cap;
     uint32_t n_eval = 0, n_comp = 0;
-    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_tile, s_resume;
     // persistent CTAs: tiles of all views are handed out by an atomic counter,
     // in the order of their expected cost (longest bin list first)
     for (;;) {
@@ -400,35 +450,38 @@ __global__ void __launch_bounds__(TW* TH / PPT) k_render(const __grid_constant__
     uint2 rg = ranges[vw.bin_off + (ty / vw.spt_y) * vw.bins_x + tx / vw.spt_x];
     uint32_t pos = rg.x;
     uint32_t hbase = 0;  // entries staged by earlier batches of this tile
+    int kc = 1;          // candidates per thread and filter round
     for (;;) {
         bool tdone = true;
 #pragma unroll
         for (int q = 0; q < PPT; ++q) tdone = tdone && ev[q] != 0xffffffffu;
         if (__syncthreads_count(tdone) == NT || pos >= rg.y) break;
         int staged = 0;
-        while (pos < rg.y && staged + NT <= cap) {
-            uint32_t c = pos + threadIdx.x;
-            uint32_t g = 0;
-            bool hit = false;
-            float4 a0, a1;
-            if (c < rg.y) {
-                g = vals[c];
-                uint2 rr = rect[g];
-                if (tile_in(rr, tx, ty)) {
-                    a0 = rec[3 * (size_t)g];
-                    a1 = rec[3 * (size_t)g + 1];
-                    hit = tile_hit(rr, a0, a1, tx, ty, TW, TH);
+        while (pos < rg.y && staged < cap) {
+            uint32_t r, tot;
+            const uint32_t mask = filter_round<NT>(pos, rg.y, kc, vals, rect, rec, tx, ty, TW, TH, s_warp, r, tot);
+            const uint32_t room = (uint32_t)(cap - staged), base = pos + threadIdx.x * (uint32_t)kc;
+            for (uint32_t m = mask; m; m &= m - 1, ++r) {
+                const uint32_t c = base + (uint32_t)(__ffs(m) - 1);
+                if (r < room) {
+                    const uint32_t g = vals[c];
+                    s0[staged + r] = rec[3 * (size_t)g];
+                    s1[staged + r] = rec[3 * (size_t)g + 1];
+                    s2[staged + r] = rec[3 * (size_t)g + 2];
+                } else if (r == room) {
+                    s_resume = c;  // the first hit that did not fit: the next round starts there
                 }
             }
-            int tot;
-            int r = block_rank<NT>(hit, s_warp, tot);
-            if (hit) {
-                s0[staged + r] = a0;
-                s1[staged + r] = a1;
-                s2[staged + r] = rec[3 * (size_t)g + 2];
+            if (tot > room) {
+                __syncthreads();
+                pos = s_resume;
+                staged = cap;
+                kc = max(kc >> 1, 1);
+            } else {
+                pos += (uint32_t)kc * NT;
+                staged += (int)tot;
+                if (4 * tot < room && kc < kMaxRound) kc <<= 1;
             }
-            staged += tot;
-            pos += NT;
         }
         __syncthreads();
         if (!tdone) {
@@ -516,8 +569,8 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float (&a)[8], int l
 
 // Phase 1 re-walks the bin list front to back with the forward's decisions.
 // The entries that pass the tile filter ("hits") are numbered in list order;
-// their Gaussian ids go to a shared-memory ring of kHitRing slots, and the
-// list position of every kHitRing-th hit is recorded, so that phase 2 can
+// their Gaussian ids go to a shared-memory ring of `ring` slots (a power of
+// two), and the list position of every ring-th hit is recorded, so that phase 2 can
 // rebuild any chunk of hits without scanning from the start.  Each pixel
 // keeps its final T and the hit number of the entry that stopped it (none if
 // it never stopped: it then saw every hit).
@@ -532,8 +585,12 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float (&a)[8], int l
 // target and its own dL/dC, writes the image and adds its loss term to the
 // tile's partial sum, and phase 2 runs on that gradient.  Nothing per pixel
 // leaves the tile.
-constexpr int kHitRing = 1024;
 constexpr int kMaxChunks = 256;
+
+// Loss partials per tile of the training step: four (pixel slot classes
+// q mod 4) where the order may split a tile into parts, i.e. one-warp CTAs,
+// so that the loss does not depend on the split; one otherwise.
+__host__ __device__ constexpr int loss_slots(int threads) { return threads <= 32 ? 4 : 1; }
 
 // CTAs per SM the register allocation is sized for.  At 4 pixels per thread
 // 12 CTAs of 64 threads (80 registers; the 17 KB of shared memory per CTA
@@ -551,32 +608,42 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
                                                              float4* __restrict__ g2d, uint32_t* __restrict__ queue,
                                                              unsigned long long* __restrict__ stats,
                                                              float* __restrict__ tile_loss,
-                                                             const uint32_t* __restrict__ order) {
+                                                             const uint32_t* __restrict__ order,
+                                                             const uint32_t* __restrict__ fb_state,
+                                                             uint32_t* __restrict__ fb, uint32_t fb_stride) {
     constexpr int NT = TW * TH / PPT;
     constexpr int ROWS = TH / PPT;
+    constexpr int SLOTS = loss_slots(NT);
     extern __shared__ float4 smem[];
     __shared__ int s_warp[NT / 32];
     __shared__ uint32_t s_end;
     __shared__ uint32_t s_chunk_pos[kMaxChunks];
-    __shared__ float s_loss[NT / 32];
+    __shared__ float s_loss[SLOTS][NT / 32];
     const int cap = rc.cap;
     float4* s0 = smem;
     float4* s1 = smem + cap;
     float4* s2 = smem + 2 * cap;
     uint32_t* hits = reinterpret_cast<uint32_t*>(smem + 3 * cap);
+    const uint32_t rmask = (1u << rc.ring_log2) - 1u;
     uint32_t n_eval1 = 0, n_eval2 = 0, n_hit2 = 0;
-    __shared__ uint32_t s_tile;
-    // persistent CTAs: tiles of all views are handed out by an atomic counter,
-    // in the order of their expected cost (longest bin list first)
+    __shared__ uint32_t s_item, s_resume;
+    // work items and the feedback buffer of this launch (set by the order kernel)
+    const uint32_t n_items = fb_state[kFbItems];
+    uint32_t* const fb_hit = fb + 2 * (size_t)fb_stride * (fb_state[kFbParity] & 1u);
+    // persistent CTAs: work items (tiles, or parts of the heaviest tiles) of
+    // all views are handed out by an atomic counter, longest first
     for (;;) {
     if (threadIdx.x == 0) {
         uint32_t q = atomicAdd(queue, 1u);
-        s_tile = q < b.total_tiles ? order[q] : b.total_tiles;
+        s_item = q < n_items ? order[q] : kItemNone;
     }
     __syncthreads();
-    const uint32_t tile = s_tile;
+    const uint32_t item = s_item;
     __syncthreads();
-    if (tile >= b.total_tiles) break;
+    if (item == kItemNone) break;
+    const uint32_t tile = item & 0xffffffu;
+    // a part owns the pixel slots q with q mod nparts == part
+    const int part = (int)((item >> 24) & 15u), pmask = (1 << (item >> 28)) - 1;
     const ViewDev& vw = b.v[view_of_tile(b, tile)];
     const CamDev& cam = vw.cam;
     const uint32_t lt = tile - vw.tile_off;
@@ -592,7 +659,7 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
         int py = py0 + q * ROWS;
-        bool inside = px < cam.W && py < cam.H;
+        bool inside = px < cam.W && py < cam.H && (q & pmask) == part;
         fy[q] = (float)py + 0.5f;
         gr[q] = gg[q] = gb[q] = 0.f;
         Cr[q] = Cg[q] = Cb[q] = 0.f;
@@ -615,6 +682,7 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
     // ---- phase 1
     uint32_t nhit = 0;  // hits found so far (uniform)
     uint32_t pos = rg.x;
+    int kc = 1;         // candidates per thread and filter round
     for (;;) {
         bool tdone = true;
 #pragma unroll
@@ -622,33 +690,36 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
         if (__syncthreads_count(tdone) == NT || pos >= rg.y) break;
         int staged = 0;
         uint32_t h0 = nhit;
-        while (pos < rg.y && staged + NT <= cap) {
-            uint32_t c = pos + threadIdx.x;
-            uint32_t g = 0;
-            bool hit = false;
-            float4 a0, a1;
-            if (c < rg.y) {
-                g = vals[c];
-                uint2 rr = rect[g];
-                if (tile_in(rr, tx, ty)) {
-                    a0 = rec[3 * (size_t)g];
-                    a1 = rec[3 * (size_t)g + 1];
-                    hit = tile_hit(rr, a0, a1, tx, ty, TW, TH);
+        while (pos < rg.y && staged < cap) {
+            uint32_t r, tot;
+            const uint32_t mask = filter_round<NT>(pos, rg.y, kc, vals, rect, rec, tx, ty, TW, TH, s_warp, r, tot);
+            const uint32_t room = (uint32_t)(cap - staged), base = pos + threadIdx.x * (uint32_t)kc;
+            for (uint32_t m = mask; m; m &= m - 1, ++r) {
+                const uint32_t c = base + (uint32_t)(__ffs(m) - 1);
+                if (r < room) {
+                    const uint32_t g = vals[c];
+                    s0[staged + r] = rec[3 * (size_t)g];
+                    s1[staged + r] = rec[3 * (size_t)g + 1];
+                    if (LOSS != kLossNone) s2[staged + r] = rec[3 * (size_t)g + 2];
+                    const uint32_t hid = nhit + r;
+                    hits[hid & rmask] = g;
+                    if ((hid & rmask) == 0 && (hid >> rc.ring_log2) < kMaxChunks) s_chunk_pos[hid >> rc.ring_log2] = c;
+                } else if (r == room) {
+                    s_resume = c;  // the first hit that did not fit: the next round starts there
                 }
             }
-            int tot;
-            int r = block_rank<NT>(hit, s_warp, tot);
-            if (hit) {
-                s0[staged + r] = a0;
-                s1[staged + r] = a1;
-                if (LOSS != kLossNone) s2[staged + r] = rec[3 * (size_t)g + 2];
-                uint32_t hid = nhit + r;
-                hits[hid % kHitRing] = g;
-                if (hid % kHitRing == 0 && hid / kHitRing < kMaxChunks) s_chunk_pos[hid / kHitRing] = c;
+            if (tot > room) {
+                __syncthreads();
+                pos = s_resume;
+                staged = cap;
+                nhit += room;
+                kc = max(kc >> 1, 1);
+            } else {
+                pos += (uint32_t)kc * NT;
+                staged += (int)tot;
+                nhit += tot;
+                if (4 * tot < room && kc < kMaxRound) kc <<= 1;
             }
-            staged += tot;
-            nhit += tot;
-            pos += NT;
         }
         __syncthreads();
         if (!tdone) {
@@ -685,10 +756,13 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
     for (int q = 0; q < PPT; ++q)
         if (active[q]) n_eval1 += ev[q] == 0xffffffffu ? nhit : ev[q];
     if (LOSS != kLossNone) {
-        // image out, loss term and dL/dC of every pixel; the tile's loss sum
-        // goes to its partial (fixed order: pixels of a thread, warp
-        // butterfly, warps in order)
-        float lsum = 0.f;
+        // image out, loss term and dL/dC of every pixel; the tile's loss goes
+        // to SLOTS partials, one per pixel slot class q mod SLOTS (fixed
+        // order: pixels of a thread, warp butterfly, warps in order), so that
+        // the sums do not depend on how the tile was split into parts
+        float lsum[SLOTS];
+#pragma unroll
+        for (int r = 0; r < SLOTS; ++r) lsum[r] = 0.f;
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
             if (!active[q]) continue;
@@ -699,20 +773,23 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
                 vw.image[2 * HW + pix] = Cb[q];
             }
             const float* tg = vw.target;
-            lsum += hdr_term(Cr[q], tg[pix]) + hdr_term(Cg[q], tg[HW + pix]) + hdr_term(Cb[q], tg[2 * HW + pix]);
+            lsum[q & (SLOTS - 1)] += hdr_term(Cr[q], tg[pix]) + hdr_term(Cg[q], tg[HW + pix]) + hdr_term(Cb[q], tg[2 * HW + pix]);
             gr[q] = hdr_grad(Cr[q], tg[pix], LOSS == kLossHdrFull, vw.invk);
             gg[q] = hdr_grad(Cg[q], tg[HW + pix], LOSS == kLossHdrFull, vw.invk);
             gb[q] = hdr_grad(Cb[q], tg[2 * HW + pix], LOSS == kLossHdrFull, vw.invk);
             active[q] = gr[q] != 0.f || gg[q] != 0.f || gb[q] != 0.f;
         }
-        lsum = warp_sum(lsum);
-        if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = lsum;
+#pragma unroll
+        for (int r = 0; r < SLOTS; ++r) {
+            const float ls = warp_sum(lsum[r]);
+            if ((threadIdx.x & 31) == 0) s_loss[r][threadIdx.x >> 5] = ls;
+        }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < SLOTS && (threadIdx.x & pmask) == part) {  // the partials this item owns
             float t = 0.f;
 #pragma unroll
-            for (int w = 0; w < NT / 32; ++w) t += s_loss[w];
-            tile_loss[tile] = t;
+            for (int w = 0; w < NT / 32; ++w) t += s_loss[threadIdx.x][w];
+            tile_loss[SLOTS * (size_t)tile + threadIdx.x] = t;
         }
     }
     if (threadIdx.x == 0) s_end = 0;
@@ -730,6 +807,12 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
     if (mylast) atomicMax(&s_end, mylast);
     __syncthreads();
     const uint32_t hend = s_end;
+    // feedback for the next launch's order: the tile's (parts': largest) hits
+    // front to back and length back to front
+    if (threadIdx.x == 0) {
+        atomicMax(&fb_hit[tile], nhit);
+        atomicMax(&fb_hit[fb_stride + tile], hend);
+    }
     uint32_t wlast = mylast;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(kFull, wlast, o));
@@ -742,32 +825,28 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
 #pragma unroll
     for (int q = 0; q < PPT; ++q) DS[q] = 0.f;
     int lane = threadIdx.x & 31;
-    int ring_chunk = nhit ? (int)((nhit - 1) / kHitRing) : -1;  // chunk whose hits the ring holds
-    for (int ch = hend ? (int)((hend - 1) / kHitRing) : -1; ch >= 0; --ch) {
-        const uint32_t hc0 = (uint32_t)ch * kHitRing;
-        const uint32_t hc1 = min(hc0 + kHitRing, hend);
+    int ring_chunk = nhit ? (int)((nhit - 1) >> rc.ring_log2) : -1;  // chunk whose hits the ring holds
+    for (int ch = hend ? (int)((hend - 1) >> rc.ring_log2) : -1; ch >= 0; --ch) {
+        const uint32_t hc0 = (uint32_t)ch << rc.ring_log2;
+        const uint32_t hc1 = min(hc0 + rmask + 1u, hend);
         if (ch != ring_chunk) {
             // rebuild hits [hc0, hc1) from the nearest recorded chunk start
             int base_chunk = ch < kMaxChunks ? ch : kMaxChunks - 1;
             uint32_t p = s_chunk_pos[base_chunk];
-            uint32_t h = (uint32_t)base_chunk * kHitRing;
+            uint32_t h = (uint32_t)base_chunk << rc.ring_log2;
             __syncthreads();
+            int kr = 1;
             while (h < hc1 && p < rg.y) {
-                uint32_t c = p + threadIdx.x;
-                uint32_t g = 0;
-                bool hit = false;
-                if (c < rg.y) {
-                    g = vals[c];
-                    uint2 rr = rect[g];
-                    if (tile_in(rr, tx, ty))
-                        hit = tile_hit(rr, rec[3 * (size_t)g], rec[3 * (size_t)g + 1], tx, ty, TW, TH);
+                uint32_t r, tot;
+                const uint32_t mask = filter_round<NT>(p, rg.y, kr, vals, rect, rec, tx, ty, TW, TH, s_warp, r, tot);
+                const uint32_t base = p + threadIdx.x * (uint32_t)kr;
+                for (uint32_t m = mask; m; m &= m - 1, ++r) {
+                    const uint32_t hid = h + r;
+                    if (hid >= hc0 && hid < hc1) hits[hid & rmask] = vals[base + (uint32_t)(__ffs(m) - 1)];
                 }
-                int tot;
-                int r = block_rank<NT>(hit, s_warp, tot);
-                uint32_t hid = h + r;
-                if (hit && hid >= hc0 && hid < hc1) hits[hid % kHitRing] = g;
                 h += tot;
-                p += NT;
+                p += (uint32_t)kr * NT;
+                if (4 * tot < (uint32_t)(kr * NT) && kr < kMaxRound) kr <<= 1;
             }
             ring_chunk = ch;
         }
@@ -777,7 +856,7 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
             int n = (int)(b1 - b0);
             __syncthreads();
             for (int i = threadIdx.x; i < n; i += NT) {
-                uint32_t g = hits[(b0 + i) % kHitRing];
+                uint32_t g = hits[(b0 + i) & rmask];
                 s0[i] = rec[3 * (size_t)g];
                 s1[i] = rec[3 * (size_t)g + 1];
                 s2[i] = rec[3 * (size_t)g + 2];
@@ -843,7 +922,7 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_blocks(PPT)) k_render_bw
                     // values 0..7 -> floats 0..5, 8, 9 of the 12-float 2D gradient record
                     float tot = warp_reduce_scatter8(v8, lane);
                     float blue = warp_sum(dcb);
-                    float* gg2 = reinterpret_cast<float*>(g2d + 3 * (size_t)hits[j % kHitRing]);
+                    float* gg2 = reinterpret_cast<float*>(g2d + 3 * (size_t)hits[j & rmask]);
                     if ((lane & 3) == 0) {
                         int v = lane >> 2;
                         atomicAdd(gg2 + (v < 6 ? v : v + 2), tot);
@@ -1052,15 +1131,88 @@ __device__ __forceinline__ int view_of_bin(const BatchDev& b, uint32_t bin) {
     return v;
 }
 
+// Geometry of a batch as far as the per-tile feedback is concerned: the tile
+// grid of every view (FNV-1a over the words; never 0, which means none).
+__device__ uint32_t batch_signature(const BatchDev& b, const RasterDev& rc) {
+    uint32_t h = 2166136261u;
+    auto mix = [&](uint32_t w) { h = (h ^ w) * 16777619u; };
+    mix((uint32_t)b.nviews);
+    mix(b.total_tiles);
+    mix((uint32_t)rc.tile_w);
+    mix((uint32_t)rc.tile_h);
+    for (int v = 0; v < b.nviews; ++v) {
+        mix((uint32_t)b.v[v].tiles_x);
+        mix((uint32_t)b.v[v].tiles_y);
+    }
+    return h | 1u;
+}
+
+// Per-tile cost for the feedback order, ahead of k_tile_order: the largest
+// front-to-back hit count plus back-to-front length of the last gradient
+// launch among a tile and its eight neighbours (the view moves a little
+// between frames), and the sum of the tiles' own costs.  It also clears the
+// buffer the coming gradient kernel writes.
+constexpr int kCostThreads = 256;
+__global__ void __launch_bounds__(kCostThreads) k_tile_cost(const __grid_constant__ BatchDev b,
+                                                            uint32_t* __restrict__ fb, uint32_t fb_stride,
+                                                            uint32_t* __restrict__ fb_state) {
+    __shared__ unsigned long long s_sum[kCostThreads / 32];
+    const uint32_t parity = fb_state[kFbParity];
+    const uint32_t* fb_hit = fb + 2 * (size_t)fb_stride * (parity & 1u);  // written by the last gradient launch
+    const uint32_t* fb_len = fb_hit + fb_stride;
+    uint32_t* w_hit = fb + 2 * (size_t)fb_stride * ((parity + 1u) & 1u);
+    uint32_t* cost = fb + 4 * (size_t)fb_stride;
+    unsigned long long own = 0;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < b.total_tiles; t += gridDim.x * blockDim.x) {
+        const ViewDev& vw = b.v[view_of_tile(b, t)];
+        const uint32_t lt = t - vw.tile_off;
+        const int tx = (int)(lt % (uint32_t)vw.tiles_x), ty = (int)(lt / (uint32_t)vw.tiles_x);
+        uint32_t c = 0;
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int x = tx + dx, y = ty + dy;
+                if (x < 0 || y < 0 || x >= vw.tiles_x || y >= vw.tiles_y) continue;
+                const uint32_t u = vw.tile_off + (uint32_t)(y * vw.tiles_x + x);
+                c = max(c, fb_hit[u] + fb_len[u]);
+            }
+        cost[t] = c;
+        own += fb_hit[t] + fb_len[t];
+        w_hit[t] = 0u;
+        w_hit[fb_stride + t] = 0u;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) own += __shfl_xor_sync(kFull, own, o);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = own;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kCostThreads / 32; ++w) t += s_sum[w];
+        if (t) atomicAdd(reinterpret_cast<unsigned long long*>(fb_state + kFbTotal), t);
+    }
+}
+
 // One CTA.  With `totals` (the digit counts of a one-pass pair sort, where
 // the digit is the whole bin id) it first writes every bin's range as the
-// exclusive scan of the counts.  Then per bin: its class and tile count; the
-// tile counts are summed per class and scanned, and every bin takes its start
-// in its class and writes its tiles there in row-major order.
+// exclusive scan of the counts.  Then the work items, longest first:
+//
+// kOrderPlain, or kOrderFeedback without usable feedback: per bin its class
+// and tile count; the tile counts are summed per class and scanned, and every
+// bin takes its start in its class and writes its tiles there in row-major
+// order.
+//
+// kOrderFeedback with feedback from the last gradient launch of the same
+// geometry: the items are ordered by the tile costs k_tile_cost wrote.  With one-warp
+// CTAs a tile whose cost exceeds half of the mean work of one of the
+// launch's `grid` persistent CTAs is split into min(4, pixels per thread)
+// parts, so that no single CTA holds the launch back.  The order and the split decide which CTA renders which
+// pixels, never a result.  In feedback mode it also advances the launch
+// parity and resets the cost sum.
 __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_constant__ BatchDev b,
                                                               const uint32_t* __restrict__ totals,
                                                               uint2* __restrict__ ranges, RasterDev rc,
-                                                              uint32_t* __restrict__ order) {
+                                                              uint32_t* __restrict__ order, int mode, int grid,
+                                                              uint32_t* __restrict__ fb, uint32_t fb_stride,
+                                                              uint32_t* __restrict__ fb_state) {
     __shared__ uint32_t cls[kOrderClasses];
     __shared__ uint32_t wsum[kOrderThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1079,55 +1231,110 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_const
         __syncthreads();
         return before + x - v;
     };
-    const uint32_t nb = b.total_bins;
+    const uint32_t nb = b.total_bins, nt = b.total_tiles;
     if (totals) {  // the caller guarantees nb <= kOrderThreads here
         uint32_t c = threadIdx.x < nb ? totals[threadIdx.x] : 0u;
         uint32_t s = block_scan(c);
         if (threadIdx.x < nb) ranges[threadIdx.x] = make_uint2(s, s + c);
     }
     if (threadIdx.x < kOrderClasses) cls[threadIdx.x] = 0;
-    __syncthreads();  // also makes the ranges written above visible to the CTA
-    auto bin_info = [&](uint32_t bin, uint32_t& klass, uint32_t& ntiles) {
-        const ViewDev& vw = b.v[view_of_bin(b, bin)];
-        const uint32_t lb = bin - vw.bin_off;
-        const int bx = (int)(lb % (uint32_t)vw.bins_x), by = (int)(lb / (uint32_t)vw.bins_x);
-        const int w = min(vw.spt_x, vw.tiles_x - bx * vw.spt_x), h = min(vw.spt_y, vw.tiles_y - by * vw.spt_y);
-        ntiles = (uint32_t)(w * h);
-        const uint2 rg = ranges[bin];
-        const float l = log2f((float)(rg.y - rg.x) + 1.0f) * 8.0f;
-        klass = (uint32_t)(kOrderClasses - 1) - (uint32_t)fminf(l, (float)(kOrderClasses - 1));
-    };
-    for (uint32_t bin = threadIdx.x; bin < nb; bin += kOrderThreads) {
-        uint32_t k, nt;
-        bin_info(bin, k, nt);
-        atomicAdd(&cls[k], nt);
+    bool use_fb = false;
+    uint32_t sig = 0, parity = 0;
+    if (mode == kOrderFeedback) {
+        sig = batch_signature(b, rc);
+        parity = fb_state[kFbParity];
+        use_fb = fb_state[kFbSignature] == sig && grid > 0;
     }
-    __syncthreads();
-    uint32_t c = threadIdx.x < kOrderClasses ? cls[threadIdx.x] : 0u;
-    uint32_t s = block_scan(c);
-    if (threadIdx.x < kOrderClasses) cls[threadIdx.x] = s;
-    __syncthreads();
-    // one warp per bin: it takes the bin's start in its class and writes
-    // the bin's tiles, row-major, 32 at a time
-    for (uint32_t bin = warp; bin < nb; bin += kOrderThreads / 32) {
-        uint32_t k, nt;
-        bin_info(bin, k, nt);
-        uint32_t st = 0;
-        if (lane == 0) st = atomicAdd(&cls[k], nt);
-        st = __shfl_sync(kFull, st, 0);
-        const ViewDev& vw = b.v[view_of_bin(b, bin)];
-        const uint32_t lb = bin - vw.bin_off;
-        const int bx = (int)(lb % (uint32_t)vw.bins_x), by = (int)(lb / (uint32_t)vw.bins_x);
-        const int w = min(vw.spt_x, vw.tiles_x - bx * vw.spt_x);
-        for (uint32_t li = (uint32_t)lane; li < nt; li += 32) {
-            const int ry = (int)li / w, rx = (int)li - ry * w;
-            order[st + li] = vw.tile_off + (uint32_t)((by * vw.spt_y + ry) * vw.tiles_x + bx * vw.spt_x + rx);
+    __syncthreads();  // also makes the ranges written above visible to the CTA
+    const uint32_t* cost = fb + 4 * (size_t)fb_stride;
+    // only a one-warp CTA splits its heavy tiles: a larger CTA walks a tile's
+    // list about as fast alone as its parts would, each part redoing the
+    // list filter (measured at 2 and 4 pixels per thread)
+    const uint32_t max_parts = rc.tile_w * rc.tile_h / rc.ppt <= 32 ? (uint32_t)min(4, rc.ppt) : 1u;
+    auto klass_of = [](float c) -> uint32_t {
+        const float l = log2f(c + 1.0f) * 8.0f;
+        return (uint32_t)(kOrderClasses - 1) - (uint32_t)fminf(l, (float)(kOrderClasses - 1));
+    };
+    if (use_fb) {
+        // a tile above half the mean load of a CTA is split
+        const unsigned long long total = *reinterpret_cast<const unsigned long long*>(fb_state + kFbTotal);
+        const float split_at = 0.5f * (float)total / (float)grid;
+        auto parts_of = [&](uint32_t c) -> uint32_t {
+            return (max_parts > 1 && (float)c > split_at) ? max_parts : 1u;
+        };
+        auto item_cost = [](uint32_t c, uint32_t p) -> float {  // a part redoes the per-entry work
+            return (float)c * (float)(p + 1) / (float)(2 * p);
+        };
+        for (uint32_t t = threadIdx.x; t < nt; t += kOrderThreads) {
+            const uint32_t c = cost[t], p = parts_of(c);
+            atomicAdd(&cls[klass_of(item_cost(c, p))], p);
+        }
+        __syncthreads();
+        uint32_t v = threadIdx.x < kOrderClasses ? cls[threadIdx.x] : 0u;
+        uint32_t sc = block_scan(v);
+        if (threadIdx.x < kOrderClasses) cls[threadIdx.x] = sc;
+        if (threadIdx.x == kOrderClasses - 1) fb_state[kFbItems] = sc + v;
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < nt; t += kOrderThreads) {
+            const uint32_t c = cost[t], p = parts_of(c);
+            const uint32_t st = atomicAdd(&cls[klass_of(item_cost(c, p))], p);
+            const uint32_t lp = p == 4 ? 2u : (p == 2 ? 1u : 0u);
+            for (uint32_t k = 0; k < p; ++k) order[st + k] = make_item(t, k, lp);
+        }
+    } else {
+        auto bin_info = [&](uint32_t bin, uint32_t& klass, uint32_t& ntiles) {
+            const ViewDev& vw = b.v[view_of_bin(b, bin)];
+            const uint32_t lb = bin - vw.bin_off;
+            const int bx = (int)(lb % (uint32_t)vw.bins_x), by = (int)(lb / (uint32_t)vw.bins_x);
+            const int w = min(vw.spt_x, vw.tiles_x - bx * vw.spt_x), h = min(vw.spt_y, vw.tiles_y - by * vw.spt_y);
+            ntiles = (uint32_t)(w * h);
+            const uint2 rg = ranges[bin];
+            klass = klass_of((float)(rg.y - rg.x));
+        };
+        for (uint32_t bin = threadIdx.x; bin < nb; bin += kOrderThreads) {
+            uint32_t k, n;
+            bin_info(bin, k, n);
+            atomicAdd(&cls[k], n);
+        }
+        __syncthreads();
+        uint32_t c = threadIdx.x < kOrderClasses ? cls[threadIdx.x] : 0u;
+        uint32_t s = block_scan(c);
+        if (threadIdx.x < kOrderClasses) cls[threadIdx.x] = s;
+        __syncthreads();
+        // one warp per bin: it takes the bin's start in its class and writes
+        // the bin's tiles, row-major, 32 at a time
+        for (uint32_t bin = warp; bin < nb; bin += kOrderThreads / 32) {
+            uint32_t k, n;
+            bin_info(bin, k, n);
+            uint32_t st = 0;
+            if (lane == 0) st = atomicAdd(&cls[k], n);
+            st = __shfl_sync(kFull, st, 0);
+            const ViewDev& vw = b.v[view_of_bin(b, bin)];
+            const uint32_t lb = bin - vw.bin_off;
+            const int bx = (int)(lb % (uint32_t)vw.bins_x), by = (int)(lb / (uint32_t)vw.bins_x);
+            const int w = min(vw.spt_x, vw.tiles_x - bx * vw.spt_x);
+            for (uint32_t li = (uint32_t)lane; li < n; li += 32) {
+                const int ry = (int)li / w, rx = (int)li - ry * w;
+                order[st + li] = vw.tile_off + (uint32_t)((by * vw.spt_y + ry) * vw.tiles_x + bx * vw.spt_x + rx);
+            }
+        }
+        if (threadIdx.x == 0) fb_state[kFbItems] = nt;
+    }
+    if (mode == kOrderFeedback) {
+        __syncthreads();  // every read of the state above is done
+        if (threadIdx.x == 0) {
+            fb_state[kFbParity] = parity + 1u;
+            fb_state[kFbSignature] = sig;
+            *reinterpret_cast<unsigned long long*>(fb_state + kFbTotal) = 0ull;
         }
     }
 }
 
+// persistent CTAs of the gradient kernel of this launch configuration
+static int bwd_grid_hint(const RasterDev& rc, uint32_t tiles);
+
 cudaError_t bin_gaussians(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t** sorted_vals,
-                          cudaStream_t s) {
+                          cudaStream_t s, int order_mode) {
     uint32_t n = b.total_g;
     uint32_t nblk = (n + 255) / 256;
     if (nblk == 0) nblk = 1;
@@ -1165,13 +1372,19 @@ cudaError_t bin_gaussians(const BatchDev& b, const RasterDev& rc, gsc_workspace*
         // are their exclusive scan (done by k_tile_order); more passes: the
         // ranges come from the boundaries of the sorted keys
         const bool one_pass = radix_passes(bits) == 1 && bins <= (uint32_t)kOrderThreads;
-        PhaseScope ph(kPhRanges, s, one_pass ? 1 : 2);
+        PhaseScope ph(kPhRanges, s, (one_pass ? 1 : 2) + (order_mode == kOrderFeedback ? 1 : 0));
         if (!one_pass) {
             cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * bins, s);
             k_ranges<<<152 * 8, 256, 0, s>>>(keys, ws->counters, ws->ranges);
         }
+        const int grid = order_mode == kOrderFeedback ? bwd_grid_hint(rc, b.total_tiles) : 0;
+        if (order_mode == kOrderFeedback) {
+            const uint32_t nblk = min((b.total_tiles + kCostThreads - 1) / kCostThreads, 152u * 4u);
+            k_tile_cost<<<nblk ? nblk : 1u, kCostThreads, 0, s>>>(b, ws->fb, (uint32_t)ws->max_tiles, ws->fb_state);
+        }
         k_tile_order<<<1, kOrderThreads, 0, s>>>(b, one_pass ? radix_totals(ws->hist) : nullptr, ws->ranges, rc,
-                                                 ws->tile_order);
+                                                 ws->tile_order, order_mode, grid, ws->fb, (uint32_t)ws->max_tiles,
+                                                 ws->fb_state);
         ws->order = ws->tile_order;
     }
     return cudaGetLastError();
@@ -1220,19 +1433,35 @@ static cudaError_t render_t(const BatchDev& b, const RasterDev& rc, gsc_workspac
 }
 
 template <int TW, int TH, int PPT, int LOSS>
-static cudaError_t render_bwd_t(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
-                                cudaStream_t s) {
-    size_t smem = sizeof(float4) * 3 * rc.cap + sizeof(uint32_t) * kHitRing;
+static size_t bwd_smem(const RasterDev& rc) {
+    return sizeof(float4) * 3 * rc.cap + (sizeof(uint32_t) << rc.ring_log2);
+}
+
+// grid of the gradient kernel: every CTA that fits at once, at most one per
+// work item (a tile is at most 4 items)
+template <int TW, int TH, int PPT, int LOSS>
+static cudaError_t bwd_grid(const RasterDev& rc, uint32_t tiles, int* grid) {
+    const size_t smem = bwd_smem<TW, TH, PPT, LOSS>(rc);
     auto kern = k_render_bwd<TW, TH, PPT, LOSS>;
     static int cached = 32 * 1024;
     cudaError_t e = ensure_smem(kern, smem, &cached);
     if (e != cudaSuccess) return e;
     static size_t gs = 0;
     static int gg = 0;
-    int grid = persistent_grid(kern, TW * TH / PPT, smem, b.total_tiles, &gs, &gg);
+    *grid = persistent_grid(kern, TW * TH / PPT, smem, 4 * tiles, &gs, &gg);
+    return cudaSuccess;
+}
+
+template <int TW, int TH, int PPT, int LOSS>
+static cudaError_t render_bwd_t(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
+                                cudaStream_t s) {
+    int grid = 0;
+    cudaError_t e = bwd_grid<TW, TH, PPT, LOSS>(rc, b.total_tiles, &grid);
+    if (e != cudaSuccess) return e;
     cudaMemsetAsync(ws->counters + kCntTilesBwd, 0, sizeof(uint32_t), s);
-    kern<<<grid, TW * TH / PPT, smem, s>>>(b, ws->ranges, vals, ws->rect, ws->rec, rc, ws->g2d,
-                                           ws->counters + kCntTilesBwd, ws->stats, ws->red, ws->order);
+    k_render_bwd<TW, TH, PPT, LOSS><<<grid, TW * TH / PPT, bwd_smem<TW, TH, PPT, LOSS>(rc), s>>>(
+        b, ws->ranges, vals, ws->rect, ws->rec, rc, ws->g2d, ws->counters + kCntTilesBwd, ws->stats, ws->red,
+        ws->order, ws->fb_state, ws->fb, (uint32_t)ws->max_tiles);
     return cudaGetLastError();
 }
 
@@ -1283,6 +1512,17 @@ static cudaError_t bwd_train_hdr_full(const BatchDev& b, const RasterDev& rc, gs
         return cudaErrorInvalidValue;                                                         \
     }
 
+template <int TW, int TH, int PPT>
+static cudaError_t bwd_grid_t(const RasterDev& rc, uint32_t tiles, int* grid) {
+    return bwd_grid<TW, TH, PPT, kLossHdr>(rc, tiles, grid);
+}
+
+static int bwd_grid_hint(const RasterDev& rc, uint32_t tiles) {
+    int g = 0;
+    auto f = [&]() -> cudaError_t { GSC_TILE_DISPATCH(bwd_grid_t, rc, tiles, &g) };
+    return f() == cudaSuccess ? g : 0;
+}
+
 cudaError_t launch_render(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
                           cudaStream_t s) {
     PhaseScope ph(kPhRender, s, 1);
@@ -1292,12 +1532,13 @@ cudaError_t launch_render(const BatchDev& b, const RasterDev& rc, gsc_workspace*
 // per view: the sum of its tiles' loss partials (in a fixed order, FP64) / k
 constexpr int kViewLossThreads = 1024;
 __global__ void __launch_bounds__(kViewLossThreads) k_view_loss(const __grid_constant__ BatchDev b,
-                                                                const float* __restrict__ tile_loss) {
+                                                                const float* __restrict__ tile_loss, int slots) {
     __shared__ double sm[32];
     const ViewDev& vw = b.v[blockIdx.x];
-    const uint32_t n = (uint32_t)vw.tiles_x * (uint32_t)vw.tiles_y;
+    // `slots` partials per tile
+    const uint32_t n = (uint32_t)slots * (uint32_t)vw.tiles_x * (uint32_t)vw.tiles_y;
     double acc = 0.0;
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) acc += (double)tile_loss[vw.tile_off + i];
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) acc += (double)tile_loss[(size_t)slots * vw.tile_off + i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
     if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
@@ -1350,7 +1591,7 @@ cudaError_t launch_train(const BatchDev& b, const RasterDev& rc, gsc_workspace* 
     }
     if (e == cudaSuccess) {
         PhaseScope ph(kPhLoss, s, 1);
-        k_view_loss<<<b.nviews, kViewLossThreads, 0, s>>>(b, ws->red);
+        k_view_loss<<<b.nviews, kViewLossThreads, 0, s>>>(b, ws->red, loss_slots(rc.tile_w * rc.tile_h / rc.ppt));
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return e;

@@ -269,3 +269,52 @@ def test_frozen_differences_equal_the_backward_for_every_parameter(orc):
         assert gmax > 0, s
         err = np.abs(fd[m] - an[m])
         assert (err <= 2e-4 * np.maximum(np.abs(an[m]), 1e-3 * gmax) + 1e-10).all(), (s, err.max(), gmax)
+
+
+def test_gradient_term_magnitudes(orc):
+    """render_backward_terms: the same gradient as render_backward; per
+    Gaussian, the absolute sums bound the 2D gradient (triangle inequality)
+    and equal it where one term contributes; the term counts are the
+    composited pairs of the frozen per-pixel lists."""
+    p = synth.gaussians(300, 41)
+    cam = synth.orbit_camera(40, 32, 25.0)
+    dl = np.random.default_rng(3).uniform(-1, 1, (3, 32, 40))
+    g_ref, g2_ref = orc.render_backward(p, cam, dl, CFG)
+    g, g2, a2, nterm = orc.render_backward_terms(p, cam, dl, CFG)
+    # the FP64 sums take their terms in the order the threads reach them
+    np.testing.assert_allclose(g, g_ref, rtol=1e-11, atol=1e-13 * np.abs(g_ref).max())
+    np.testing.assert_allclose(g2, g2_ref, rtol=1e-11, atol=1e-13 * np.abs(g2_ref).max())
+    assert np.all(a2 >= np.abs(g2) * (1 - 1e-12))
+    lists = orc.FrozenLists(p, cam, CFG)
+    counts = np.bincount(lists.g[:lists.offsets[-1]], minlength=len(p))
+    np.testing.assert_array_equal(nterm, counts)
+    # one pixel: every Gaussian contributes one term, so the sums are exact
+    _, g21, a21, n1 = orc.render_backward_terms(p, cam, dl[:, 16:17, 20:21], CFG, window=(20, 16, 1, 1))
+    one = n1 == 1
+    assert one.sum() > 3 and n1.max() == 1
+    np.testing.assert_allclose(a21[one], np.abs(g21[one]), rtol=1e-12, atol=0)
+    # |J a| <= |J| |a| for the packed gradient
+    bound = orc.grad_abs_map(p, cam, a2, CFG)
+    assert np.all(np.abs(g) <= bound * (1 + 1e-9) + 1e-300)
+    assert np.all(bound[nterm == 0] == 0.0)
+
+
+def test_grad_abs_map_closed_form_columns(orc):
+    """Columns of the 2D-record-to-parameter Jacobian whose form is plain:
+    dL/dmx reaches the mean through the pinhole projection only
+    (d mx / d t = (fx / tz, 0, -fx tx / tz^2), camera rotation identity), the
+    opacity-logit record reaches slot 3 alone, and the colour records reach
+    the colour slots one to one."""
+    cam = _axis_cam()
+    p = _one([0.8, 0.3, 1.2], [math.log(0.06)] * 3, [0.9, 0.1, -0.2, 0.3], 0.2, [0.4, 0.5, 0.6])
+    tx, tz = float(p[0, 0]) - 0.5, float(p[0, 2]) + 1.0
+    assert np.allclose(np.asarray(cam.R, np.float64), np.eye(3))
+    for k, want in [(0, {0: cam.fx / tz, 2: cam.fx * abs(tx) / tz ** 2}), (5, {3: 1.0}),
+                    (6, {12: 1.0}), (7, {13: 1.0}), (8, {14: 1.0})]:
+        m = np.zeros((1, 9))
+        m[0, k] = 2.0
+        out = orc.grad_abs_map(p, cam, m, CFG)[0]
+        expect = np.zeros(16)
+        for j, v in want.items():
+            expect[j] = 2.0 * v
+        np.testing.assert_allclose(out, expect, rtol=1e-9, atol=1e-12)
