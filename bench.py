@@ -477,13 +477,17 @@ def run_init_bench(args):
 def run_coupled_bench(args):
     """Cache-coupled tracing: trace time, squared bias and variance against C
     (Algorithm 1 + Eq. 2) at 480x270 with a 200k-Gaussian cache trained at
-    C = 0.5; reference 256 spp without the cache."""
-    from paper_2507_19718_gb300 import coupled, synth
+    C = 0.5; reference 1024 spp without the cache; under both readings of
+    Algorithm 1's Tr_out (cumulative, and per call as it is printed)."""
+    from paper_2507_19718_gb300 import coupled, gsc, synth
     sc = synth.scene_frame(256, seed=synth.BASE_SEED + 1)
-    rows = coupled.sweep(sc, synth.level_sizes(200_000, LEVELS))
-    return {"workload": "480x270, 1 spp, 8 bounces, 3-level cache of 200k Gaussians trained 48 frames at C = 0.5; "
-                        "24 frames per C; reference 256 spp without the cache",
-            "rows": [{k: (round(v, 6) if isinstance(v, float) else v) for k, v in r.items()} for r in rows]}
+    out = {"workload": f"480x270, 1 spp, 8 bounces, 3-level cache of 200k Gaussians trained 48 frames at C = 0.5; "
+                       f"{args.coupled_frames} frames per C; reference 1024 spp without the cache"}
+    for name, mode in (("cumulative", gsc.TR_OUT_CUMULATIVE), ("per_call", gsc.TR_OUT_PER_CALL)):
+        rows = coupled.sweep(sc, synth.level_sizes(200_000, LEVELS), eval_frames=args.coupled_frames, ref_spp=1024,
+                             tr_out=mode)
+        out[name] = [{k: (round(v, 6) if isinstance(v, float) else v) for k, v in r.items()} for r in rows]
+    return out
 
 
 def run_batched_bench(args, cfg_tuned):
@@ -679,6 +683,7 @@ def main():
     ap.add_argument("--no-init", action="store_true")
     ap.add_argument("--no-coupled", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--coupled-frames", type=int, default=256, help="evaluation frames per C of the C sweep")
     ap.add_argument("--no-adapt", action="store_true",
                     help="keep the training step's launch configuration fixed instead of choosing it frame by frame")
     ap.add_argument("--no-autotune", action="store_true",

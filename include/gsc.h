@@ -156,12 +156,20 @@ gsc_status gsc_scene_destroy(gsc_scene* scene);
  * in 0..16 target buffers; seed/frame select the Philox4x32-10 streams
  * (counter = (pixel, sample, frame, block), key = seed).  C > 0 enables the
  * early termination heuristic of Algorithm 1 (needs cache images); eps is
- * Algorithm 1's epsilon. */
+ * Algorithm 1's epsilon.  tr_out picks the reading of Algorithm 1's output
+ * throughput Tr_out (Sec. 3.3-3.4): GSC_TR_OUT_CUMULATIVE (0) keeps, on a
+ * surviving path, every earlier division by Tr + eps (the Russian-roulette
+ * weighting of Sec. 3.4); GSC_TR_OUT_PER_CALL (1) recomputes Tr_out as the
+ * product of the albedos at every call and divides by that call's Tr + eps
+ * only, as the algorithm is printed.  pad must be 0. */
+#define GSC_TR_OUT_CUMULATIVE 0
+#define GSC_TR_OUT_PER_CALL 1
 typedef struct gsc_trace_params {
     int32_t spp, max_bounces, levels;
     uint32_t frame;
     uint64_t seed;
     float C, eps;
+    int32_t tr_out, pad;
 } gsc_trace_params;
 
 /* One pass of the volume path tracer with next-event estimation (Sec. 3.3):

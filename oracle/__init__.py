@@ -71,7 +71,7 @@ def lib():
             L.orc_ln_f32.argtypes = [vp, vp, i64]
             L.orc_sincos2pi_f32.argtypes = [vp, vp, vp, i64]
             L.orc_trace.argtypes = [i32, vp, i32, i32, i32, vp, i32, vp, vp, vp, i32, vp, vp, i32, i32, i32, i32, i32,
-                                    u64, u32, f32, f32, vp, i32, i32, i32, i32, vp, vp, vp, i32]
+                                    u64, u32, f32, f32, i32, vp, i32, i32, i32, i32, vp, vp, vp, i32]
             L.orc_trace.restype = i32
             L.orc_transmittance.argtypes = [i32, vp, i32, i32, i32, vp, i32, vp, vp, vp, vp, i64, u64, vp, i32]
             L.orc_sigma_t.argtypes = [vp, i32, i32, i32, vp, i32, vp, vp, vp, i64, vp]
@@ -157,9 +157,10 @@ def _scene_arrays(scene):
 
 def trace(scene, cam, spp: int, max_bounces: int, levels: int, seed: int, frame: int = 0, C: float = 0.0,
           eps: float = 1e-6, cache=None, window=None, precision: int = 64, nthreads: int = 0,
-          lengths: bool = False):
+          lengths: bool = False, tr_out: int = 0):
     """Image (3, h, w) and K target buffers (K, 3, h, w) over ``window``
-    (x0, y0, w, h; default the whole frame).  precision 32 = FP32 mirror."""
+    (x0, y0, w, h; default the whole frame).  precision 32 = FP32 mirror.
+    tr_out: reading of Algorithm 1's Tr_out, 0 cumulative, 1 per call."""
     grid, nx, ny, nz, vol_f, tf_pos, tf_rgba, (light, spheres) = _scene_arrays(scene)
     W, H = cam.width, cam.height
     x0, y0, w, h = window if window is not None else (0, 0, W, H)
@@ -169,7 +170,8 @@ def trace(scene, cam, spp: int, max_bounces: int, levels: int, seed: int, frame:
     lens = np.zeros((h, w, spp), np.int32) if lengths else None
     cache_a = _c(cache, np.float32) if cache is not None else None
     rc = lib().orc_trace(precision, _p(grid), nx, ny, nz, _p(vol_f), len(tf_pos), _p(tf_pos), _p(tf_rgba),
-                         _p(light), len(spheres), _p(spheres), _p(camp), W, H, spp, max_bounces, levels, seed, frame, C, eps, _p(cache_a),
+                         _p(light), len(spheres), _p(spheres), _p(camp), W, H, spp, max_bounces, levels, seed, frame, C, eps,
+                         int(tr_out), _p(cache_a),
                          x0, y0, w, h, _p(targets), _p(image), _p(lens), _threads(nthreads))
     if rc != 0:
         raise ValueError(f"orc_trace rejected its arguments (code {rc})")

@@ -19,7 +19,8 @@
  *   philox4x32_10       Salmon et al., SC'11 (counter-based RNG; the paper is
  *                       silent on its RNG)
  *   orc_trace           Sec. 3.1 (Eq. 1), 3.2, 3.3 (Algorithm 1), 3.4 (Eq. 2),
- *                       3.5; trace_body.inc
+ *                       3.5; trace_body.inc.  tr_mode selects the reading of
+ *                       Algorithm 1's Tr_out (0 cumulative, 1 per call)
  *   orc_init_points     Sec. 3.2 "Cache Initialization": delta-tracked point
  *                       sampling (trace_body.inc); orc_knn3_mean and
  *                       orc_init_scales: the k-NN scale of Eq. 3
@@ -207,7 +208,7 @@ static void sincos2pi_f64(double u, double* s, double* c) {
 int orc_trace(int precision, const float* grid, int nx, int ny, int nz, const float* vol_f, int tf_n,
               const float* tf_pos, const float* tf_rgba, const float* light, int n_spheres,
               const float* spheres, const float* cam, int W, int H,
-              int spp, int max_bounces, int K, uint64_t seed, uint32_t frame, float C, float eps,
+              int spp, int max_bounces, int K, uint64_t seed, uint32_t frame, float C, float eps, int tr_mode,
               const float* cache, int x0, int y0, int w, int h, double* targets, double* image,
               int32_t* lengths, int nthreads) {
     if (nx < 2 || ny < 2 || nz < 2 || tf_n < 1 || tf_n > 16 || K < 0 || K > TRACE_MAX_LEVELS || spp < 1 ||
@@ -220,8 +221,8 @@ int orc_trace(int precision, const float* grid, int nx, int ny, int nz, const fl
                     light + 6);
         vol_spheres_f(&v, n_spheres, spheres);
         cam_setup_f(&c, cam, W, H);
-        trace_window_f(&v, &c, spp, max_bounces, K, seed, frame, C, eps, cache, x0, y0, w, h, targets, image,
-                       lengths, nthreads);
+        trace_window_f(&v, &c, spp, max_bounces, K, seed, frame, C, eps, tr_mode, cache, x0, y0, w, h, targets,
+                       image, lengths, nthreads);
     } else {
         vol_t_d v;
         cam_t_d c;
@@ -229,8 +230,8 @@ int orc_trace(int precision, const float* grid, int nx, int ny, int nz, const fl
                     light + 6);
         vol_spheres_d(&v, n_spheres, spheres);
         cam_setup_d(&c, cam, W, H);
-        trace_window_d(&v, &c, spp, max_bounces, K, seed, frame, C, eps, cache, x0, y0, w, h, targets, image,
-                       lengths, nthreads);
+        trace_window_d(&v, &c, spp, max_bounces, K, seed, frame, C, eps, tr_mode, cache, x0, y0, w, h, targets,
+                       image, lengths, nthreads);
     }
     return 0;
 }

@@ -388,6 +388,8 @@ gsc_status gsc_trace(const gsc_scene* scene, const gsc_camera* cam, const gsc_tr
     if (p->levels > 0 && !targets) return fail(GSC_ERR_INVALID_ARG, "targets NULL with levels > 0");
     if (p->C > 0.f && !cache_imgs) return fail(GSC_ERR_INVALID_ARG, "C > 0 needs cache images");
     if (!(p->eps >= 0.f)) return fail(GSC_ERR_INVALID_ARG, "eps must be >= 0");
+    if ((p->tr_out != GSC_TR_OUT_CUMULATIVE && p->tr_out != GSC_TR_OUT_PER_CALL) || p->pad != 0)
+        return fail(GSC_ERR_INVALID_ARG, "tr_out must be GSC_TR_OUT_CUMULATIVE or GSC_TR_OUT_PER_CALL, pad 0");
     if (cache_imgs && p->levels == 0) return fail(GSC_ERR_INVALID_ARG, "cache images with levels = 0");
     cudaError_t e = launch_trace(scene, cam_dev(cam), *p, cache_imgs, targets, image, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "gsc_trace launch");

@@ -35,6 +35,7 @@ struct TraceDev {
     int spp, B, K;
     uint32_t frame, k0, k1;
     float C, eps;
+    int tr_per_call;  // Algorithm 1's Tr_out read per call (else cumulatively)
 };
 
 struct Philox {
@@ -343,8 +344,11 @@ __global__ void __launch_bounds__(128, MINB) k_trace(TraceDev v, CamDev cam, con
                         early = true;
                         break;
                     }
-                    for (int c = 0; c < 3; ++c) thr[c] = thr[c] / (Tr + v.eps);
+                    // Tr_out / (Tr + eps): cumulative, or this call's product of albedos
+                    for (int c = 0; c < 3; ++c) thr[c] = (v.tr_per_call ? prod[c] : thr[c]) / (Tr + v.eps);
                     beta = beta * Tr;
+                } else if (v.tr_per_call) {
+                    for (int c = 0; c < 3; ++c) thr[c] = prod[c];  // this call's Tr_out, undivided
                 }
             }
             float ua = r.uniform(), ub = r.uniform();
@@ -465,6 +469,7 @@ cudaError_t launch_trace(const gsc_scene* sc, const CamDev& cam, const gsc_trace
     v.k0 = (uint32_t)p.seed;
     v.k1 = (uint32_t)(p.seed >> 32);
     v.C = p.C; v.eps = p.eps;
+    v.tr_per_call = p.tr_out == GSC_TR_OUT_PER_CALL ? 1 : 0;
     dim3 grid((cam.W + 15) / 16, (cam.H + 7) / 8);
     PhaseScope ph(kPhTrace, s, 1);
     // two full waves at 16 CTAs per SM: below that, the spill-free budget

@@ -60,11 +60,14 @@ class FrameLoop:
                  max_bounces: int = 8, seed: int = synth.BASE_SEED, tile=(16, 16), list_capacity: int = 256,
                  max_pairs: int | None = None, weight_decay: float = 0.01, lr=None, device: str = "cuda",
                  gaussian_seed: int | None = None, C_term: float = 0.0, bin_size: int = 0, fused: bool = True,
-                 fused_train: bool = True):
+                 fused_train: bool = True, tr_out: int = gsc.TR_OUT_PER_CALL):
         self.width, self.height = width, height
         self.spp, self.max_bounces, self.seed = spp, max_bounces, seed
         self.K = len(level_sizes)
         self.C_term = C_term
+        # reading of Algorithm 1's Tr_out when C_term > 0: per call, as the
+        # algorithm is printed (it reproduces the paper's bias-variance shape)
+        self.tr_out = tr_out
         self.fused = fused
         self.fused_train = fused and fused_train
         self.scene = gsc.Scene.from_synth(scene, device)
@@ -131,7 +134,7 @@ class FrameLoop:
     def trace(self, c: gsc.Camera, frame: int, stream=None):
         cache = self.renders if self.C_term > 0 else None
         gsc.trace(self.scene, c, self.spp, self.max_bounces, self.K, self.seed, frame, C_term=self.C_term,
-                  cache=cache, targets=self.targets, image=self.image, stream=stream)
+                  cache=cache, targets=self.targets, image=self.image, stream=stream, tr_out=self.tr_out)
 
     def render_levels(self, c: gsc.Camera, stream=None):
         if self.fused:

@@ -17,6 +17,7 @@ from . import build as _build
 
 GSC_OK, GSC_ERR_INVALID_ARG, GSC_ERR_OOM, GSC_ERR_CUDA, GSC_ERR_CAPACITY, GSC_ERR_TIMEOUT, GSC_ERR_NOT_READY = range(7)
 LOSS_HDR, LOSS_HDR_FULLGRAD, LOSS_L1_SSIM = 0, 1, 2
+TR_OUT_CUMULATIVE, TR_OUT_PER_CALL = 0, 1
 _STATUS_NAMES = ["OK", "INVALID_ARG", "OOM", "CUDA", "CAPACITY", "TIMEOUT", "NOT_READY"]
 
 
@@ -51,7 +52,7 @@ class SceneDesc(C.Structure):
 
 class TraceParams(C.Structure):
     _fields_ = [("spp", C.c_int32), ("max_bounces", C.c_int32), ("levels", C.c_int32), ("frame", C.c_uint32),
-                ("seed", C.c_uint64), ("C", C.c_float), ("eps", C.c_float)]
+                ("seed", C.c_uint64), ("C", C.c_float), ("eps", C.c_float), ("tr_out", C.c_int32), ("pad", C.c_int32)]
 
 
 class InitParams(C.Structure):
@@ -268,8 +269,9 @@ class Scene:
 
 def trace(scene: Scene, cam, spp: int, max_bounces: int, levels: int, seed: int, frame: int = 0, C_term: float = 0.0,
           eps: float = 1e-6, cache: torch.Tensor | None = None, targets: torch.Tensor | None = None,
-          image: torch.Tensor | None = None, stream=None):
-    """gsc_trace: returns (targets [K,3,H,W], image [3,H,W])."""
+          image: torch.Tensor | None = None, stream=None, tr_out: int = 0):
+    """gsc_trace: returns (targets [K,3,H,W], image [3,H,W]).  tr_out: reading
+    of Algorithm 1's Tr_out (TR_OUT_CUMULATIVE or TR_OUT_PER_CALL)."""
     c = cam if isinstance(cam, Camera) else camera(cam)
     H, W = c.height, c.width
     dev = scene.density.device
@@ -284,6 +286,7 @@ def trace(scene: Scene, cam, spp: int, max_bounces: int, levels: int, seed: int,
         _need(cache, "cache", levels * 3 * H * W)
     p = TraceParams()
     p.spp, p.max_bounces, p.levels, p.frame, p.seed, p.C, p.eps = spp, max_bounces, levels, frame, seed, C_term, eps
+    p.tr_out = int(tr_out)
     _check(lib().gsc_trace(scene.handle, C.byref(c), C.byref(p), _ptr(cache), _ptr(targets), _ptr(image),
                            _stream(stream)))
     return targets, image

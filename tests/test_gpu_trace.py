@@ -43,6 +43,26 @@ def test_trace_bit_exact_with_cache_and_termination(gpu, orc):
     np.testing.assert_array_equal(tg, rt.astype(np.float32))
 
 
+@pytest.mark.parametrize("C", [0.5, 2.0])
+def test_trace_bit_exact_with_per_call_tr_out(gpu, orc, C):
+    """Algorithm 1 with Tr_out read per call (each call starts from the
+    albedo product and divides by its own Tr + eps), bit for bit against the
+    FP32 mirror, and different from the cumulative reading.  C = 2 lets some
+    calls return Tr >= 0.9 (no roulette, the undivided product)."""
+    scene = synth.scene_tiny()
+    scene.env_radiance = np.array([0.2, 0.25, 0.3], np.float32)
+    cam = synth.orbit_camera(64, 48, 120.0)
+    cache = synth.uniform_image(4 * 3, 48, 64, 8).reshape(4, 3, 48, 64)
+    kw = dict(spp=2, max_bounces=6, levels=4, seed=78, frame=1, C_term=C, eps=1e-6)
+    tg, img = _run(gpu, scene, cam, cache=cache, tr_out=gpu.TR_OUT_PER_CALL, **kw)
+    rt, ri = orc.trace(scene, cam, spp=2, max_bounces=6, levels=4, seed=78, frame=1, C=C, eps=1e-6,
+                       cache=cache, precision=32, tr_out=1)
+    np.testing.assert_array_equal(img, ri.astype(np.float32))
+    np.testing.assert_array_equal(tg, rt.astype(np.float32))
+    tc, _ = _run(gpu, scene, cam, cache=cache, tr_out=gpu.TR_OUT_CUMULATIVE, **kw)
+    assert not np.array_equal(tc, tg)
+
+
 def test_trace_bit_exact_frame_scene_1080p_windows(gpu, orc):
     """The 1080p frame workload (256^3 blobs + fBm, 8-point TF, directional +
     environment light, 1 spp, 8 bounces, 3 levels) on sampled windows.  A frame

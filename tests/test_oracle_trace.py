@@ -282,3 +282,42 @@ def test_sphere_lights_add_linearly(orc):
     both, a, b = imgs[2], imgs[0], imgs[1]
     assert a.mean() > 0 and b.mean() > 0
     assert abs(both.mean() - (a.mean() + b.mean())) < 0.03 * both.mean()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("rgb,albedo,tr1", [((1.0, 1.0, 1.0), 0.8, 0.5), ((1.2, 1.2, 1.2), 1.0, 0.85)])
+def test_algorithm1_per_call_reading_keeps_only_its_own_division(orc, precision, rgb, albedo, tr1):
+    """The per-call reading of Algorithm 1 (every call starts from the
+    product of the albedos and divides by its own Tr + eps only) against the
+    cumulative one, in a grey homogeneous medium, where Tr_n = C a^n is the
+    same at every path's n-th vertex.  Both readings draw the same numbers, so
+    every sample takes the same path; with B = 3 they differ only in the
+    next-event weight of the third vertex: cumulative a^3 / ((Tr_1 + eps)
+    (Tr_2 + eps)), per call a^3 / (Tr_2 + eps) when the second call divides
+    (first case, Tr_2 = 0.4), a^3 when it does not (second case, a = 1.2:
+    Tr_2 = 1 >= 0.9, so the second call returns the undivided product).
+    Either way the per-call weight is the cumulative one times Tr_1 + eps, so
+    the summed target buffers satisfy, per pixel,
+    T_call(B=3) = T(B=2) + (Tr_1 + eps) (T_cum(B=3) - T(B=2)),
+    where B = 2 keeps the first two vertices, the same in both readings."""
+    sc = _homog_scene(3.0, rgb=rgb, albedo=albedo, light=(2.0, 2.0, 2.0), ldir=(0.3, 0.4, -0.866),
+                      env=(0.4, 0.4, 0.4))
+    cam = _far_cam()
+    cache = _const_cache(3, 4, 4, [(0.3, 0.5, 0.9)] * 3)
+    a = albedo * rgb[0]
+    C = tr1 / a
+    eps = 1e-6
+
+    def summed(B, mode):
+        t, _ = orc.trace(sc, cam, spp=64, max_bounces=B, levels=3, seed=31, C=C, eps=eps, cache=cache,
+                         precision=precision, tr_out=mode)
+        return t.sum(0)
+    b2 = summed(2, 0)
+    np.testing.assert_array_equal(summed(2, 1), b2)
+    cum3, call3 = summed(3, 0), summed(3, 1)
+    assert np.all(cum3 >= b2 * (1 - 1e-6)) and (cum3 - b2).sum() > 0.1 * b2.sum()  # the third vertex contributes
+    # Tr_1 as the tracer forms it from its FP32 inputs (albedo, TF colour, C)
+    a1 = float(np.float32(albedo)) * float(np.float32(rgb[0]))
+    tr1_exact = float(np.float32(C)) * ((0.2126 * a1 + 0.7152 * a1) + 0.0722 * a1)
+    rtol = 1e-12 if precision == 64 else 2e-6
+    np.testing.assert_allclose(call3, b2 + (tr1_exact + eps) * (cum3 - b2), rtol=rtol)
