@@ -11,7 +11,11 @@ Passages followed (Bauer et al., "GSCache"):
   trace              Sec. 3.1 Eq. 1, Sec. 3.2, Sec. 3.3 + Algorithm 1,
                      Sec. 3.4 Eq. 2, Sec. 3.5 (intermediate path buffers)
   project / render   Sec. 3.1 (Gaussian splatting of each cache level)
-  render_backward    Sec. 3.5 ("inverse splatting step")
+  render_backward    Sec. 3.5 ("inverse splatting step"); render_backward_terms,
+                     project_backward and grad_abs_map for the rounding bounds
+                     of an FP32 implementation
+  render_leaves,     the same with every decision within 2e-4 of its
+  render_backward_bounds  threshold taken both ways
   init_*             Sec. 3.2 "Cache Initialization" and Eq. 3
   FrozenLists        the same render with its threshold decisions held fixed,
                      for central differences of the backward at 1M Gaussians
@@ -83,6 +87,12 @@ def lib():
             L.orc_render_backward_ex.argtypes = [i64, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, vp, i32]
             L.orc_render_backward_ex.restype = i32
             L.orc_grad_abs_map.argtypes = [i64, vp, vp, vp, vp, vp, i32]
+            L.orc_render_leaves.argtypes = [i64, vp, vp, vp, i32, i32, i32, i32, i32, vp, vp, i32]
+            L.orc_render_leaves.restype = i32
+            L.orc_render_backward_bounds.argtypes = [i64, vp, vp, vp, i32, i32, i32, i32, vp, i32, vp, vp, vp, vp,
+                                                     vp, i32]
+            L.orc_render_backward_bounds.restype = i32
+            L.orc_project_backward.argtypes = [i64, vp, vp, vp, vp, vp, i32]
             L.orc_render_lists.argtypes = [i64, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, i32]
             L.orc_render_lists.restype = i32
             L.orc_frozen_fd.argtypes = [i64, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, i32, vp, vp, f64, vp,
@@ -331,14 +341,64 @@ def render_backward_terms(params, cam, dL_dimage, cfg=None, window=None, nthread
 
 
 def grad_abs_map(params, cam, abs2d, cfg=None, nthreads: int = 0) -> np.ndarray:
-    """|J| m per Gaussian (N, 16): J the Jacobian of the packed parameter
-    gradient with respect to the 2D gradient record, m = abs2d (N, 9)."""
+    """Magnitude of the packed parameter gradient (N, 16) for 2D records of
+    magnitude abs2d (N, 9): the projection backward evaluated on absolute
+    values (it bounds |J a| for |a| <= abs2d, J the Jacobian, and the
+    intermediate values of the computation)."""
     params = _c(params, np.float32)
     m = _c(abs2d, np.float64)
     assert m.shape == (len(params), 9)
     out = np.zeros((len(params), 16), np.float64)
     lib().orc_grad_abs_map(len(params), _p(params), _p(cam.packed()), _p(_cfg(cfg)), _p(m), _p(out),
                            _threads(nthreads))
+    return out
+
+
+def render_leaves(params, cam, cfg=None, window=None, max_leaves: int = 64, nthreads: int = 0):
+    """Every value a pixel may take when its marginal compositing decisions
+    (alpha_min and T_min within the margin) go either way: leaves
+    (h, w, max_leaves, 3) and their count (h, w); -1 marks a pixel with more
+    than max_leaves.  One leaf where nothing is marginal: render's value."""
+    params = _c(params, np.float32)
+    x0, y0, w, h = window if window is not None else (0, 0, cam.width, cam.height)
+    leaves = np.zeros((h, w, max_leaves, 3), np.float64)
+    n = np.zeros((h, w), np.int32)
+    rc = lib().orc_render_leaves(len(params), _p(params), _p(cam.packed()), _p(_cfg(cfg)), x0, y0, w, h, max_leaves,
+                                 _p(leaves), _p(n), _threads(nthreads))
+    if rc:
+        raise MemoryError("orc_render_leaves")
+    return leaves, n
+
+
+def render_backward_bounds(params, cam, dL_dimage, cfg=None, window=None, max_leaves: int = 64, nthreads: int = 0):
+    """Bounds of the 2D gradient record over every way the marginal
+    decisions (alpha_min, T_min, alpha_max clamp) may go: lo2d, hi2d (N, 9),
+    the per-pixel largest absolute contributions summed (N, 9), the number of
+    contributing pixels (N,) and the leaves per pixel (h, w; -1 beyond
+    max_leaves)."""
+    params = _c(params, np.float32)
+    x0, y0, w, h = window if window is not None else (0, 0, cam.width, cam.height)
+    g = _c(dL_dimage, np.float64)
+    assert g.shape == (3, h, w)
+    n = len(params)
+    lo, hi, ab = (np.zeros((n, 9), np.float64) for _ in range(3))
+    nterm = np.zeros(n, np.int64)
+    nl = np.zeros((h, w), np.int32)
+    rc = lib().orc_render_backward_bounds(n, _p(params), _p(cam.packed()), _p(_cfg(cfg)), x0, y0, w, h, _p(g),
+                                          max_leaves, _p(lo), _p(hi), _p(ab), _p(nterm), _p(nl), _threads(nthreads))
+    if rc:
+        raise MemoryError("orc_render_backward_bounds")
+    return lo, hi, ab, nterm, nl
+
+
+def project_backward(params, cam, g2d, cfg=None, nthreads: int = 0) -> np.ndarray:
+    """The packed parameter gradient (N, 16) of 2D gradient records (N, 9)."""
+    params = _c(params, np.float32)
+    a = _c(g2d, np.float64)
+    assert a.shape == (len(params), 9)
+    out = np.zeros((len(params), 16), np.float64)
+    lib().orc_project_backward(len(params), _p(params), _p(cam.packed()), _p(_cfg(cfg)), _p(a), _p(out),
+                               _threads(nthreads))
     return out
 
 

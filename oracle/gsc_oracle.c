@@ -30,7 +30,17 @@
  *   orc_render          front-to-back alpha compositing of all Gaussians per
  *                       pixel (Sec. 3.1)
  *   orc_render_backward analytic gradient of orc_render (the "inverse
- *                       splatting step", Sec. 3.5)
+ *                       splatting step", Sec. 3.5); orc_render_backward_ex
+ *                       adds per Gaussian the summed absolute (pixel, term)
+ *                       contributions and their count, orc_project_backward
+ *                       its last step alone (2D record -> packed gradient)
+ *                       and orc_grad_abs_map that step on absolute values:
+ *                       the magnitudes that bound an FP32 evaluation's
+ *                       rounding
+ *   orc_render_leaves,  orc_render / orc_render_backward taken every way
+ *   orc_render_backward_bounds   the decisions within MARGIN_REL of a
+ *                       threshold can go (the results and gradient bounds a
+ *                       lower-precision implementation may reach)
  *   orc_loss_hdr        Sec. 3.6 "Loss", Eq. after Noise2Noise
  *   orc_loss_l1ssim     0.8 L1 + 0.2 (1 - SSIM), Wang et al. 2004 (not in the
  *                       paper; the 1M-Gaussian differentiation workload)
@@ -41,7 +51,8 @@
  * images) is pinned by the C -> infinity identity and by closed forms in a
  * homogeneous medium with constant cache images: C -> 0+, one roulette
  * survival then an escape from a dense half-space, and no roulette from
- * Tr = 0.9 up.
+ * Tr = 0.9 up; the per-call reading of Tr_out by its exact relation to the
+ * cumulative one when only the third vertex's weight differs.
  */
 #include <math.h>
 #include <stdint.h>
@@ -794,13 +805,86 @@ int orc_render_backward_ex(int64_t N, const float* params, const float* cam, con
 }
 
 /*
- * |J| m per Gaussian, with J the 16 x 9 Jacobian of the packed parameter
- * gradient with respect to the 2D gradient record (project_backward_one is
- * linear in the record; column k is its image of the k-th unit record) and
- * m = abs2d: an upper bound on the parameter-gradient magnitude that record
- * errors of relative size e (per component) can cause, e |J| m.  out: N x 16
- * (overwritten); Gaussians with a zero m row get zeros.
+ * Magnitude of the projection backward (project_backward_one) for a record
+ * of magnitudes m >= 0: the same operations with every operand replaced by
+ * its absolute value and every difference by a sum.  It bounds |J a| for any
+ * record |a| <= m (J the record-to-packed-gradient Jacobian), and it bounds
+ * the intermediate values too, so that u times it (times the number of
+ * operations on the way) bounds the rounding of a low-precision evaluation,
+ * including the cancellation of the quaternion gradient's radial part.
+ * out: N x 16 (overwritten); Gaussians with a zero m row get zeros.
  */
+static void project_backward_mag(const float* p, const rcam_t* c, const double* cfg, const double* m,
+                                 double* grad) {
+    proj_t pr;
+    proj_aux_t x;
+    project_one(p, c, cfg, &pr, &x);
+    if (!pr.visible) return;
+    const double A = fabs(x.A), B = fabs(x.B), Cc = fabs(x.Cc), det2 = x.det * x.det;
+    const double ga = m[2], gb = m[3], gc = m[4];
+    const double dA = (ga * Cc * Cc + gb * B * Cc + gc * B * B) / det2;
+    const double dB = (ga * 2 * B * Cc + gb * (A * Cc + B * B) + gc * 2 * A * B) / det2;
+    const double dC = (ga * B * B + gb * A * B + gc * A * A) / det2;
+    double T0[3], T1[3], Sg[9], G[9];
+    for (int k = 0; k < 3; ++k) { T0[k] = fabs(x.Tm[k]); T1[k] = fabs(x.Tm[3 + k]); }
+    for (int k = 0; k < 9; ++k) Sg[k] = fabs(x.Sig[k]);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) G[3 * i + j] = dA * T0[i] * T0[j] + dB * T0[i] * T1[j] + dC * T1[i] * T1[j];
+    double ST0[3], ST1[3];
+    for (int k = 0; k < 3; ++k) {
+        ST0[k] = Sg[3 * k] * T0[0] + Sg[3 * k + 1] * T0[1] + Sg[3 * k + 2] * T0[2];
+        ST1[k] = Sg[3 * k] * T1[0] + Sg[3 * k + 1] * T1[1] + Sg[3 * k + 2] * T1[2];
+    }
+    double dTm[6];
+    for (int k = 0; k < 3; ++k) {
+        dTm[k] = 2 * dA * ST0[k] + dB * ST1[k];
+        dTm[3 + k] = dB * ST0[k] + 2 * dC * ST1[k];
+    }
+    double dJ[6];
+    for (int r = 0; r < 2; ++r)
+        for (int mm = 0; mm < 3; ++mm) {
+            double acc = 0;
+            for (int k = 0; k < 3; ++k) acc += dTm[3 * r + k] * fabs(c->R[3 * mm + k]);
+            dJ[3 * r + mm] = acc;
+        }
+    const double tx = fabs(x.t[0]), ty = fabs(x.t[1]), tz = fabs(x.t[2]);
+    const double tz2 = tz * tz, tz3 = tz2 * tz, fx = fabs(c->fx), fy = fabs(c->fy);
+    double dt[3] = {0, 0, 0};
+    dt[0] += dJ[2] * fx / tz2 + m[0] * fx / tz;
+    dt[1] += dJ[5] * fy / tz2 + m[1] * fy / tz;
+    dt[2] += dJ[0] * fx / tz2 + dJ[2] * 2 * fx * tx / tz3 + dJ[4] * fy / tz2 + dJ[5] * 2 * fy * ty / tz3 +
+             m[0] * fx * tx / tz2 + m[1] * fy * ty / tz2;
+    for (int k = 0; k < 3; ++k)
+        grad[k] += fabs(c->R[k]) * dt[0] + fabs(c->R[3 + k]) * dt[1] + fabs(c->R[6 + k]) * dt[2];
+    double dM[9];
+    for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) {
+            double acc = 0;
+            for (int j = 0; j < 3; ++j) acc += (G[3 * k + j] + G[3 * j + k]) * fabs(x.M[3 * j + l]);
+            dM[3 * k + l] = acc;
+        }
+    double dR[9];
+    for (int l = 0; l < 3; ++l) {
+        double ds = 0;
+        for (int k = 0; k < 3; ++k) {
+            ds += dM[3 * k + l] * fabs(x.Rq[3 * k + l]);
+            dR[3 * k + l] = dM[3 * k + l] * x.s[l];
+        }
+        grad[4 + l] += ds * x.s[l];
+    }
+    const double w = fabs(x.qn[0]), qx = fabs(x.qn[1]), qy = fabs(x.qn[2]), qz = fabs(x.qn[3]);
+    double dq[4];
+    dq[0] = 2 * (qz * dR[1] + qy * dR[2] + qz * dR[3] + qx * dR[5] + qy * dR[6] + qx * dR[7]);
+    dq[1] = 2 * (qy * dR[1] + qz * dR[2] + qy * dR[3] + w * dR[5] + qz * dR[6] + w * dR[7]) + 4 * qx * (dR[4] + dR[8]);
+    dq[2] = 2 * (qx * dR[1] + w * dR[2] + qx * dR[3] + qz * dR[5] + w * dR[6] + qz * dR[7]) + 4 * qy * (dR[0] + dR[8]);
+    dq[3] = 2 * (w * dR[1] + qx * dR[2] + w * dR[3] + qy * dR[5] + qx * dR[6] + qy * dR[7]) + 4 * qz * (dR[0] + dR[4]);
+    const double dot = w * dq[0] + qx * dq[1] + qy * dq[2] + qz * dq[3];
+    const double qa[4] = {w, qx, qy, qz};
+    for (int k = 0; k < 4; ++k) grad[8 + k] += (dq[k] + qa[k] * dot) / x.qnorm;
+    grad[3] += m[5];
+    for (int k = 0; k < 3; ++k) grad[12 + k] += m[6 + k];
+}
+
 void orc_grad_abs_map(int64_t N, const float* params, const float* cam, const double* cfg, const double* abs2d,
                       double* out, int nthreads) {
     rcam_t c;
@@ -812,14 +896,336 @@ void orc_grad_abs_map(int64_t N, const float* params, const float* cam, const do
         const double* m = abs2d + 9 * g;
         int any = 0;
         for (int k = 0; k < 9; ++k) any |= m[k] != 0.0;
-        if (!any) continue;
-        for (int k = 0; k < 9; ++k) {
-            if (m[k] == 0.0) continue;
-            double e[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, col[16] = {0};
-            e[k] = 1.0;
-            project_backward_one(params + 16 * g, &c, cfg, e, col);
-            for (int j = 0; j < 16; ++j) o[j] += fabs(col[j]) * m[k];
+        if (any) project_backward_mag(params + 16 * g, &c, cfg, m, o);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* marginal decisions: every way a lower-precision walk may take them       */
+
+/*
+ * The compositing decisions of a pixel (alpha >= alpha_min, T (1 - alpha) <
+ * T_min, and for gradients the alpha_max clamp) are taken in FP64 here.  An
+ * FP32 implementation evaluates alpha and T with relative errors far below
+ * MARGIN_REL, so it can take a decision the other way only where the FP64
+ * value lies within MARGIN_REL of its threshold.  walk_from follows the plain
+ * definition and, at every such marginal decision, both ways: each complete
+ * walk (a "leaf") is a result such an implementation may produce.  The
+ * leaves of a pixel are capped at max_leaves (the pixel is then flagged).
+ */
+typedef struct {
+    const proj_t* pr;
+    const int64_t* order;
+    int64_t V;
+    const double* cfg;
+    double px, py;
+    int grad;        /* also branch on the alpha_max clamp */
+    term_t* terms;   /* the composited terms of the walk in progress */
+    int64_t cap;
+    int nleaves, max_leaves, overflow;
+    void (*leaf)(void* ud, const double C[3], const term_t* terms, int64_t n);
+    void* ud;
+} walk_ctx;
+
+static void emit_leaf(walk_ctx* w, const double C[3], int64_t n) {
+    if (++w->nleaves > w->max_leaves) {
+        w->overflow = 1;
+        return;
+    }
+    w->leaf(w->ud, C, w->terms, n);
+}
+
+static void walk_from(walk_ctx* w, int64_t k, double T, const double C[3], int64_t n);
+
+/* composite term k with the given alpha and clamp state and walk on; or stop
+ * before it (T_min), or both when that decision is marginal */
+static void take_term(walk_ctx* w, int64_t k, double T, const double C[3], int64_t n, double alpha, double G,
+                      double dx, double dy, int clamped) {
+    if (w->overflow) return;
+    const double tmin = w->cfg[2];
+    const double Tn = T * (1.0 - alpha);
+    const int near = near_rel(Tn, tmin, MARGIN_REL);
+    if (Tn < tmin || near) emit_leaf(w, C, n);
+    if (Tn < tmin && !near) return;
+    if (n >= w->cap) {
+        w->overflow = 1;
+        return;
+    }
+    const proj_t* p = &w->pr[w->order[k]];
+    term_t* t = &w->terms[n];
+    t->g = w->order[k]; t->alpha = alpha; t->T = T; t->G = G; t->dx = dx; t->dy = dy; t->clamped = clamped;
+    double C2[3];
+    for (int ch = 0; ch < 3; ++ch) C2[ch] = C[ch] + p->col[ch] * alpha * T;
+    walk_from(w, k + 1, Tn, C2, n + 1);
+}
+
+/* term k taken, with its clamp as FP64 decides it and, for gradients, also
+ * the other way when araw is within the margin of alpha_max */
+static void take_alts(walk_ctx* w, int64_t k, double T, const double C[3], int64_t n, double araw, double G,
+                      double dx, double dy) {
+    const double amax = w->cfg[0];
+    const int clamped = araw >= amax;
+    take_term(w, k, T, C, n, clamped ? amax : araw, G, dx, dy, clamped);
+    if (w->grad && near_rel(araw, amax, MARGIN_REL)) take_term(w, k, T, C, n, clamped ? araw : amax, G, dx, dy, !clamped);
+}
+
+static void walk_from(walk_ctx* w, int64_t k, double T, const double C[3], int64_t n) {
+    const double amax = w->cfg[0], amin = w->cfg[1];
+    for (; k < w->V; ++k) {
+        if (w->overflow) return;
+        const proj_t* p = &w->pr[w->order[k]];
+        const double dx = w->px - p->mx, dy = w->py - p->my;
+        const double power = -0.5 * (p->a * dx * dx + p->c * dy * dy) - p->b * dx * dy;
+        if (power < p->lthr - 1e-3) continue;
+        const double G = exp(power), araw = p->op * G;
+        const double alpha = araw < amax ? araw : amax;
+        const int marg = near_rel(araw, amin, MARGIN_REL);
+        if (!(alpha >= amin)) {
+            if (marg) take_alts(w, k, T, C, n, araw, G, dx, dy);  /* FP64 drops it, FP32 may take it */
+            continue;
         }
+        if (marg) walk_from(w, k + 1, T, C, n);  /* FP64 takes it, FP32 may drop it */
+        take_alts(w, k, T, C, n, araw, G, dx, dy);
+        return;
+    }
+    emit_leaf(w, C, n);
+}
+
+typedef struct {
+    double* out;  /* max_leaves x 3 colours of the pixel */
+    int i;
+} leaf_colours;
+
+static void leaf_colour(void* ud, const double C[3], const term_t* terms, int64_t n) {
+    (void)terms; (void)n;
+    leaf_colours* lc = (leaf_colours*)ud;
+    for (int ch = 0; ch < 3; ++ch) lc->out[3 * lc->i + ch] = C[ch];
+    lc->i++;
+}
+
+/*
+ * Every result of the window's pixels an implementation may produce by taking
+ * marginal decisions either way: leaves (h x w x max_leaves x 3, pixel-major)
+ * and their number per pixel in nleaves (h x w; -1: more than max_leaves).
+ * Without marginal decisions a pixel has one leaf, orc_render's value.
+ */
+int orc_render_leaves(int64_t N, const float* params, const float* cam, const double* cfg, int x0, int y0, int w,
+                      int h, int max_leaves, double* leaves, int32_t* nleaves, int nthreads) {
+    rcam_t c;
+    rcam_setup(&c, cam);
+    proj_t* pr = (proj_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(proj_t));
+    int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    if (!pr || !order) { free(pr); free(order); return 2; }
+    const int64_t V = project_sorted(N, params, &c, cfg, pr, order, nthreads);
+    int bad = 0;
+#pragma omp parallel num_threads(nthreads)
+    {
+        const int64_t cap = 1 << 16;
+        term_t* terms = (term_t*)malloc(sizeof(term_t) * (size_t)cap);
+        if (!terms) {
+#pragma omp atomic write
+            bad = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int jj = 0; jj < h; ++jj) {
+            for (int ii = 0; ii < w; ++ii) {
+                if (!terms) continue;
+                const long p = (long)jj * w + ii;
+                leaf_colours lc = {leaves + (size_t)p * max_leaves * 3, 0};
+                walk_ctx wc = {pr, order, V, cfg, x0 + ii + 0.5, y0 + jj + 0.5, 0, terms, cap, 0, max_leaves, 0,
+                               leaf_colour, &lc};
+                const double C0[3] = {0, 0, 0};
+                walk_from(&wc, 0, 1.0, C0, 0);
+                nleaves[p] = wc.overflow ? -1 : wc.nleaves;
+            }
+        }
+        free(terms);
+    }
+    free(pr);
+    free(order);
+    return bad ? 2 : 0;
+}
+
+/* 2D gradient contributions (9 per term, the record of orc_render_backward)
+ * of one walk's terms for the pixel gradient gC */
+static void walk_terms_backward(const proj_t* pr, const float* params, const term_t* terms, int64_t n,
+                                const double gC[3], double* v9) {
+    double S[3] = {0, 0, 0};
+    for (int64_t k = n - 1; k >= 0; --k) {
+        const term_t* t = &terms[k];
+        const proj_t* q = &pr[t->g];
+        const float* pp = params + 16 * t->g;
+        double* v = v9 + 9 * k;
+        double dalpha = 0;
+        for (int ch = 0; ch < 3; ++ch) {
+            v[6 + ch] = pp[12 + ch] > 0.0f ? t->alpha * t->T * gC[ch] : 0.0;
+            dalpha += gC[ch] * (q->col[ch] * t->T - S[ch] / (1.0 - t->alpha));
+            S[ch] += q->col[ch] * t->alpha * t->T;
+        }
+        for (int j = 0; j < 6; ++j) v[j] = 0.0;
+        if (t->clamped) continue;
+        const double dpow = dalpha * t->alpha;
+        v[0] = dpow * (q->a * t->dx + q->b * t->dy);
+        v[1] = dpow * (q->b * t->dx + q->c * t->dy);
+        v[2] = dpow * (-0.5 * t->dx * t->dx);
+        v[3] = dpow * (-t->dx * t->dy);
+        v[4] = dpow * (-0.5 * t->dy * t->dy);
+        v[5] = dalpha * t->G * q->op * (1.0 - q->op);
+    }
+}
+
+typedef struct {
+    int64_t g;
+    int leaf;
+    double v[9];
+} leaf_row;
+
+typedef struct {
+    const proj_t* pr;
+    const float* params;
+    double gC[3];
+    leaf_row* rows;
+    int64_t nrows, caprows;
+    double* v9;  /* scratch: 9 per term */
+    int64_t capv;
+    int leaf, failed;
+} leaf_grads;
+
+static void leaf_grad(void* ud, const double C[3], const term_t* terms, int64_t n) {
+    (void)C;
+    leaf_grads* lg = (leaf_grads*)ud;
+    if (n > lg->capv) {
+        double* v = (double*)realloc(lg->v9, sizeof(double) * 9 * (size_t)n);
+        if (!v) { lg->failed = 1; return; }
+        lg->v9 = v;
+        lg->capv = n;
+    }
+    if (lg->nrows + n > lg->caprows) {
+        int64_t c = (lg->nrows + n) * 2;
+        leaf_row* r = (leaf_row*)realloc(lg->rows, sizeof(leaf_row) * (size_t)c);
+        if (!r) { lg->failed = 1; return; }
+        lg->rows = r;
+        lg->caprows = c;
+    }
+    walk_terms_backward(lg->pr, lg->params, terms, n, lg->gC, lg->v9);
+    for (int64_t k = 0; k < n; ++k) {
+        leaf_row* r = &lg->rows[lg->nrows++];
+        r->g = terms[k].g;
+        r->leaf = lg->leaf;
+        for (int j = 0; j < 9; ++j) r->v[j] = lg->v9[9 * k + j];
+    }
+    lg->leaf++;
+}
+
+static int row_cmp(const void* pa, const void* pb) {
+    const leaf_row* a = (const leaf_row*)pa;
+    const leaf_row* b = (const leaf_row*)pb;
+    return (a->g > b->g) - (a->g < b->g);
+}
+
+/*
+ * Bounds of the 2D gradient record over every way the window's marginal
+ * decisions may be taken: per Gaussian (N x 9, +=), lo2d and hi2d sum over
+ * the pixels the smallest and largest contribution among the pixel's leaves
+ * (0 where a leaf does not composite the Gaussian); abs2d the largest
+ * absolute contribution and nterm the number of contributing pixels (for the
+ * rounding bound of an FP32 sum, as in orc_render_backward_ex).  nleaves
+ * (h x w): leaves per pixel, -1 beyond max_leaves.  An implementation that
+ * takes each pixel's decisions one of these ways has its record, in exact
+ * arithmetic, in [lo2d, hi2d].
+ */
+int orc_render_backward_bounds(int64_t N, const float* params, const float* cam, const double* cfg, int x0, int y0,
+                               int w, int h, const double* dL_dimage, int max_leaves, double* lo2d, double* hi2d,
+                               double* abs2d, int64_t* nterm, int32_t* nleaves, int nthreads) {
+    rcam_t c;
+    rcam_setup(&c, cam);
+    proj_t* pr = (proj_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(proj_t));
+    int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    if (!pr || !order) { free(pr); free(order); return 2; }
+    const int64_t V = project_sorted(N, params, &c, cfg, pr, order, nthreads);
+    const long WH = (long)w * h;
+    int bad = 0;
+#pragma omp parallel num_threads(nthreads)
+    {
+        const int64_t cap = 1 << 16;
+        term_t* terms = (term_t*)malloc(sizeof(term_t) * (size_t)cap);
+        leaf_grads lg = {pr, params, {0, 0, 0}, NULL, 0, 0, NULL, 0, 0, 0};
+#pragma omp for schedule(dynamic, 1)
+        for (int jj = 0; jj < h; ++jj) {
+            for (int ii = 0; ii < w; ++ii) {
+                const long p = (long)jj * w + ii;
+                nleaves[p] = 0;
+                const double gC[3] = {dL_dimage[p], dL_dimage[WH + p], dL_dimage[2 * WH + p]};
+                if (!terms || (gC[0] == 0 && gC[1] == 0 && gC[2] == 0)) continue;
+                lg.gC[0] = gC[0]; lg.gC[1] = gC[1]; lg.gC[2] = gC[2];
+                lg.nrows = 0;
+                lg.leaf = 0;
+                walk_ctx wc = {pr, order, V, cfg, x0 + ii + 0.5, y0 + jj + 0.5, 1, terms, cap, 0, max_leaves, 0,
+                               leaf_grad, &lg};
+                const double C0[3] = {0, 0, 0};
+                walk_from(&wc, 0, 1.0, C0, 0);
+                if (wc.overflow || lg.failed) {
+                    nleaves[p] = -1;
+                    continue;
+                }
+                nleaves[p] = wc.nleaves;
+                const int L = wc.nleaves;
+                if (L > 1) qsort(lg.rows, (size_t)lg.nrows, sizeof(leaf_row), row_cmp);
+                for (int64_t r0 = 0; r0 < lg.nrows;) {
+                    int64_t r1 = r0 + 1;
+                    while (r1 < lg.nrows && lg.rows[r1].g == lg.rows[r0].g) ++r1;
+                    const int64_t g = lg.rows[r0].g;
+                    const int in_all = (int)(r1 - r0) == L;
+                    for (int j = 0; j < 9; ++j) {
+                        double lo = in_all ? lg.rows[r0].v[j] : 0.0, hi = lo, mag = 0.0;
+                        for (int64_t r = r0; r < r1; ++r) {
+                            const double x = lg.rows[r].v[j];
+                            lo = x < lo ? x : lo;
+                            hi = x > hi ? x : hi;
+                            mag = fabs(x) > mag ? fabs(x) : mag;
+                        }
+#pragma omp atomic
+                        lo2d[9 * g + j] += lo;
+#pragma omp atomic
+                        hi2d[9 * g + j] += hi;
+                        if (abs2d) {
+#pragma omp atomic
+                            abs2d[9 * g + j] += mag;
+                        }
+                    }
+                    if (nterm) {
+#pragma omp atomic
+                        nterm[g] += 1;
+                    }
+                    r0 = r1;
+                }
+            }
+        }
+        if (lg.failed || !terms) {
+#pragma omp atomic write
+            bad = 1;
+        }
+        free(lg.rows);
+        free(lg.v9);
+        free(terms);
+    }
+    free(pr);
+    free(order);
+    return bad ? 2 : 0;
+}
+
+/* the packed parameter gradient of 2D records g2d (N x 9), as the last step
+ * of orc_render_backward: grads (N x 16) += project_backward(g2d) */
+void orc_project_backward(int64_t N, const float* params, const float* cam, const double* cfg, const double* g2d,
+                          double* grads, int nthreads) {
+    rcam_t c;
+    rcam_setup(&c, cam);
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int64_t g = 0; g < N; ++g) {
+        const double* a9 = g2d + 9 * g;
+        int any = 0;
+        for (int k = 0; k < 9; ++k) any |= a9[k] != 0;
+        if (any) project_backward_one(params + 16 * g, &c, cfg, a9, grads + 16 * g);
     }
 }
 

@@ -11,25 +11,25 @@ The gradient is confined to a 64x64 crop so that the oracle can follow it:
 each level's target is its own render outside the crop (the HDR gradient is
 then exactly zero there) and the render plus seeded noise inside it.
 Checked, per level and launch configuration:
-- the image the step writes: bit-identical to gsc_cache_render's, and within
-  1e-4 of the oracle's render on the crop and on sampled windows (the ragged
-  bottom-right corner among them);
+- the image the step writes: bit-identical to gsc_cache_render's, and on the
+  crop and on sampled windows (the ragged bottom-right corner among them)
+  every pixel within 1e-4 of a result the oracle allows (its own, and each way
+  a decision within 2e-4 of a threshold can go);
 - the loss against the oracle's HDR loss of the GPU's own image (2e-6);
 - post-step p, m, v of every Gaussian the crop touches against the oracle's
   AdamW applied to the oracle's gradient: AdamW is monotone in the gradient
   for the moments used here (m = 0, v > 0 before the step), so the GPU value
-  must lie between the oracle's outputs at the two ends of the gradient bar,
-  widened by AdamW's own FP32 bound.  The bar is 1e-3 |g| plus the rounding
-  an FP32 sum of the gradient's terms may carry: with m the sum of the
-  absolute (pixel, term) contributions to the 2D record and n their number
-  (both from the oracle), (80 + 8 sqrt(n)) u |J| m, u = 2^-24, J the
-  record-to-parameter Jacobian -- 80 u for each term's own FP32 arithmetic and
-  the projection backward, 8 sqrt(n) u for eight standard deviations of the
-  rounding of an n-term sum taken in an arbitrary order (atomics);
+  must lie between the oracle's outputs at the two ends of the gradient's
+  bounds, widened by AdamW's own FP32 bound.  The gradient's bounds are the
+  oracle's over every way a marginal decision of a crop pixel can go, plus
+  1e-3 of their centre and the rounding an FP32 sum of the gradient's terms
+  may carry (tests/parity.py);
 - Gaussians the crop does not touch: the oracle's zero-gradient step.
 """
 import numpy as np
 import pytest
+
+from parity import assert_grad_within, grad_bounds, render_check
 
 from paper_2507_19718_gb300 import synth
 
@@ -65,22 +65,21 @@ def case(gpu, orc):
         R = gpu.cache_render(torch.from_numpy(p).cuda(), cam, gpu.raster_cfg(), ws)
         ws.status()
         R = R.cpu().numpy()
-        ref_crop, marg, ncon, _ = orc.render(p, cam, window=CROP, grad_margins=True)
+        _, _, ncon, _ = orc.render(p, cam, window=CROP)
         assert ncon.mean() > 20, ncon.mean()
         tgt = R.copy()
         noise = R[:, y0:y0 + ch, x0:x0 + cw] * rng.uniform(-0.25, 0.25, (3, ch, cw)) + \
             rng.uniform(0.0, 0.02, (3, ch, cw))
-        noise[:, marg] = 0.0  # a decision within the margin: no gradient through that pixel
         tgt[:, y0:y0 + ch, x0:x0 + cw] = (R[:, y0:y0 + ch, x0:x0 + cw] + noise).astype(np.float32)
         val, dl = orc.loss_hdr(R, tgt)
         outside = np.ones((3, H, W), bool)
         outside[:, y0:y0 + ch, x0:x0 + cw] = False
         assert np.all(dl[outside] == 0.0)
-        g_ref, _, a2d, nterm = orc.render_backward_terms(p, cam, dl[:, y0:y0 + ch, x0:x0 + cw], window=CROP)
-        fp32 = (80.0 + 8.0 * np.sqrt(nterm))[:, None] * 2.0 ** -24 * orc.grad_abs_map(p, cam, a2d)
+        g_mid, g_rad, bar, nl = grad_bounds(orc, p, cam, dl[:, y0:y0 + ch, x0:x0 + cw], window=CROP)
+        assert (nl > 1).sum() > 0  # marginal pixels are in the comparison
         m0 = np.zeros_like(p)
         v0 = rng.uniform(1e-8, 1e-5, p.shape).astype(np.float32)
-        out.append(dict(p=p, R=R, tgt=tgt, loss=val, g=g_ref, fp32=fp32, m0=m0, v0=v0, ref_crop=ref_crop, marg=marg))
+        out.append(dict(p=p, R=R, tgt=tgt, loss=val, g=g_mid, tol=g_rad + 1e-3 * np.abs(g_mid) + bar, m0=m0, v0=v0))
     return cam, out, ws
 
 
@@ -116,14 +115,11 @@ def test_train_step_matches_oracle_at_bench_scale(gpu, orc, case, launch):
         # the step's image is the forward's, bit for bit
         np.testing.assert_array_equal(image, L["R"], err_msg=f"level {k}")
         # ... and the oracle's render, on the crop and on sampled windows
-        crop_img = image[:, y0:y0 + ch, x0:x0 + cw].astype(np.float64)
-        err = np.abs(crop_img - L["ref_crop"])[:, ~L["marg"]]
-        assert L["marg"].mean() < 0.2 and err.max() <= 1e-4, (k, L["marg"].mean(), err.max())
+        render_check(orc, image[:, y0:y0 + ch, x0:x0 + cw], L["p"], cam, CROP, what=f"level {k} crop")
         for (wx, wy, ww, wh) in WINDOWS:
             ww, wh = min(ww, W - wx), min(wh, H - wy)
-            ref, marg, _, _ = orc.render(L["p"], cam, window=(wx, wy, ww, wh))
-            e = np.abs(image[:, wy:wy + wh, wx:wx + ww] - ref)[:, ~marg]
-            assert marg.mean() < 0.2 and e.max() <= 1e-4, (k, (wx, wy), e.max())
+            render_check(orc, image[:, wy:wy + wh, wx:wx + ww], L["p"], cam, (wx, wy, ww, wh),
+                         what=f"level {k} {(wx, wy)}")
         # the loss of the GPU's own image
         ref_loss, _ = orc.loss_hdr(image, L["tgt"])
         assert float(loss) == pytest.approx(ref_loss, rel=2e-6), k
@@ -134,7 +130,7 @@ def test_train_step_matches_oracle_at_bench_scale(gpu, orc, case, launch):
         g = L["g"]
         touched = np.abs(g).sum(1) > 0
         assert touched.sum() > 200, touched.sum()
-        tol = 1e-3 * np.abs(g) + L["fp32"]
+        tol = L["tol"]
         idx = np.nonzero(touched)[0]
         p_ref = L["p"][idx]
         lo = _adam_ref(orc, p_ref, g[idx] - tol[idx], L["m0"][idx], L["v0"][idx], lr)
@@ -180,10 +176,8 @@ def test_feedback_order_and_split_change_no_result(gpu, orc, tile, ppt):
     ws = gpu.Workspace(len(p), 1 << 21, w, h)
     P = torch.from_numpy(p).cuda()
     R = gpu.cache_render(P, cam, cfg, ws).cpu().numpy()
-    _, marg, _, _ = orc.render(p, cam, grad_margins=True)
     rng = np.random.default_rng(7)
     tgt = (R * (1 + rng.uniform(-0.3, 0.3, R.shape)) + rng.uniform(0, 0.05, R.shape)).astype(np.float32)
-    tgt[:, marg] = R[:, marg]  # no gradient through a pixel with a decision within the margin
     T = torch.from_numpy(tgt).cuda()
     tiles = (-(-w // tile[0])) * (-(-h // tile[1]))
     runs = []
@@ -201,9 +195,8 @@ def test_feedback_order_and_split_change_no_result(gpu, orc, tile, ppt):
         assert lv == runs[0][1]
         np.testing.assert_allclose(g, runs[0][2], rtol=1e-5, atol=1e-6 * np.abs(runs[0][2]).max())
         assert (items > tiles) if one_warp else (items == tiles), (items, tiles)
-    # the split launch's gradient against the oracle's, with the FP32 bar of the at-scale test
+    # the split launch's gradient against the oracle's bounds, every pixel included
     _, dl = orc.loss_hdr(runs[2][0], tgt)
-    g_ref, _, a2d, nterm = orc.render_backward_terms(p, cam, dl)
-    fp32 = (80.0 + 8.0 * np.sqrt(nterm))[:, None] * 2.0 ** -24 * orc.grad_abs_map(p, cam, a2d)
-    bad = np.abs(runs[2][2] - g_ref) > 1e-3 * np.abs(g_ref) + fp32
-    assert np.abs(g_ref).max() > 0 and not bad.any(), (np.argwhere(bad)[:5], runs[2][2][bad][:5], g_ref[bad][:5])
+    g_mid, g_rad, bar, _ = grad_bounds(orc, p, cam, dl)
+    assert np.abs(g_mid).max() > 0
+    assert_grad_within(runs[2][2], g_mid, g_rad, bar)

@@ -318,3 +318,90 @@ def test_grad_abs_map_closed_form_columns(orc):
         for j, v in want.items():
             expect[j] = 2.0 * v
         np.testing.assert_allclose(out, expect, rtol=1e-9, atol=1e-12)
+
+
+def test_leaves_are_the_render_where_nothing_is_marginal(orc):
+    """render_leaves: one leaf, render's value bit for bit, on every pixel the
+    render does not flag; on a flagged pixel more than one leaf, render's
+    value among them."""
+    p = synth.gaussians(1024, synth.BASE_SEED + 2)
+    cam = synth.orbit_camera(96, 80, 30.0)
+    img, marg, _, _ = orc.render(p, cam, CFG)
+    lv, n = orc.render_leaves(p, cam, CFG)
+    assert n.min() >= 1 and marg.sum() > 5
+    np.testing.assert_array_equal(marg, n > 1)
+    one = n == 1
+    np.testing.assert_array_equal(lv[one][:, 0, :].T, img[:, one])
+    d = np.abs(lv - img.transpose(1, 2, 0)[:, :, None, :]).max(-1)
+    d = np.where(np.arange(lv.shape[2])[None, None, :] < n[:, :, None], d, np.inf).min(-1)
+    assert d.max() == 0.0
+
+
+def _centre_pixel_gaussians(alphas, rgbs, cam):
+    """Gaussians on the optical axis in depth order, each with peak alpha
+    sigmoid(logit) at the centre pixel (the FP32 logit of the given alpha)."""
+    p = np.concatenate([_one([0.5, 0.5, 0.4 + 0.1 * k], [math.log(0.05)] * 3, [1, 0, 0, 0],
+                             math.log(a / (1 - a)), rgb) for k, (a, rgb) in enumerate(zip(alphas, rgbs))])
+    return p, [1 / (1 + math.exp(-float(x))) for x in p[:, 3]]
+
+
+def test_leaves_of_a_marginal_alpha_min_decision(orc):
+    """A Gaussian whose alpha at the pixel centre lies within the margin
+    above 1/255: the pixel may composite it (c alpha) or drop it (0)."""
+    cam = _axis_cam()
+    p, (a,) = _centre_pixel_gaussians([(1 / 255) * (1 + 5e-5)], [(0.8, 0.4, 0.2)], cam)
+    lv, n = orc.render_leaves(p, cam, CFG, window=(32, 32, 1, 1))
+    assert n[0, 0] == 2
+    got = sorted(tuple(lv[0, 0, k]) for k in range(2))
+    np.testing.assert_allclose(got[0], [0, 0, 0], atol=0)
+    np.testing.assert_allclose(got[1], p[0, 12:15].astype(np.float64) * a, rtol=1e-12)
+    # and its colour gradient lies between the two: 0 (dropped) and alpha (taken)
+    lo, hi, _, nterm, nl = orc.render_backward_bounds(p, cam, np.ones((3, 1, 1)), CFG, window=(32, 32, 1, 1))
+    assert nl[0, 0] == 2 and nterm[0] == 1
+    np.testing.assert_allclose(lo[0, 6:9], 0.0, atol=0)
+    np.testing.assert_allclose(hi[0, 6:9], a, rtol=1e-12)
+
+
+def test_leaves_of_a_marginal_t_min_stop(orc):
+    """Two Gaussians on the axis whose transmittance after the second lands
+    within the margin above T_min: the pixel may composite the second (FP64
+    does) or stop before it."""
+    cam = _axis_cam()
+    a1 = 0.99
+    a2 = 1 - 1e-4 * (1 + 5e-5) / (1 - a1)
+    (p, (b1, b2)) = _centre_pixel_gaussians([a1, a2], [(1.0, 0.5, 0.25), (0.2, 0.6, 1.0)], cam)
+    cfg = dict(CFG, alpha_max=0.999)
+    lv, n = orc.render_leaves(p, cam, cfg, window=(32, 32, 1, 1))
+    # T after both: (1 - b1)(1 - b2), b2 as the FP32 logit gives it
+    t2 = (1 - b1) * (1 - b2)
+    assert abs(t2 / 1e-4 - 1) < 2e-4, t2
+    assert n[0, 0] == 2
+    first = p[0, 12:15].astype(np.float64) * b1
+    both = first + p[1, 12:15].astype(np.float64) * b2 * (1 - b1)
+    got = sorted((tuple(lv[0, 0, k]) for k in range(2)), key=lambda v: v[2])
+    np.testing.assert_allclose(got[0], first, rtol=1e-12)
+    np.testing.assert_allclose(got[1], both, rtol=1e-12)
+
+
+def test_backward_bounds_and_projection_match_the_backward(orc):
+    """Without marginal decisions the bounds collapse to the backward's 2D
+    record, and project_backward of that record is the backward's packed
+    gradient; with them, the record lies inside the bounds."""
+    p = synth.gaussians(600, 44)
+    cam = synth.orbit_camera(48, 40, 35.0)
+    dl = np.random.default_rng(4).uniform(-1, 1, (3, 40, 48))
+    _, marg, _, _ = orc.render(p, cam, CFG, grad_margins=True)
+    g, g2 = orc.render_backward(p, cam, dl, CFG)
+    lo, hi, ab, nterm, nl = orc.render_backward_bounds(p, cam, dl, CFG)
+    assert nl.min() >= 1 and marg.sum() > 0
+    np.testing.assert_array_equal(marg, nl > 1)
+    scale = np.abs(g2).max()
+    assert np.all(lo <= g2 + 1e-12 * scale) and np.all(g2 <= hi + 1e-12 * scale)
+    dz = dl.copy()
+    dz[:, marg] = 0.0
+    g_z, g2_z = orc.render_backward(p, cam, dz, CFG)
+    lo_z, hi_z, _, _, _ = orc.render_backward_bounds(p, cam, dz, CFG)
+    np.testing.assert_allclose(lo_z, g2_z, rtol=1e-11, atol=1e-13 * scale)
+    np.testing.assert_allclose(hi_z, g2_z, rtol=1e-11, atol=1e-13 * scale)
+    np.testing.assert_allclose(orc.project_backward(p, cam, g2_z, CFG), g_z, rtol=1e-11,
+                               atol=1e-13 * np.abs(g_z).max())
