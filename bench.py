@@ -540,6 +540,18 @@ def run_batched_bench(args, cfg_tuned):
     plain_ms = e0.elapsed_time(e1) / reps
     plain_ws.status()
     px = sum(v["cam"].width * v["cam"].height for v in step.views)
+    # roofline of the batch's training-step kernel: device counters and the
+    # kernel's CUDA-event time over the same step run eagerly
+    step.ws.counters()
+    gsc.profile_read(reset=True)
+    gsc.profile_enable(True)
+    for _ in range(reps):
+        step.step()
+    torch.cuda.synchronize()
+    gsc.profile_enable(False)
+    prof = gsc.profile_read(reset=True)
+    cnt = step.ws.counters()
+    roof = train_roofline(cnt, prof, 3 * px * reps, reps)
     del step, plain_ws
     torch.cuda.empty_cache()
     return {"workload": "32 views (256^2 / 640x480 / 1280x720 / 1920x1080, seeded) over 4 scenes of "
@@ -547,7 +559,22 @@ def run_batched_bench(args, cfg_tuned):
             "pixels": px, "graph_ms_per_step": round(graph_ms, 3),
             "launch": dict(best[0], ms=round(best[1], 3)),
             "separate_launches_ms_per_step": round(separate_ms, 3), "plain_ms_per_step": round(plain_ms, 3),
-            "plain_host_ms_per_step": round(plain_wall, 3), "speedup_vs_plain": round(plain_ms / graph_ms, 3)}
+            "plain_host_ms_per_step": round(plain_wall, 3), "speedup_vs_plain": round(plain_ms / graph_ms, 3),
+            "roofline": roof}
+
+
+def train_roofline(cnt, prof, channel_elements, steps, phase="train"):
+    """FP32 roofline of a compositing kernel phase from the device counters
+    (algorithmic flops per unit as for the frame) and its CUDA-event time."""
+    kind, flops = phase_algorithmic(phase, cnt, 0, channel_elements, steps)
+    ms = prof.get(phase, (0.0, 0, 0))[0]
+    if not ms or kind != "flop":
+        return None
+    achieved = flops / (ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": phase, "achieved": round(achieved, 2), "peak": round(FP32_PEAK_TFLOPS, 1),
+            "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+            "ms_per_step": round(ms / steps, 3), "gflop_per_step": round(flops / steps / 1e9, 2),
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
 
 
 def run_served_bench(args, cfg_tuned):
@@ -557,7 +584,8 @@ def run_served_bench(args, cfg_tuned):
     one-view-per-call path on the same trace."""
     import copy
     import torch
-    from paper_2507_19718_gb300 import serve, synth
+    from paper_2507_19718_gb300 import gsc, serve, synth
+    K = LEVELS
     scenes_np = serve.frame_scenes(8)
     sizes = [200_000 + k * 800_000 // 7 for k in range(8)]
     scenes = [serve.ResidentScene(sc, synth.level_sizes(n, LEVELS), seed=synth.BASE_SEED + 3000 + 10 * k)
@@ -601,6 +629,29 @@ def run_served_bench(args, cfg_tuned):
                      "tf_retrain_p50_ms": round(tfl.get("p50_ms", float("nan")), 1),
                      "mean_views_per_batch": round(srv.stats["mean_views_per_batch"], 2),
                      "wall_s": round(srv.stats["wall_s"], 2)}
+    # roofline of the served work: a shorter run of the batched server with
+    # the kernels' CUDA-event times and the workspaces' device counters (kept
+    # apart from the latency runs above, which it would perturb)
+    reset()
+    for ws in srv.view_ws + [srv.trainer.ws]:
+        ws.counters()
+    tr = serve.poisson_trace(200.0, 3.0, 8, seed=synth.BASE_SEED + 72)
+    gsc.profile_read(reset=True)
+    gsc.profile_enable(True)
+    srv.run_batched(tr)
+    torch.cuda.synchronize()
+    gsc.profile_enable(False)
+    prof = gsc.profile_read(reset=True)
+    cv = [ws.counters() for ws in srv.view_ws]
+    view_cnt = {k: sum(c[k] for c in cv) for k in cv[0]}
+    train_cnt = srv.trainer.ws.counters()
+    view_px = sum(r.width * r.height * K for r in tr if r.kind == "view")
+    tw, th = srv.trainer.w, srv.trainer.h
+    train_px = train_cnt["binnings"] * tw * th * K
+    roofs = {"render": train_roofline(view_cnt, prof, 3 * view_px, 1, phase="render"),
+             "train": train_roofline(train_cnt, prof, 3 * train_px, 1, phase="train")}
+    busy = {k: round(prof.get(k, (0.0,))[0], 2) for k in ("render", "train")}
+    out["batched"]["roofline"] = {"workload": "3 s of the same arrivals (batched server)", "kernel_ms": busy, **roofs}
     del srv, scenes, snap
     torch.cuda.empty_cache()
     return out
@@ -608,65 +659,165 @@ def run_served_bench(args, cfg_tuned):
 
 # ------------------------------------------------------------------ oracle (CPU) arm
 
-def oracle_sample(rank=0):
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+# The oracle's cost per pixel varies by orders of magnitude over the frame:
+# a pixel where the cache saturates stops after a few hundred Gaussians, one
+# at the edge of the volume walks all of them.  A step of the oracle arm
+# therefore samples three 16 x 9 windows, each at a seeded place in one of
+# the frame's ninths, three ninths per step in turn, so that every three steps
+# cover the frame in a stratified sample.
+SAMPLE_W, SAMPLE_H = 16, 9
+
+
+def sample_windows(step: int):
+    rng = np.random.default_rng(synth_seed() + 900 + step)
+    out = []
+    for c in range(3):
+        cell = (3 * step + c) % 9
+        i, j = cell % 3, cell // 3
+        x = int(i * WIDTH / 3 + rng.integers(0, WIDTH // 3 - SAMPLE_W))
+        y = int(j * HEIGHT / 3 + rng.integers(0, HEIGHT // 3 - SAMPLE_H))
+        out.append((x, y, SAMPLE_W, SAMPLE_H))
+    return out
+
+
+def synth_seed() -> int:
+    from paper_2507_19718_gb300 import synth
+    return synth.BASE_SEED
+
+
+def oracle_sample(nthreads=0, step=0):
     """Time the oracle on a bounded sample of the frame's train + render work
-    and extrapolate to one frame.  Per level: render + backward over a window
-    (per-pixel work) and over a 1x1 window (the per-call projection and depth
-    sort), HDR loss on the window, AdamW over all the level's Gaussians."""
+    and extrapolate to one frame: per level, render + backward + HDR loss over
+    three windows in three ninths of the frame (sample_windows(step); the
+    steps together make a stratified sample of its pixels), the per-call projection and depth sort measured once
+    on a 1x1 window and taken out of each window's time, AdamW over all the
+    level's Gaussians.  Returns (ms per frame, the sample's wall seconds, its
+    description)."""
     import oracle
     from paper_2507_19718_gb300 import synth
     oracle.build()
     sizes = synth.level_sizes(TOTAL_GAUSSIANS, LEVELS)
     cam = synth.orbit_camera(WIDTH, HEIGHT, 0.0)
-    win = (720, 405, 480, 270)
-    frame_px, win_px = WIDTH * HEIGHT, win[2] * win[3]
+    frame_px = WIDTH * HEIGHT
     est_s, used_s = 0.0, 0.0
     for k, n in enumerate(sizes):
         p = synth.gaussians(n, synth.BASE_SEED + 1000 + k)
         t0 = time.perf_counter()
-        oracle.render(p, cam, window=(win[0], win[1], 1, 1))
-        oracle.render_backward(p, cam, np.ones((3, 1, 1)), window=(win[0], win[1], 1, 1))
+        oracle.render(p, cam, window=(WIDTH // 2, HEIGHT // 2, 1, 1), nthreads=nthreads)
+        oracle.render_backward(p, cam, np.ones((3, 1, 1)), window=(WIDTH // 2, HEIGHT // 2, 1, 1),
+                               nthreads=nthreads)
         t_fix = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        img, _, _, _ = oracle.render(p, cam, window=win)
-        g = np.random.default_rng(k).uniform(-1, 1, (3, win[3], win[2]))
-        oracle.render_backward(p, cam, g, window=win)
-        tgt = np.random.default_rng(k + 7).uniform(0, 1, img.shape).astype(np.float32)
-        oracle.loss_hdr(img.astype(np.float32), tgt)
-        t_win = time.perf_counter() - t0
+        t_pix, px = 0.0, 0
+        for i, win in enumerate(sample_windows(step)):
+            t0 = time.perf_counter()
+            img, _, _, _ = oracle.render(p, cam, window=win, nthreads=nthreads)
+            g = np.random.default_rng(k * 16 + i).uniform(-1, 1, (3, win[3], win[2]))
+            oracle.render_backward(p, cam, g, window=win, nthreads=nthreads)
+            tgt = np.random.default_rng(k * 16 + i + 7).uniform(0, 1, img.shape).astype(np.float32)
+            oracle.loss_hdr(img.astype(np.float32), tgt)
+            t_win = time.perf_counter() - t0
+            t_pix += max(t_win - t_fix, 0.0)
+            px += win[2] * win[3]
+            used_s += t_win
         pp = p.astype(np.float64).reshape(-1)
         gg = np.random.default_rng(k).normal(0, 1e-3, pp.size)
         mm, vv = np.zeros_like(pp), np.zeros_like(pp)
         t0 = time.perf_counter()
         oracle.adamw(pp, gg, mm, vv, np.tile(np.float64(1e-3), 16), 1.0, 0.9, 0.999, 1e-15, 0.01, 1)
         t_adam = time.perf_counter() - t0
-        per_px = max(t_win - t_fix, 0.0) / win_px
-        est_s += t_fix + per_px * frame_px + t_adam
-        used_s += t_fix + t_win + t_adam
-    sample = (f"oracle (FP64 C, OpenMP) render+backward+HDR loss on a {win[2]}x{win[3]} window at the "
-              f"centre of the 1080p frame per level and on a 1x1 window (per-call projection/sort), AdamW on "
-              f"all 1M Gaussians; per-pixel cost extrapolated to {frame_px} px; {used_s:.1f} s wall")
-    return est_s * 1e3, sample
+        est_s += t_fix + t_pix / px * frame_px + t_adam
+        used_s += t_fix + t_adam
+    threads = nthreads or (os.cpu_count() or 1)
+    sample = (f"oracle (FP64 C, OpenMP, {threads} thread{'s' if threads > 1 else ''}): per level render + "
+              f"backward + HDR loss on three {SAMPLE_W}x{SAMPLE_H} windows at seeded places in three ninths of "
+              f"the 1080p frame (every three steps cover all nine), the per-call projection and sort once, "
+              f"AdamW on all Gaussians; per-pixel cost extrapolated to {frame_px} px")
+    return est_s * 1e3, used_s, sample
+
+
+def oracle_workloads(nthreads):
+    """The oracle's time on config 0 in full (trace 128x128 at 4 spp, 4
+    bounces, 4 buffers; render, HDR loss, backward and AdamW of 1,024
+    Gaussians) and on the 256x256 crop of the 1M-Gaussian 1080p
+    differentiation check (render, L1 + D-SSIM loss, backward), in seconds."""
+    import oracle
+    from paper_2507_19718_gb300 import synth
+    scene = synth.scene_tiny()
+    cam0 = synth.orbit_camera(128, 128, 30.0)
+    p0 = synth.gaussians(1024, synth.BASE_SEED + 2)
+    t0 = time.perf_counter()
+    tg, _ = oracle.trace(scene, cam0, spp=4, max_bounces=4, levels=4, seed=synth.BASE_SEED, nthreads=nthreads)
+    img, _, _, _ = oracle.render(p0, cam0, nthreads=nthreads)
+    _, dl = oracle.loss_hdr(img.astype(np.float32), tg[0].astype(np.float32))
+    g, _ = oracle.render_backward(p0, cam0, dl, nthreads=nthreads)
+    pp, gg = p0.astype(np.float64).reshape(-1), g.reshape(-1).copy()
+    oracle.adamw(pp, gg, np.zeros_like(pp), np.zeros_like(pp), np.tile(np.float64(1e-3), 16))
+    t_cfg0 = time.perf_counter() - t0
+    p2 = synth.gaussians(1_000_000, synth.BASE_SEED + 2)
+    cam2 = synth.orbit_camera(WIDTH, HEIGHT, 0.0)
+    crop = (832, 412, 256, 256)
+    t0 = time.perf_counter()
+    img2, _, _, _ = oracle.render(p2, cam2, window=crop, nthreads=nthreads)
+    tgt = np.random.default_rng(3).uniform(0, 1, img2.shape).astype(np.float32)
+    _, dl2, _ = oracle.loss_l1ssim(img2.astype(np.float32), tgt)
+    oracle.render_backward(p2, cam2, dl2, window=crop, nthreads=nthreads)
+    t_cfg2 = time.perf_counter() - t0
+    return {"config0_full_s": round(t_cfg0, 3), "config2_crop256_s": round(t_cfg2, 3)}
 
 
 def run_reference(args, world, rank):
+    """The CPU oracle as the reference arm: every step is one bounded sample
+    of the frame (oracle_sample, all host cores), the line's value its
+    extrapolation to a full frame; then the same sample and the config-0 and
+    config-2 workloads at one thread and at all cores."""
     if rank != 0:
         return None
-    vals = []
+    vals, walls = [], []
     sample = ""
     for i in range(args.warmup + args.steps):
-        ms, sample = oracle_sample(rank)
+        t0 = time.perf_counter()
+        ms, _, sample = oracle_sample(step=i)
         if i >= args.warmup:
             vals.append(ms)
-    value = float(np.median(vals))
+            walls.append(time.perf_counter() - t0)
+    # the steps sample different places of the frame: their mean estimates it
+    value = float(np.mean(vals))
     cores = os.cpu_count() or 1
+    detail = {"cpu_model": cpu_model(), "nproc": cores}
+    if not args.no_cpu_detail:
+        ms1, wall1, _ = oracle_sample(nthreads=1, step=args.warmup)
+        detail.update({"frame_extrapolated_ms": {"all_cores": round(value, 1), "one_thread": round(ms1, 1)},
+                       "frame_sample_wall_s": {"all_cores": round(float(np.median(walls)), 3),
+                                               "one_thread": round(wall1, 3)},
+                       "all_cores": oracle_workloads(0), "one_thread": oracle_workloads(1)})
     return {
         "metric": METRIC, "impl": "reference", "value": round(value, 1), "unit": "ms/frame", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value, 1), "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * float(np.mean(walls)), 1),
+        "step": "one bounded sample of the frame (oracle_sample); value = its extrapolation to a full frame",
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(),
         "cpu_baseline": {"value": round(value, 1), "unit": "ms/frame", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu_model": detail["cpu_model"]},
+        "cpu_detail": detail,
         "e2e": {"value": round(value, 1), "unit": "ms/frame", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -678,6 +829,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-detail", action="store_true",
+                    help="reference arm: skip the one-thread and config-0 / config-2 oracle timings")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-init", action="store_true")
@@ -718,9 +871,12 @@ def main():
         res["cache_coupled"] = run_coupled_bench(args)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
-            ms, sample = oracle_sample()
+            # three steps of the oracle arm: one stratified cover of the frame
+            runs = [oracle_sample(step=i) for i in range(3)]
+            ms, wall, sample = float(np.mean([r[0] for r in runs])), sum(r[1] for r in runs), runs[0][2]
             res["cpu_baseline"] = {"value": round(ms, 1), "unit": "ms/frame", "cores": os.cpu_count() or 1,
-                                   "kind": "oracle", "sample": sample}
+                                   "kind": "oracle", "sample": sample + "; mean of three such steps",
+                                   "sample_wall_s": round(wall, 2), "cpu_model": cpu_model()}
         print(json.dumps(res), flush=True)
     if world > 1:
         import torch.distributed as dist

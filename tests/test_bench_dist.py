@@ -55,7 +55,7 @@ def test_reference_arm_under_torchrun_prints_once(tmp_path):
     env = dict(os.environ, OMP_NUM_THREADS="2", CUDA_VISIBLE_DEVICES="")
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py", "--impl", "reference",
-           "--gpus", "2", "--steps", "1", "--warmup", "3"]
+           "--gpus", "2", "--steps", "1", "--warmup", "3", "--no-cpu-detail"]
     p = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert p.returncode == 0, p.stderr[-2000:]
     lines = [l for l in p.stdout.splitlines() if l.startswith("{")]
@@ -63,3 +63,6 @@ def test_reference_arm_under_torchrun_prints_once(tmp_path):
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+    # a step is one bounded sample: its measured time, not the extrapolated frame
+    assert d["steps"] == 1 and 0 < d["ms_per_step"] < d["value"]
+    assert d["cpu_detail"]["nproc"] >= 1 and d["cpu_detail"]["cpu_model"]
