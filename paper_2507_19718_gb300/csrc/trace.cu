@@ -278,8 +278,12 @@ __global__ void __launch_bounds__(128, MINB) k_trace(TraceDev v, CamDev cam, con
     if (i >= cam.W || j >= cam.H) return;
     size_t HW = (size_t)cam.W * cam.H, pix = (size_t)j * cam.W + i;
     float img[3] = {0.0f, 0.0f, 0.0f};
-    float tgt[kMaxLevels][3];
-    for (int k = 0; k < v.K; ++k) tgt[k][0] = tgt[k][1] = tgt[k][2] = 0.0f;
+    // the pixel's target buffers accumulate in place (the thread owns the
+    // pixel): a per-thread array indexed by path length would live in local
+    // memory, which at every warp slot of the SM spills into L2 and evicts
+    // the volume
+    for (int k = 0; k < v.K; ++k)
+        for (int c = 0; c < 3; ++c) targets[((size_t)k * 3 + c) * HW + pix] = 0.0f;
     const bool cache_on = cache != nullptr;
     for (int s = 0; s < v.spp; ++s) {
         Philox r;
@@ -366,11 +370,18 @@ __global__ void __launch_bounds__(128, MINB) k_trace(TraceDev v, CamDev cam, con
         }
         for (int c = 0; c < 3; ++c) img[c] = img[c] + val[c];
         if (n >= 1 && n <= v.K)
-            for (int c = 0; c < 3; ++c) tgt[n - 1][c] = tgt[n - 1][c] + L[c];
+            for (int c = 0; c < 3; ++c) {
+                float* t = &targets[((size_t)(n - 1) * 3 + c) * HW + pix];
+                *t = *t + L[c];
+            }
     }
     for (int c = 0; c < 3; ++c) image[c * HW + pix] = img[c] / (float)v.spp;
-    for (int k = 0; k < v.K; ++k)
-        for (int c = 0; c < 3; ++c) targets[((size_t)k * 3 + c) * HW + pix] = tgt[k][c] / (float)v.spp;
+    if (v.spp > 1)  // x / 1 = x
+        for (int k = 0; k < v.K; ++k)
+            for (int c = 0; c < 3; ++c) {
+                float* t = &targets[((size_t)k * 3 + c) * HW + pix];
+                *t = *t / (float)v.spp;
+            }
 }
 
 // Cache initialisation, point sampling (Sec. 3.2 "Cache Initialization"):
