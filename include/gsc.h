@@ -228,8 +228,11 @@ gsc_status gsc_workspace_status(gsc_workspace* ws, gsc_stream_t stream, int64_t*
  * the pairs composited for pixels whose dL/dimage is not zero, which are the
  * pairs that contribute back to front.  out[10]: work items of the last
  * binning's order (its tiles, plus one for every extra part a gradient
- * launch split a heavy tile into; not reset).  n: entries wanted (<= 11). */
-#define GSC_COUNTER_WORDS 11
+ * launch split a heavy tile into; not reset).  out[11]: pairs the binnings
+ * emitted for a bin of the Gaussian's tile rectangle that its falloff bound
+ * cannot reach (listed in no bin; included in out[0], out[1] and out[6]).
+ * n: entries wanted (<= 12). */
+#define GSC_COUNTER_WORDS 12
 gsc_status gsc_workspace_counters(gsc_workspace* ws, gsc_stream_t stream, int64_t* out, int32_t n);
 
 /* ------------------------------------------------------------------ */

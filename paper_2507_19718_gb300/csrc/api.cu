@@ -472,7 +472,8 @@ gsc_status gsc_workspace_counters(gsc_workspace* ws, gsc_stream_t stream, int64_
     int64_t all[GSC_COUNTER_WORDS] = {counters[kCntPairs], counters[kCntPairsMax], (int64_t)st[kStEvalFwd],
                                       (int64_t)st[kStCompFwd], (int64_t)st[kStEvalRewalk], (int64_t)st[kStEvalBack],
                                       (int64_t)st[kStPairsSum], (int64_t)st[kStBinnings],
-                                      (int64_t)st[kStCompRewalk], (int64_t)st[kStHitBack], (int64_t)fb[kFbItems]};
+                                      (int64_t)st[kStCompRewalk], (int64_t)st[kStHitBack], (int64_t)fb[kFbItems],
+                                      (int64_t)st[kStCulled]};
     for (int k = 0; k < n; ++k) out[k] = all[k];
     return GSC_OK;
 }

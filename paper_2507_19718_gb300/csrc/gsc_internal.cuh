@@ -136,7 +136,7 @@ __host__ __device__ __forceinline__ uint32_t make_item(uint32_t tile, uint32_t p
 enum : int { kOrderPlain = 0, kOrderFeedback = 1 };
 // 64-bit work statistics in the workspace
 enum : int { kStEvalFwd = 0, kStCompFwd = 1, kStEvalRewalk = 2, kStEvalBack = 3, kStPairsSum = 4, kStBinnings = 5,
-             kStCompRewalk = 6, kStHitBack = 7, kStatWords = 8 };
+             kStCompRewalk = 6, kStHitBack = 7, kStCulled = 8, kStatWords = 9 };
 
 }  // namespace gsc
 

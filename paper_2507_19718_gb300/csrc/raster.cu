@@ -188,91 +188,6 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchDe
     rec[3 * (size_t)g + 2] = make_float4(fmaxf(p3.x, 0.f), fmaxf(p3.y, 0.f), fmaxf(p3.z, 0.f), 0.f);
 }
 
-// One warp emits the (bin, Gaussian) pairs of 32 consecutive depth-ordered
-// Gaussians.  Their outputs form one contiguous run (the offsets are an
-// exclusive scan in that order), so the warp walks the run 32 elements at a
-// time: element e belongs to the last lane whose offset is <= e (a five-step
-// search over the lanes' offsets), and every store instruction is contiguous.
-// The bin rectangle follows from the tile rectangle.
-__global__ void __launch_bounds__(256) k_emit(const __grid_constant__ BatchDev b, const uint32_t* __restrict__ sidx,
-                                              const uint32_t* __restrict__ off, const uint32_t* __restrict__ cnt,
-                                              const uint2* __restrict__ rect, RasterDev rc,
-                                              const uint32_t* __restrict__ counters, uint32_t* __restrict__ pkey,
-                                              uint32_t* __restrict__ pval) {
-    const uint32_t N = b.total_g;
-    const uint32_t total = counters[kCntPairs];
-    const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (wid * 32 >= N || total == 0) return;  // warp-uniform
-    const uint32_t i = wid * 32 + lane;
-    uint32_t g = 0, c = 0, o = 0;
-    if (i < N) {
-        g = sidx[i];
-        c = cnt[g];
-        o = off[i];
-    }
-    // lanes past N continue the run with no pairs, keeping the offsets monotone
-    const uint32_t nv = min(32u, N - wid * 32);
-    const uint32_t last_o = __shfl_sync(kFull, o, nv - 1), last_c = __shfl_sync(kFull, c, nv - 1);
-    if (i >= N) o = last_o + last_c;
-    const uint32_t start = __shfl_sync(kFull, o, 0);
-    const uint32_t end = min(last_o + last_c, total);
-    // per lane: bin rectangle origin and width, bins of its view
-    uint32_t bx0 = 0, by0 = 0, wx = 1, boff = 0, bins_x = 0;
-    if (c) {
-        uint2 rr = rect[g];
-        const ViewDev& vw = b.v[view_of_gaussian(b, g)];
-        bx0 = (rr.x & 0xffffu) / vw.spt_x;
-        uint32_t bx1 = ((rr.x >> 16) - 1) / vw.spt_x + 1;
-        by0 = (rr.y & 0xffffu) / vw.spt_y;
-        wx = bx1 - bx0;
-        boff = vw.bin_off;
-        bins_x = (uint32_t)vw.bins_x;
-    }
-    for (uint32_t e0 = start; e0 < end; e0 += 32) {
-        const uint32_t e = e0 + lane;
-        int j = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            uint32_t oj = __shfl_sync(kFull, o, j + step);
-            if (j + step < 32 && oj <= e) j += step;
-        }
-        const uint32_t k = e - __shfl_sync(kFull, o, j);
-        const uint32_t gj = __shfl_sync(kFull, g, j);
-        const uint32_t wj = __shfl_sync(kFull, wx, j);
-        const uint32_t x0 = __shfl_sync(kFull, bx0, j), y0 = __shfl_sync(kFull, by0, j);
-        const uint32_t bo = __shfl_sync(kFull, boff, j), bxn = __shfl_sync(kFull, bins_x, j);
-        if (e < end) {
-            // row of pair k in a rectangle wj bins wide, floor((k + 1/2) / wj)
-            // in FP32: the quotient stays 1 / (2 wj) away from an integer and
-            // its two roundings move it by at most (k + 1/2) 2^-23 / wj, which
-            // is less while k < 2^22 - 1/2 (a view has at most 2048 x 2048
-            // bins of 32 px, so k < 2^22)
-            const uint32_t ky = (uint32_t)(((float)k + 0.5f) * __frcp_rn((float)wj));
-            const uint32_t kx = k - ky * wj;
-            pkey[e] = bo + (y0 + ky) * bxn + x0 + kx;
-            pval[e] = gj;
-        }
-    }
-}
-
-__global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ counters,
-                         uint2* __restrict__ ranges) {
-    uint32_t n = counters[kCntPairs];
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        uint32_t k = keys[i];
-        if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
-        if (i == n - 1 || keys[i + 1] != k) ranges[k].y = i + 1;
-    }
-}
-
-
-
-__device__ __forceinline__ bool tile_in(uint2 r, int tx, int ty) {
-    return tx >= (int)(r.x & 0xffffu) && tx < (int)(r.x >> 16) && ty >= (int)(r.y & 0xffffu) &&
-           ty < (int)(r.y >> 16);
-}
-
 // Largest log2-falloff p = qa dx^2 + qb dx dy + qc dy^2 (negative definite)
 // of a Gaussian over the rectangle [x0, x1] x [y0, y1] of pixel centres:
 // 0 if its mean lies inside, else the best of the four edges, each a 1-D
@@ -299,6 +214,115 @@ __device__ __forceinline__ float rect_max_falloff(float4 r0, float qc, float x0,
 // tile.  The margin (in log2 units) keeps the test conservative against the
 // rounding of the per-pixel evaluation, so no composited pair is dropped.
 constexpr float kCullMargin = 4e-3f;
+
+// One warp emits the (bin, Gaussian) pairs of 32 consecutive depth-ordered
+// Gaussians.  Their outputs form one contiguous run (the offsets are an
+// exclusive scan in that order), so the warp walks the run 32 elements at a
+// time: element e belongs to the last lane whose offset is <= e (a five-step
+// search over the lanes' offsets), and every store instruction is contiguous.
+// The bin rectangle follows from the tile rectangle.  A bin of that
+// rectangle whose pixel centres the Gaussian's falloff cannot bring to its
+// alpha_min threshold (the bound of the tile filter over the whole bin,
+// with a wider margin) gets the key total_bins, which sorts after every bin
+// and belongs to no bin's list: no tile of the bin would have kept it.
+constexpr float kBinCullMargin = 4.f * kCullMargin;
+__global__ void __launch_bounds__(256) k_emit(const __grid_constant__ BatchDev b, const uint32_t* __restrict__ sidx,
+                                              const uint32_t* __restrict__ off, const uint32_t* __restrict__ cnt,
+                                              const uint2* __restrict__ rect, const float4* __restrict__ rec,
+                                              RasterDev rc, const uint32_t* __restrict__ counters,
+                                              uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval,
+                                              unsigned long long* __restrict__ stats) {
+    const uint32_t N = b.total_g;
+    const uint32_t total = counters[kCntPairs];
+    const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid * 32 >= N || total == 0) return;  // warp-uniform
+    const uint32_t i = wid * 32 + lane;
+    uint32_t g = 0, c = 0, o = 0;
+    if (i < N) {
+        g = sidx[i];
+        c = cnt[g];
+        o = off[i];
+    }
+    // lanes past N continue the run with no pairs, keeping the offsets monotone
+    const uint32_t nv = min(32u, N - wid * 32);
+    const uint32_t last_o = __shfl_sync(kFull, o, nv - 1), last_c = __shfl_sync(kFull, c, nv - 1);
+    if (i >= N) o = last_o + last_c;
+    const uint32_t start = __shfl_sync(kFull, o, 0);
+    const uint32_t end = min(last_o + last_c, total);
+    // per lane: bin rectangle origin and width, bins of its view
+    uint32_t bx0 = 0, by0 = 0, wx = 1, boff = 0, bins_x = 0, bsz = 0;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+    if (c) {
+        uint2 rr = rect[g];
+        const ViewDev& vw = b.v[view_of_gaussian(b, g)];
+        r0 = rec[3 * (size_t)g];
+        r1 = rec[3 * (size_t)g + 1];
+        bsz = (uint32_t)vw.bin;
+        bx0 = (rr.x & 0xffffu) / vw.spt_x;
+        uint32_t bx1 = ((rr.x >> 16) - 1) / vw.spt_x + 1;
+        by0 = (rr.y & 0xffffu) / vw.spt_y;
+        wx = bx1 - bx0;
+        boff = vw.bin_off;
+        bins_x = (uint32_t)vw.bins_x;
+    }
+    uint32_t n_cull = 0;
+    for (uint32_t e0 = start; e0 < end; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        int j = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            uint32_t oj = __shfl_sync(kFull, o, j + step);
+            if (j + step < 32 && oj <= e) j += step;
+        }
+        const uint32_t k = e - __shfl_sync(kFull, o, j);
+        const uint32_t gj = __shfl_sync(kFull, g, j);
+        const uint32_t wj = __shfl_sync(kFull, wx, j);
+        const uint32_t x0 = __shfl_sync(kFull, bx0, j), y0 = __shfl_sync(kFull, by0, j);
+        const uint32_t bo = __shfl_sync(kFull, boff, j), bxn = __shfl_sync(kFull, bins_x, j);
+        const uint32_t bs = __shfl_sync(kFull, bsz, j);
+        const float4 q0 = make_float4(__shfl_sync(kFull, r0.x, j), __shfl_sync(kFull, r0.y, j),
+                                      __shfl_sync(kFull, r0.z, j), __shfl_sync(kFull, r0.w, j));
+        const float qc = __shfl_sync(kFull, r1.x, j), thr = __shfl_sync(kFull, r1.z, j);
+        if (e < end) {
+            // row of pair k in a rectangle wj bins wide, floor((k + 1/2) / wj)
+            // in FP32: the quotient stays 1 / (2 wj) away from an integer and
+            // its two roundings move it by at most (k + 1/2) 2^-23 / wj, which
+            // is less while k < 2^22 - 1/2 (a view has at most 2048 x 2048
+            // bins of 32 px, so k < 2^22)
+            const uint32_t ky = (uint32_t)(((float)k + 0.5f) * __frcp_rn((float)wj));
+            const uint32_t kx = k - ky * wj;
+            const float px0 = (float)((x0 + kx) * bs) + 0.5f, py0 = (float)((y0 + ky) * bs) + 0.5f;
+            const float m = rect_max_falloff(q0, qc, px0, px0 + (float)(bs - 1), py0, py0 + (float)(bs - 1));
+            const bool reach = m >= thr - kBinCullMargin * (1.f + fabsf(thr));
+            pkey[e] = reach ? bo + (y0 + ky) * bxn + x0 + kx : b.total_bins;
+            pval[e] = gj;
+            n_cull += reach ? 0u : 1u;
+        }
+    }
+    n_cull = __reduce_add_sync(kFull, n_cull);
+    if (lane == 0 && n_cull) atomicAdd(&stats[kStCulled], (unsigned long long)n_cull);
+}
+
+// bin ranges from the sorted keys; keys >= nbins (culled pairs) have none
+__global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ counters,
+                         uint2* __restrict__ ranges, uint32_t nbins) {
+    uint32_t n = counters[kCntPairs];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t k = keys[i];
+        if (k >= nbins) continue;
+        if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
+        if (i == n - 1 || keys[i + 1] != k) ranges[k].y = i + 1;
+    }
+}
+
+
+
+__device__ __forceinline__ bool tile_in(uint2 r, int tx, int ty) {
+    return tx >= (int)(r.x & 0xffffu) && tx < (int)(r.x >> 16) && ty >= (int)(r.y & 0xffffu) &&
+           ty < (int)(r.y >> 16);
+}
+
 __device__ __forceinline__ bool tile_hit(uint2 rect, float4 r0, float4 r1, int tx, int ty, int TW, int TH) {
     if (!tile_in(rect, tx, ty)) return false;
     float x0 = (float)(tx * TW) + 0.5f, y0 = (float)(ty * TH) + 0.5f;
@@ -1355,10 +1379,11 @@ cudaError_t bin_gaussians(const BatchDev& b, const RasterDev& rc, gsc_workspace*
     }
     {
         PhaseScope ph(kPhEmit, s, 1);
-        k_emit<<<nblk, 256, 0, s>>>(b, sidx, ws->off, ws->cnt, ws->rect, rc, ws->counters, ws->pkey0, ws->pval0);
+        k_emit<<<nblk, 256, 0, s>>>(b, sidx, ws->off, ws->cnt, ws->rect, ws->rec, rc, ws->counters, ws->pkey0,
+                                    ws->pval0, ws->stats);
     }
     uint32_t bins = b.total_bins;
-    int bits = bits_for(bins);
+    int bits = bits_for(bins + 1);  // key total_bins: culled pairs
     int p;
     {
         PhaseScope ph(kPhTileSort, s, 3 * radix_passes(bits));
@@ -1375,7 +1400,7 @@ cudaError_t bin_gaussians(const BatchDev& b, const RasterDev& rc, gsc_workspace*
         PhaseScope ph(kPhRanges, s, (one_pass ? 1 : 2) + (order_mode == kOrderFeedback ? 1 : 0));
         if (!one_pass) {
             cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * bins, s);
-            k_ranges<<<152 * 8, 256, 0, s>>>(keys, ws->counters, ws->ranges);
+            k_ranges<<<152 * 8, 256, 0, s>>>(keys, ws->counters, ws->ranges, bins);
         }
         const int grid = order_mode == kOrderFeedback ? bwd_grid_hint(rc, b.total_tiles) : 0;
         if (order_mode == kOrderFeedback) {

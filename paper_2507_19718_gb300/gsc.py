@@ -343,11 +343,11 @@ class Workspace:
 
     def counters(self, stream=None) -> dict:
         """Synchronise and return (then reset) the workspace's work counters."""
-        out = (C.c_int64 * 11)()
-        _check(lib().gsc_workspace_counters(self.handle, _stream(stream), out, 11))
+        out = (C.c_int64 * 12)()
+        _check(lib().gsc_workspace_counters(self.handle, _stream(stream), out, 12))
         return dict(pairs_last=out[0], pairs_max=out[1], eval_fwd=out[2], composited_fwd=out[3],
                     eval_rewalk=out[4], eval_back=out[5], pairs_sum=out[6], binnings=out[7],
-                    composited_rewalk=out[8], hits_back=out[9], items_last=out[10])
+                    composited_rewalk=out[8], hits_back=out[9], items_last=out[10], pairs_culled=out[11])
 
     def close(self):
         if getattr(self, "handle", None):

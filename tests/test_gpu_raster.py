@@ -204,6 +204,30 @@ def test_work_counters_count_the_composited_pairs(gpu, orc):
         assert c["binnings"] == 2 and c["pairs_sum"] > 0
 
 
+def test_bin_culling_drops_only_unreachable_pairs(gpu, orc):
+    """Long thin Gaussians (one axis e^-1.2, two e^-4.5, random rotations)
+    have tile rectangles much larger than their ellipses: the binning lists
+    a pair only in the bins of the rectangle that the falloff bound can
+    reach.  Culling does drop pairs at every bin size, and the images at bin
+    32, 64 and 128 (different culled sets) are the same bits and match the
+    oracle on every pixel."""
+    p = synth.gaussians(600, synth.BASE_SEED + 41)
+    rng = np.random.default_rng(43)
+    p[:, 4:7] = np.float32(-4.5)
+    p[np.arange(len(p)), 4 + rng.integers(0, 3, len(p))] = np.float32(-1.2)
+    cam = synth.orbit_camera(320, 240, 20.0)
+    ws = _ws(gpu, len(p), 1 << 22, cam.width, cam.height)
+    ws.counters()
+    imgs = []
+    for b in (32, 64, 128):
+        imgs.append(_render(gpu, p, cam, gpu.raster_cfg(tile=(16, 16), bin_size=b), ws))
+        c = ws.counters()
+        assert 0 < c["pairs_culled"] < c["pairs_last"], (b, c)
+    for img in imgs[1:]:
+        np.testing.assert_array_equal(img, imgs[0])
+    render_check(orc, imgs[0], p, cam, (0, 0, cam.width, cam.height))
+
+
 def test_nine_bit_pair_sort_gives_the_same_bits(gpu, orc):
     """300 coarse bins (bin 32 on 640x480) are sorted in one 9-bit radix pass,
     20 bins (bin 128) in one 8-bit pass: the images are bit-identical, and
