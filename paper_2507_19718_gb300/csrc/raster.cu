@@ -192,9 +192,13 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchDe
 // of a Gaussian over the rectangle [x0, x1] x [y0, y1] of pixel centres:
 // 0 if its mean lies inside, else the best of the four edges, each a 1-D
 // concave quadratic maximised at its clamped stationary point.
-__device__ __forceinline__ float edge_max(float qa, float qb, float qc, float fixed, float lo, float hi) {
+// The stationary point comes from an approximate reciprocal of 2 qc: an
+// error d in it lowers the value found by |qc| d^2 (the quadratic is flat
+// at its maximum), some 1e-6 here, far inside the cull margin below.
+__device__ __forceinline__ float edge_max(float qa, float qb, float qc, float inv2qc, float fixed, float lo,
+                                          float hi) {
     // p(fixed, t) = qa fixed^2 + qb fixed t + qc t^2, maximum over t in [lo, hi]
-    float t = -qb * fixed / (2.f * qc);
+    float t = -qb * fixed * inv2qc;
     t = fminf(fmaxf(t, lo), hi);
     return qa * fixed * fixed + qb * fixed * t + qc * t * t;
 }
@@ -202,10 +206,11 @@ __device__ __forceinline__ float edge_max(float qa, float qb, float qc, float fi
 __device__ __forceinline__ float rect_max_falloff(float4 r0, float qc, float x0, float x1, float y0, float y1) {
     float ax = x0 - r0.x, bx = x1 - r0.x, ay = y0 - r0.y, by = y1 - r0.y;
     if (ax <= 0.f && bx >= 0.f && ay <= 0.f && by >= 0.f) return 0.f;
-    float m = edge_max(r0.z, r0.w, qc, ax, ay, by);
-    m = fmaxf(m, edge_max(r0.z, r0.w, qc, bx, ay, by));
-    m = fmaxf(m, edge_max(qc, r0.w, r0.z, ay, ax, bx));
-    m = fmaxf(m, edge_max(qc, r0.w, r0.z, by, ax, bx));
+    const float ic = rcp_approx(2.f * qc), ia = rcp_approx(2.f * r0.z);
+    float m = edge_max(r0.z, r0.w, qc, ic, ax, ay, by);
+    m = fmaxf(m, edge_max(r0.z, r0.w, qc, ic, bx, ay, by));
+    m = fmaxf(m, edge_max(qc, r0.w, r0.z, ia, ay, ax, bx));
+    m = fmaxf(m, edge_max(qc, r0.w, r0.z, ia, by, ax, bx));
     return m;
 }
 
