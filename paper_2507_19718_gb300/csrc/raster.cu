@@ -616,10 +616,11 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float (&a)[8], int l
 // leaves the tile.
 constexpr int kMaxChunks = 256;
 
-// Loss partials per tile of the training step: four (pixel slot classes
-// q mod 4) where the order may split a tile into parts, i.e. one-warp CTAs,
-// so that the loss does not depend on the split; one otherwise.
-__host__ __device__ constexpr int loss_slots(int threads) { return threads <= 32 ? 4 : 1; }
+// Loss partials per tile of the training step, one per pixel slot class
+// q mod SLOTS: as many as the parts the order may split a tile into (4 with
+// one-warp CTAs, 2 with larger ones), so that every part owns whole classes
+// and the loss does not depend on the split.
+__host__ __device__ constexpr int loss_slots(int threads) { return threads <= 32 ? 4 : 2; }
 
 // CTAs per SM the register allocation is sized for.  At 4 pixels per thread
 // 12 CTAs of 64 threads (80 registers; the 17 KB of shared memory per CTA
@@ -1276,18 +1277,21 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_const
     }
     __syncthreads();  // also makes the ranges written above visible to the CTA
     const uint32_t* cost = fb + 4 * (size_t)fb_stride;
-    // only a one-warp CTA splits its heavy tiles: a larger CTA walks a tile's
-    // list about as fast alone as its parts would, each part redoing the
-    // list filter (measured at 2 and 4 pixels per thread)
-    const uint32_t max_parts = rc.tile_w * rc.tile_h / rc.ppt <= 32 ? (uint32_t)min(4, rc.ppt) : 1u;
+    // A one-warp CTA splits a tile above half the mean load of a CTA into up
+    // to 4 parts.  A larger CTA walks a tile faster alone, and every part
+    // redoes the list filter and the gradient reductions, so it splits only
+    // the tiles that would outlast the mean load (above 0.75 of it), in 2
+    // parts: once the cache has trained, a few such tiles set the length of
+    // the launch (measured at 2 and 4 pixels per thread).
+    const bool one_warp = rc.tile_w * rc.tile_h / rc.ppt <= 32;
+    const uint32_t max_parts = (uint32_t)min(one_warp ? 4 : 2, rc.ppt);
     auto klass_of = [](float c) -> uint32_t {
         const float l = log2f(c + 1.0f) * 8.0f;
         return (uint32_t)(kOrderClasses - 1) - (uint32_t)fminf(l, (float)(kOrderClasses - 1));
     };
     if (use_fb) {
-        // a tile above half the mean load of a CTA is split
         const unsigned long long total = *reinterpret_cast<const unsigned long long*>(fb_state + kFbTotal);
-        const float split_at = 0.5f * (float)total / (float)grid;
+        const float split_at = (one_warp ? 0.5f : 0.75f) * (float)total / (float)grid;
         auto parts_of = [&](uint32_t c) -> uint32_t {
             return (max_parts > 1 && (float)c > split_at) ? max_parts : 1u;
         };

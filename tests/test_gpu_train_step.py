@@ -163,11 +163,14 @@ def test_train_step_matches_oracle_at_bench_scale(gpu, orc, case, launch):
 @pytest.mark.parametrize("tile,ppt", [((16, 16), 8), ((32, 8), 8), ((16, 16), 4), ((8, 8), 1)])
 def test_feedback_order_and_split_change_no_result(gpu, orc, tile, ppt):
     """A gradient launch orders the next launch's tiles by the work it
-    measured (same geometry) and, with one-warp CTAs, splits the heaviest
-    tiles into parts.  The training step's image and loss are the same bits
-    on the first call (plain order) and on the later ones, the gradients agree
-    up to the order of the FP32 atomics and match the oracle, and the split
-    happened (more work items than tiles) exactly where it can."""
+    measured (same geometry) and splits the heaviest tiles into parts (up to
+    4 with one-warp CTAs, 2 with larger ones, never more than a thread's
+    pixels).  The training step's image and loss are the same bits on the
+    first call (plain order) and on the later ones, the gradients agree up to
+    the order of the FP32 atomics and match the oracle, and the split
+    happened (more work items than tiles) exactly where it can: on this small
+    frame the grid has 4 CTAs per tile, so every tile outlasts a CTA's mean
+    load."""
     import torch
     w, h = 128, 96
     p = synth.gaussians(1024, synth.BASE_SEED + 2)
@@ -188,13 +191,13 @@ def test_feedback_order_and_split_change_no_result(gpu, orc, tile, ppt):
         gpu.train_batch([dict(params=P, cam=cam, target=T, grads=G, loss=loss, image=img)], cfg, ws, gpu.LOSS_HDR)
         c = ws.counters()
         runs.append((img.cpu().numpy(), float(loss), G.cpu().numpy().astype(np.float64), c["items_last"]))
-    one_warp = tile[0] * tile[1] // ppt <= 32
+    can_split = ppt > 1
     assert runs[0][3] == tiles
     for img, lv, g, items in runs[1:]:
         np.testing.assert_array_equal(img, runs[0][0])
         assert lv == runs[0][1]
         np.testing.assert_allclose(g, runs[0][2], rtol=1e-5, atol=1e-6 * np.abs(runs[0][2]).max())
-        assert (items > tiles) if one_warp else (items == tiles), (items, tiles)
+        assert (items > tiles) if can_split else (items == tiles), (items, tiles)
     # the split launch's gradient against the oracle's bounds, every pixel included
     _, dl = orc.loss_hdr(runs[2][0], tgt)
     g_mid, g_rad, bar, _ = grad_bounds(orc, p, cam, dl)
