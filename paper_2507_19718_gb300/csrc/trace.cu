@@ -275,7 +275,9 @@ __device__ float sphere_nee(const TraceDev& v, Philox& r, const float* x, const 
 // registers (1080p: 1.40 ms against 1.54 ms at MINB = 5).  MINB = 5 (no
 // spills): on a frame of a few waves or less the warps are there anyway and
 // the spills only cost (256^2 to 640x480: 17-19% faster than MINB = 16).
-template <int MINB>
+// CACHE: whether a cache is given (Algorithm 1 and natural-termination
+// sampling); without one its per-path state takes no registers.
+template <int MINB, bool CACHE>
 __global__ void __launch_bounds__(128, MINB) k_trace(TraceDev v, CamDev cam, const float* __restrict__ cache,
                                                      float* __restrict__ targets, float* __restrict__ image) {
     int i = blockIdx.x * 16 + (threadIdx.x & 15);
@@ -289,7 +291,7 @@ __global__ void __launch_bounds__(128, MINB) k_trace(TraceDev v, CamDev cam, con
     // the volume
     for (int k = 0; k < v.K; ++k)
         for (int c = 0; c < 3; ++c) targets[((size_t)k * 3 + c) * HW + pix] = 0.0f;
-    const bool cache_on = cache != nullptr;
+    const bool cache_on = CACHE;
     for (int s = 0; s < v.spp; ++s) {
         Philox r;
         r.init((uint32_t)(j * cam.W + i), (uint32_t)s, v.frame, v.k0, v.k1);
@@ -492,10 +494,11 @@ cudaError_t launch_trace(const gsc_scene* sc, const CamDev& cam, const gsc_trace
     dim3 grid((cam.W + 15) / 16, (cam.H + 7) / 8);
     PhaseScope ph(kPhTrace, s, 1);
     // two full waves at 16 CTAs per SM: below that, the spill-free budget
-    if ((size_t)grid.x * grid.y >= (size_t)2 * 16 * sm_count())
-        k_trace<16><<<grid, 128, 0, s>>>(v, cam, cache, targets, image);
+    const bool many = (size_t)grid.x * grid.y >= (size_t)2 * 16 * sm_count();
+    if (cache)
+        (many ? k_trace<16, true> : k_trace<5, true>)<<<grid, 128, 0, s>>>(v, cam, cache, targets, image);
     else
-        k_trace<5><<<grid, 128, 0, s>>>(v, cam, cache, targets, image);
+        (many ? k_trace<16, false> : k_trace<5, false>)<<<grid, 128, 0, s>>>(v, cam, cache, targets, image);
     return cudaGetLastError();
 }
 
