@@ -300,7 +300,7 @@ def run_ours(args, world, rank, local):
                      autotune.Trial((16, 16), 128, 256, 1, float("nan"))]
         else:
             adapt = autotune.drift_candidates(best_b, trials_b)
-        sel = loop.adapt_train_launch([t.cfg() for t in adapt])
+        sel = loop.adapt_train_launch([t.cfg() for t in adapt], prior=[t.ms for t in adapt])
     stream = torch.cuda.current_stream()
 
     # warm-up (also sizes nothing: the pair capacity is fixed)

@@ -135,17 +135,31 @@ class OnlineSelector:
     moves to a candidate that is faster by more than ``margin``.  When the
     current choice's time rises more than ``drift`` above its lowest since it
     was chosen (the data changed), the next steps explore every other
-    candidate at once.  Times
+    candidate at once.  A candidate whose newest time is more than ``far``
+    above the current choice's is left out of the regular rounds but every
+    ``far_every``-th (an exploration step costs its whole gap; at 1080p one
+    pixel per thread runs 35-55% behind four on every frame of the drift),
+    and still runs in the rounds a drift starts.  ``prior`` (optional, one
+    time per candidate, None or NaN where unknown) seeds the other
+    candidates' times, e.g. from the autotuner's trials.  Times
     come back through ``report`` whenever they are known (a step's device
     time is read without waiting for it)."""
 
     def __init__(self, n: int, explore_every: int = 4, alpha: float = 0.25, margin: float = 0.03,
-                 drift: float = 0.05):
-        if n < 1 or explore_every < 2:
-            raise ValueError("need at least one candidate and explore_every >= 2")
+                 drift: float = 0.05, far: float = 0.3, far_every: int = 8, prior=None):
+        if n < 1 or explore_every < 2 or far_every < 1:
+            raise ValueError("need at least one candidate, explore_every >= 2 and far_every >= 1")
+        if prior is not None and len(prior) != n:
+            raise ValueError("prior needs one entry per candidate")
         self.n, self.explore_every, self.alpha, self.margin, self.drift = n, explore_every, alpha, margin, drift
+        self.far, self.far_every = far, far_every
         self.current = 0
         self.est = [None] * n
+        if prior is not None:
+            for j in range(1, n):
+                if prior[j] is not None and prior[j] == prior[j]:  # NaN: unknown
+                    self.est[j] = float(prior[j])
+        self._rounds = 0          # regular exploration rounds so far
         self.runs = [0] * n
         self.switches = 0
         self._step = 0
@@ -156,18 +170,25 @@ class OnlineSelector:
     def choose(self) -> int:
         """Index of the candidate for the next step."""
         self._step += 1
+        i = self.current
         if self.n > 1 and (self._burst > 0 or self._step % self.explore_every == 0):
+            burst = self._burst > 0
             self._burst = max(0, self._burst - 1)
             self._step = 0            # the next regular exploration counts from here
+            if not burst:
+                self._rounds += 1
+            allow_far = burst or self._rounds % self.far_every == 0
             for _ in range(self.n):
                 self._next = (self._next + 1) % self.n
-                if self._next != self.current:
+                if self._next != self.current and (allow_far or not self._is_far(self._next)):
+                    i = self._next
                     break
-            i = self._next
-        else:
-            i = self.current
         self.runs[i] += 1
         return i
+
+    def _is_far(self, j: int) -> bool:
+        cur, e = self.est[self.current], self.est[j]
+        return cur is not None and e is not None and e > cur * (1.0 + self.far)
 
     def report(self, i: int, ms: float):
         """Device time of a step that ran candidate ``i``."""

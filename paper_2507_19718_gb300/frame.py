@@ -162,17 +162,18 @@ class FrameLoop:
             gsc.cache_backward(L.params, c, cfg_b, self.ws, self.dL[k], L.grads, stream=stream)
             gsc.cache_step(L.params, L.grads, L.m, L.v, adam, stream=stream)
 
-    def adapt_train_launch(self, cfgs, explore_every: int = 6):
+    def adapt_train_launch(self, cfgs, explore_every: int = 6, prior=None):
         """Choose the training step's launch configuration among ``cfgs``
         while the cache trains (``autotune.OnlineSelector``; the first is the
         starting choice): every frame's training step is timed on the device
-        and every ``explore_every``-th frame runs another candidate.  The
+        and every ``explore_every``-th frame runs another candidate (``prior``:
+        the candidates' times if known, e.g. from the autotuner).  The
         configuration changes no result beyond the order of the FP32 sums.
         It applies to the one-launch training step (C <= 0); the separate
         launches of a cache-reading frame keep ``cfg_bwd``."""
         from .autotune import OnlineSelector
         cfgs = list(cfgs)
-        self._adapt = dict(cfgs=cfgs, sel=OnlineSelector(len(cfgs), explore_every), pending=[],
+        self._adapt = dict(cfgs=cfgs, sel=OnlineSelector(len(cfgs), explore_every, prior=prior), pending=[],
                            pool=[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                                  for _ in range(3)], slot=0)
         self.cfg_bwd = cfgs[0]

@@ -81,3 +81,32 @@ def test_drift_candidates_take_the_next_lower_pixels_per_thread():
     got = drift_candidates(trials[4], trials)
     assert got == [trials[4], trials[3]]
     assert drift_candidates(best, [best]) == [best]
+
+
+def test_far_candidates_wait_for_every_eighth_round_or_a_drift():
+    # the third candidate runs 50% behind the first: after its first
+    # measurement the regular rounds take only the second, except every
+    # 8th round
+    sel = OnlineSelector(3, explore_every=4)
+    seq = _run(sel, lambda i, f: (2.0, 2.4, 3.0)[i], 4 * 16)
+    rounds = [seq[k] for k in range(3, len(seq), 4)]
+    assert rounds[:2] == [1, 2]
+    assert rounds[2:7] == [1] * 5 and rounds[7] == 2
+    assert sel.runs[2] == 3 and sel.current == 0
+    # a drift of the current choice explores the far candidate at once
+    sel = OnlineSelector(3, explore_every=8)
+    cost = lambda i, f: (2.0, 2.4, 3.0)[i] if f < 20 else (3.0, 2.9, 2.2)[i]
+    seq = _run(sel, cost, 30, lag=1)
+    assert 2 in seq[20:26] and sel.current == 2
+
+
+def test_prior_times_keep_a_known_slow_candidate_out_of_the_first_rounds():
+    sel = OnlineSelector(3, explore_every=4, prior=[2.9, 3.2, 4.2])
+    seq = _run(sel, lambda i, f: (2.7, 3.2, 4.2)[i], 28)
+    assert [seq[k] for k in range(3, 28, 4)] == [1] * 7
+    assert sel.runs[2] == 0
+    # unknown entries (None, NaN) are measured as before
+    sel = OnlineSelector(3, explore_every=4, prior=[None, float("nan"), 4.2])
+    assert _run(sel, lambda i, f: (2.7, 3.2, 4.2)[i], 8) == [0, 0, 0, 1, 0, 0, 0, 1]
+    with pytest.raises(ValueError):
+        OnlineSelector(3, prior=[1.0, 2.0])
