@@ -6,6 +6,8 @@ the whole forward + backward replays from a captured CUDA graph."""
 import numpy as np
 import pytest
 
+from parity import fp32_sum_bar
+
 from paper_2507_19718_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -208,10 +210,13 @@ def test_frame_loop_adaptive_training_launch(gpu):
 
 
 @pytest.mark.parametrize("kind", [0, 1])
-def test_train_batch_equals_render_loss_backward(gpu, kind):
+def test_train_batch_equals_render_loss_backward(gpu, orc, kind):
     """gsc_train_batch (render + HDR loss + backward in one launch) against
     the separate calls on the same views: images bit for bit, losses to
-    summation order, gradients to atomic order."""
+    summation order, gradients to the order of their FP32 sums (the two
+    launches may split tiles differently, which regroups the sums): within
+    twice the FP32 summation bar of each (Gaussian, slot), summed over the
+    views that share the scene, plus 1e-4 relative."""
     import torch
     scenes, views = _setup(gpu)
     cfg = gpu.raster_cfg(tile=(16, 16), list_capacity=256, bin_size=32, pixels_per_thread=2)
@@ -240,9 +245,16 @@ def test_train_batch_equals_render_loss_backward(gpu, kind):
     for v, im in zip(views, imgs_a):
         assert torch.equal(v["image"], im)
     np.testing.assert_allclose(losses_a.cpu().numpy(), losses_b, rtol=2e-6)
-    for a, b in zip(grads_a, grads_b):
-        a, b = a.cpu().numpy(), b.cpu().numpy()
-        np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-6 * np.abs(b).max())
+    bars = [np.zeros(tuple(s.shape)) for s in scenes]
+    for i, v in enumerate(views):
+        cam = synth.orbit_camera(*SIZES[i], 37.0 * i)  # the view's camera, as _setup made it
+        p_np, dl = v["params"].cpu().numpy(), v["dL_dimage"].cpu().numpy()
+        _, _, ab, nterm, _ = orc.render_backward_bounds(p_np, cam, dl)
+        bars[v["scene"]] += fp32_sum_bar(orc, p_np, cam, ab, nterm)
+    for a, b, bar in zip(grads_a, grads_b, bars):
+        a, b = a.cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64)
+        bad = np.abs(a - b) > 2 * bar + 1e-4 * np.abs(b)
+        assert not bad.any(), (np.argwhere(bad)[:5].tolist(), a[bad][:5], b[bad][:5], bar[bad][:5])
         assert np.abs(b).max() > 0
 
 
