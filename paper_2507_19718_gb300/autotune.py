@@ -135,24 +135,27 @@ class OnlineSelector:
     moves to a candidate that is faster by more than ``margin``.  When the
     current choice's time rises more than ``drift`` above its lowest since it
     was chosen (the data changed), the next steps explore every other
-    candidate at once.  A candidate whose newest time is more than ``far``
-    above the current choice's is left out of the regular rounds but every
-    ``far_every``-th (an exploration step costs its whole gap; at 1080p one
-    pixel per thread runs 35-55% behind four on every frame of the drift),
-    and still runs in the rounds a drift starts.  ``prior`` (optional, one
+    candidate at once.  An exploration step costs the candidate's whole gap
+    (at 1080p one pixel per thread runs 35-55% behind four on every frame of
+    the drift, two per thread about 20% on the first 20 frames), and a
+    drift is gradual, so a regular round skips a candidate until
+    1 + gap / ``gap_step`` rounds (at most ``far_every``) have passed since it
+    last ran, gap being its newest time over the current choice's, less 1;
+    a candidate never measured runs at the first round, and the rounds a
+    drift starts run every candidate.  ``prior`` (optional, one
     time per candidate, None or NaN where unknown) seeds the other
     candidates' times, e.g. from the autotuner's trials.  Times
     come back through ``report`` whenever they are known (a step's device
     time is read without waiting for it)."""
 
     def __init__(self, n: int, explore_every: int = 4, alpha: float = 0.25, margin: float = 0.03,
-                 drift: float = 0.05, far: float = 0.3, far_every: int = 8, prior=None):
+                 drift: float = 0.05, gap_step: float = 0.05, far_every: int = 8, prior=None):
         if n < 1 or explore_every < 2 or far_every < 1:
             raise ValueError("need at least one candidate, explore_every >= 2 and far_every >= 1")
         if prior is not None and len(prior) != n:
             raise ValueError("prior needs one entry per candidate")
         self.n, self.explore_every, self.alpha, self.margin, self.drift = n, explore_every, alpha, margin, drift
-        self.far, self.far_every = far, far_every
+        self.gap_step, self.far_every = gap_step, far_every
         self.current = 0
         self.est = [None] * n
         if prior is not None:
@@ -160,6 +163,7 @@ class OnlineSelector:
                 if prior[j] is not None and prior[j] == prior[j]:  # NaN: unknown
                     self.est[j] = float(prior[j])
         self._rounds = 0          # regular exploration rounds so far
+        self._last = [None] * n   # round in which each candidate last ran
         self.runs = [0] * n
         self.switches = 0
         self._step = 0
@@ -177,18 +181,25 @@ class OnlineSelector:
             self._step = 0            # the next regular exploration counts from here
             if not burst:
                 self._rounds += 1
-            allow_far = burst or self._rounds % self.far_every == 0
+            nxt = self._next
             for _ in range(self.n):
-                self._next = (self._next + 1) % self.n
-                if self._next != self.current and (allow_far or not self._is_far(self._next)):
-                    i = self._next
+                nxt = (nxt + 1) % self.n
+                if nxt != self.current and (burst or self._due(nxt)):
+                    i = self._next = nxt
+                    self._last[i] = self._rounds
                     break
         self.runs[i] += 1
         return i
 
-    def _is_far(self, j: int) -> bool:
+    def _due(self, j: int) -> bool:
+        """Whether candidate j's next regular exploration is due."""
         cur, e = self.est[self.current], self.est[j]
-        return cur is not None and e is not None and e > cur * (1.0 + self.far)
+        if cur is None or e is None:
+            return True
+        gap = max(0.0, e / cur - 1.0)
+        wait = min(self.far_every, 1 + int(gap / self.gap_step + 1e-6))
+        last = self._last[j] if self._last[j] is not None else 0  # a prior counts from the start
+        return self._rounds - last >= wait
 
     def report(self, i: int, ms: float):
         """Device time of a step that ran candidate ``i``."""

@@ -18,12 +18,16 @@ def _run(sel, cost, frames, lag=0):
     return seq
 
 
-def test_keeps_the_fastest_and_explores_the_others_in_turn():
+def test_keeps_the_fastest_and_explores_the_others_by_their_gap():
+    # gaps 13.8% and 20.7%: the others run at the first rounds, then again
+    # after 1 + floor(gap / 5%) rounds, i.e. every 3rd and every 5th round
     sel = OnlineSelector(3, explore_every=4)
-    seq = _run(sel, lambda i, f: (2.9, 3.3, 3.5)[i], 24)
-    assert seq == [0, 0, 0, 1, 0, 0, 0, 2] * 3
+    seq = _run(sel, lambda i, f: (2.9, 3.3, 3.5)[i], 48)
+    rounds = [seq[k] for k in range(3, 48, 4)]
+    assert rounds == [1, 2, 0, 1, 0, 0, 2, 1, 0, 0, 1, 2]
+    assert all(seq[k] == 0 for k in range(48) if k % 4 != 3)
     assert sel.current == 0 and sel.switches == 0
-    assert sel.runs == [18, 3, 3]
+    assert sel.runs == [41, 4, 3]
 
 
 def test_follows_a_drift_of_the_fastest_candidate():
@@ -47,9 +51,10 @@ def test_a_drift_of_the_current_choice_explores_at_once():
     assert 1 in seq[10:15] and 2 in seq[10:15]
     assert sel.current == 1 and seq[-3:] == [1, 1, 1]
     # a steady choice never triggers an exploration between regular rounds
+    # (the others, 20% and 28% behind, wait 5 and 6 rounds after their first run)
     sel = OnlineSelector(3, explore_every=8)
     assert _run(sel, lambda i, f: (2.5, 3.0, 3.2)[i] * (1 + 0.01 * (f % 3)), 32, lag=2) == \
-        ([0] * 7 + [1] + [0] * 7 + [2]) * 2
+        [0] * 7 + [1] + [0] * 7 + [2] + [0] * 16
 
 
 def test_margin_keeps_the_choice_between_near_ties():
@@ -83,16 +88,13 @@ def test_drift_candidates_take_the_next_lower_pixels_per_thread():
     assert drift_candidates(best, [best]) == [best]
 
 
-def test_far_candidates_wait_for_every_eighth_round_or_a_drift():
-    # the third candidate runs 50% behind the first: after its first
-    # measurement the regular rounds take only the second, except every
-    # 8th round
+def test_far_candidates_wait_at_most_eight_rounds_or_for_a_drift():
+    # 20% behind: every 5th round; 50% behind: every 8th (the cap)
     sel = OnlineSelector(3, explore_every=4)
     seq = _run(sel, lambda i, f: (2.0, 2.4, 3.0)[i], 4 * 16)
     rounds = [seq[k] for k in range(3, len(seq), 4)]
-    assert rounds[:2] == [1, 2]
-    assert rounds[2:7] == [1] * 5 and rounds[7] == 2
-    assert sel.runs[2] == 3 and sel.current == 0
+    assert rounds == [1, 2, 0, 0, 0, 1, 0, 0, 0, 2, 1, 0, 0, 0, 0, 1]
+    assert sel.runs == [58, 4, 2] and sel.current == 0
     # a drift of the current choice explores the far candidate at once
     sel = OnlineSelector(3, explore_every=8)
     cost = lambda i, f: (2.0, 2.4, 3.0)[i] if f < 20 else (3.0, 2.9, 2.2)[i]
@@ -100,13 +102,15 @@ def test_far_candidates_wait_for_every_eighth_round_or_a_drift():
     assert 2 in seq[20:26] and sel.current == 2
 
 
-def test_prior_times_keep_a_known_slow_candidate_out_of_the_first_rounds():
+def test_prior_times_keep_known_slow_candidates_out_of_the_first_rounds():
+    # with the autotuner's times the gaps are known from the start (18.5% and
+    # 55.6% behind the first measured step): waits of 4 and 8 rounds
     sel = OnlineSelector(3, explore_every=4, prior=[2.9, 3.2, 4.2])
     seq = _run(sel, lambda i, f: (2.7, 3.2, 4.2)[i], 28)
-    assert [seq[k] for k in range(3, 28, 4)] == [1] * 7
-    assert sel.runs[2] == 0
+    assert [seq[k] for k in range(3, 28, 4)] == [0, 0, 0, 1, 0, 0, 0]
+    assert sel.runs == [27, 1, 0]
     # unknown entries (None, NaN) are measured as before
     sel = OnlineSelector(3, explore_every=4, prior=[None, float("nan"), 4.2])
-    assert _run(sel, lambda i, f: (2.7, 3.2, 4.2)[i], 8) == [0, 0, 0, 1, 0, 0, 0, 1]
+    assert _run(sel, lambda i, f: (2.7, 3.2, 4.2)[i], 8) == [0, 0, 0, 1, 0, 0, 0, 0]
     with pytest.raises(ValueError):
         OnlineSelector(3, prior=[1.0, 2.0])
