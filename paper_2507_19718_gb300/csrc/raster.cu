@@ -1068,10 +1068,43 @@ __device__ __forceinline__ bool project_grad(const float4& a0, const float4& a1,
 
 // 2D gradients -> packed parameter gradients (+=), with vector atomics when
 // two views of the batch share a parameter set.
+// The training step's loss of view v from its tiles' partials (`slots` per
+// tile), summed by one 128-thread block in a fixed order in FP64: four
+// strided accumulators per thread, then the warps in order.  The gradient
+// kernels below give their first nviews blocks this work, so that it runs
+// beside theirs instead of as a launch of its own.
+__device__ void view_loss_sum(const BatchDev& b, const float* __restrict__ tile_loss, int slots, int v) {
+    __shared__ double sm[4];
+    const ViewDev& vw = b.v[v];
+    const uint32_t n = (uint32_t)slots * (uint32_t)vw.tiles_x * (uint32_t)vw.tiles_y;
+    const float* x = tile_loss + (size_t)slots * vw.tile_off;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    uint32_t i = threadIdx.x;
+    for (; i + 384 < n; i += 512) {
+        a0 += (double)x[i];
+        a1 += (double)x[i + 128];
+        a2 += (double)x[i + 256];
+        a3 += (double)x[i + 384];
+    }
+    for (; i < n; i += 128) a0 += (double)x[i];
+    double acc = (a0 + a1) + (a2 + a3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0 && vw.loss) *vw.loss = (float)(((sm[0] + sm[1]) + (sm[2] + sm[3])) * (double)vw.invk);
+}
+
 __global__ void __launch_bounds__(128) k_project_bwd(const __grid_constant__ BatchDev b, RasterDev rc,
                                                      const uint32_t* __restrict__ cnt,
-                                                     const float4* __restrict__ g2d, int shared_params) {
-    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+                                                     const float4* __restrict__ g2d, int shared_params,
+                                                     const float* __restrict__ tile_loss, int slots) {
+    const uint32_t nl = tile_loss ? (uint32_t)b.nviews : 0u;
+    if (blockIdx.x < nl) {
+        view_loss_sum(b, tile_loss, slots, (int)blockIdx.x);
+        return;
+    }
+    uint32_t g = (blockIdx.x - nl) * blockDim.x + threadIdx.x;
     if (g >= b.total_g || cnt[g] == 0) return;
     const ViewDev& vw = b.v[view_of_gaussian(b, g)];
     const size_t l = g - vw.g_off;
@@ -1107,8 +1140,14 @@ __global__ void __launch_bounds__(128) k_project_bwd(const __grid_constant__ Bat
 __global__ void __launch_bounds__(128, 8) k_project_bwd_step(const __grid_constant__ BatchDev b, RasterDev rc,
                                                           const uint32_t* __restrict__ cnt,
                                                           const float4* __restrict__ g2d,
-                                                          const __grid_constant__ AdamDev adam) {
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+                                                          const __grid_constant__ AdamDev adam,
+                                                          const float* __restrict__ tile_loss, int slots) {
+    const uint32_t nl = tile_loss ? (uint32_t)b.nviews : 0u;
+    if (blockIdx.x < nl) {
+        view_loss_sum(b, tile_loss, slots, (int)blockIdx.x);
+        return;
+    }
+    const uint32_t g = (blockIdx.x - nl) * blockDim.x + threadIdx.x;
     if (g >= b.total_g) return;
     const ViewDev& vw = b.v[view_of_gaussian(b, g)];
     const size_t l = g - vw.g_off;
@@ -1563,37 +1602,18 @@ cudaError_t launch_render(const BatchDev& b, const RasterDev& rc, gsc_workspace*
     GSC_TILE_DISPATCH(render_t, b, rc, ws, vals, s)
 }
 
-// per view: the sum of its tiles' loss partials (in a fixed order, FP64) / k
-constexpr int kViewLossThreads = 1024;
-__global__ void __launch_bounds__(kViewLossThreads) k_view_loss(const __grid_constant__ BatchDev b,
-                                                                const float* __restrict__ tile_loss, int slots) {
-    __shared__ double sm[32];
-    const ViewDev& vw = b.v[blockIdx.x];
-    // `slots` partials per tile
-    const uint32_t n = (uint32_t)slots * (uint32_t)vw.tiles_x * (uint32_t)vw.tiles_y;
-    double acc = 0.0;
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) acc += (double)tile_loss[(size_t)slots * vw.tile_off + i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sm[k];
-        if (vw.loss) *vw.loss = (float)(t * (double)vw.invk);
-    }
-}
-
+// tile_loss (nullable): the training step's loss partials, `slots` per tile,
+// summed into each view's loss by the first blocks of the launch
 static cudaError_t project_backward(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, bool shared_params,
-                                    const AdamDev* adam, cudaStream_t s) {
-    uint32_t nblk = (b.total_g + 127) / 128;
+                                    const AdamDev* adam, const float* tile_loss, int slots, cudaStream_t s) {
+    uint32_t nblk = (b.total_g + 127) / 128 + (tile_loss ? (uint32_t)b.nviews : 0u);
     if (nblk == 0) nblk = 1;
     if (adam) {
         PhaseScope ph(kPhAdam, s, 1);
-        k_project_bwd_step<<<nblk, 128, 0, s>>>(b, rc, ws->cnt, ws->g2d, *adam);
+        k_project_bwd_step<<<nblk, 128, 0, s>>>(b, rc, ws->cnt, ws->g2d, *adam, tile_loss, slots);
     } else {
         PhaseScope ph(kPhProjectBwd, s, 1);
-        k_project_bwd<<<nblk, 128, 0, s>>>(b, rc, ws->cnt, ws->g2d, shared_params ? 1 : 0);
+        k_project_bwd<<<nblk, 128, 0, s>>>(b, rc, ws->cnt, ws->g2d, shared_params ? 1 : 0, tile_loss, slots);
     }
     return cudaGetLastError();
 }
@@ -1608,7 +1628,7 @@ cudaError_t launch_render_backward(const BatchDev& b, const RasterDev& rc, gsc_w
         e = launch();
     }
     if (e != cudaSuccess) return e;
-    return project_backward(b, rc, ws, shared_params, nullptr, s);
+    return project_backward(b, rc, ws, shared_params, nullptr, nullptr, 0, s);
 }
 
 cudaError_t launch_train(const BatchDev& b, const RasterDev& rc, gsc_workspace* ws, const uint32_t* vals,
@@ -1623,13 +1643,8 @@ cudaError_t launch_train(const BatchDev& b, const RasterDev& rc, gsc_workspace* 
         };
         e = launch();
     }
-    if (e == cudaSuccess) {
-        PhaseScope ph(kPhLoss, s, 1);
-        k_view_loss<<<b.nviews, kViewLossThreads, 0, s>>>(b, ws->red, loss_slots(rc.tile_w * rc.tile_h / rc.ppt));
-        e = cudaGetLastError();
-    }
     if (e != cudaSuccess) return e;
-    return project_backward(b, rc, ws, shared_params, adam, s);
+    return project_backward(b, rc, ws, shared_params, adam, ws->red, loss_slots(rc.tile_w * rc.tile_h / rc.ppt), s);
 }
 
 }  // namespace gsc
