@@ -1324,8 +1324,11 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_const
     // the launch (measured at 2 and 4 pixels per thread).
     const bool one_warp = rc.tile_w * rc.tile_h / rc.ppt <= 32;
     const uint32_t max_parts = (uint32_t)min(one_warp ? 4 : 2, rc.ppt);
+    // one CTA classifies every tile, so the per-tile arithmetic is kept to
+    // a few instructions: the hardware log2 (a class only decides which CTA
+    // renders a tile, never a result)
     auto klass_of = [](float c) -> uint32_t {
-        const float l = log2f(c + 1.0f) * 8.0f;
+        const float l = __log2f(c + 1.0f) * 8.0f;
         return (uint32_t)(kOrderClasses - 1) - (uint32_t)fminf(l, (float)(kOrderClasses - 1));
     };
     if (use_fb) {
@@ -1334,8 +1337,8 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_const
         auto parts_of = [&](uint32_t c) -> uint32_t {
             return (max_parts > 1 && (float)c > split_at) ? max_parts : 1u;
         };
-        auto item_cost = [](uint32_t c, uint32_t p) -> float {  // a part redoes the per-entry work
-            return (float)c * (float)(p + 1) / (float)(2 * p);
+        auto item_cost = [](uint32_t c, uint32_t p) -> float {  // a part redoes the per-entry work: (p + 1) / 2p
+            return (float)c * (p == 1u ? 1.0f : (p == 2u ? 0.75f : 0.625f));
         };
         for (uint32_t t = threadIdx.x; t < nt; t += kOrderThreads) {
             const uint32_t c = cost[t], p = parts_of(c);
