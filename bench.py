@@ -344,26 +344,50 @@ def run_ours(args, world, rank, local):
     # camera pose goes in (a gsc_camera struct, read by the calls), and the
     # path-traced display image and the level losses come back to pinned host
     # memory (FrameLoop.frame_to_host: the image copy runs beside the
-    # training step); the host waits for every frame's results.
-    host_img = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, pin_memory=True)
-    host_loss = torch.empty((LEVELS,), dtype=torch.float32, pin_memory=True)
-    loop.restore(snap)
-    gsc.profile_read(reset=True)
-    gsc.profile_enable(True)
-    barrier(world)
-    torch.cuda.synchronize()
-    t_host0 = time.perf_counter()
-    for f in range(args.warmup, args.warmup + K):
-        pose = bytes(cams[f])                     # the caller's pose, host memory
-        c = gsc.Camera.from_buffer_copy(pose)
-        loop.frame_to_host(c, f, host_img, host_loss, stream)
-        stream.synchronize()
-    torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t_host0) * 1e3
-    gsc.profile_enable(False)
-    trace_e = gsc.profile_read(reset=True)["trace"][0]
-    barrier(world)
-    e2e_max = max_over_ranks(e2e_ms - trace_e, world)
+    # training step), where the host reads them.  Two ways of driving it:
+    # with one frame in flight (the host queues frame f + 1, then waits for
+    # frame f's results in their own pinned buffers, as a viewer shows one
+    # frame while the next renders), and waiting for every frame before
+    # queueing the next.
+    host_img = [torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    host_loss = [torch.empty((LEVELS,), dtype=torch.float32, pin_memory=True) for _ in range(2)]
+
+    def end_to_end(in_flight):
+        loop.restore(snap)
+        gsc.profile_read(reset=True)
+        gsc.profile_enable(True)
+        barrier(world)
+        torch.cuda.synchronize()
+        checks = []
+        pending = []
+        t_host0 = time.perf_counter()
+        for i, f in enumerate(range(args.warmup, args.warmup + K)):
+            pose = bytes(cams[f])                     # the caller's pose, host memory
+            c = gsc.Camera.from_buffer_copy(pose)
+            b = i % 2
+            loop.frame_to_host(c, f, host_img[b], host_loss[b], stream)
+            done = torch.cuda.Event()
+            done.record(stream)
+            pending.append((done, b))
+            while len(pending) > in_flight:           # read the oldest frame's results on the host
+                ev, pb = pending.pop(0)
+                ev.synchronize()
+                checks.append(float(host_loss[pb].sum()) + float(host_img[pb][0, 0, 0]))
+        for ev, pb in pending:
+            ev.synchronize()
+            checks.append(float(host_loss[pb].sum()) + float(host_img[pb][0, 0, 0]))
+        ms = (time.perf_counter() - t_host0) * 1e3
+        gsc.profile_enable(False)
+        trace = gsc.profile_read(reset=True)["trace"][0]
+        barrier(world)
+        assert len(checks) == K and all(x == x for x in checks)
+        return max_over_ranks(ms - trace, world)
+
+    # an untimed pass first: the first pass through the host path pays
+    # one-time costs (about 0.2 ms per frame over 20 frames, measured)
+    end_to_end(1)
+    e2e_max = end_to_end(1)
+    e2e_sync_max = end_to_end(0)
 
     # ---- the same frames with render, loss and backward as separate launches
     # (the path the frame takes when the tracer reads the cache images)
@@ -457,7 +481,10 @@ def run_ours(args, world, rank, local):
                               "note": "render batch + HDR loss + backward batch as separate launches"},
         "roofline": roof, "clocks": clocks, "gpu_launches": int(launches),
         "e2e": {"value": round(e2e_max / K, 3), "unit": "ms/frame",
-                "note": "host-timed frames through the public API, the tracer's device time taken out",
+                "note": "host-timed frames through the public API (pose in, display image and level losses "
+                        "read on the host every frame), one frame in flight; the tracer's device time taken out",
+                "sync_value": round(e2e_sync_max / K, 3),
+                "sync_note": "the same with the host waiting for every frame before queueing the next",
                 "h2d_bytes_per_step": 84, "d2h_bytes_per_step": 3 * WIDTH * HEIGHT * 4 + LEVELS * 4},
     }
     return result, loop.cfg_bwd or loop.cfg
