@@ -268,6 +268,7 @@ size_t layout(int64_t NG, int64_t NP, int32_t W, int32_t H, int32_t NV, gsc_work
     w->tile_order = (uint32_t*)take(4 * 4 * (size_t)tiles);  // up to 4 parts per tile
     w->fb = (uint32_t*)take(4 * 5 * (size_t)tiles);
     w->fb_state = (uint32_t*)take(4 * kFbWords);
+    w->order_cls = (uint32_t*)take(4 * 2 * kOrderClasses);
     w->g2d = (float4*)take(sizeof(float4) * 3 * ng);
     w->red = (float*)take(sizeof(float) * red);
     w->red_floats = red;
@@ -428,6 +429,7 @@ gsc_status gsc_workspace_create(void* device_buffer, size_t bytes, int64_t max_g
     if (e == cudaSuccess) e = cudaMemset(ws->counters, 0, sizeof(uint32_t) * kCounterWords);
     if (e == cudaSuccess) e = cudaMemset(ws->stats, 0, sizeof(unsigned long long) * kStatWords);
     if (e == cudaSuccess) e = cudaMemset(ws->fb_state, 0, sizeof(uint32_t) * kFbWords);
+    if (e == cudaSuccess) e = cudaMemset(ws->order_cls, 0, sizeof(uint32_t) * 2 * kOrderClasses);
     if (e != cudaSuccess) {
         delete ws;
         return cuda_fail(e, "workspace init");

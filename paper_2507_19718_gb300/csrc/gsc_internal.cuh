@@ -121,8 +121,11 @@ enum : int { kCntPairs = 0, kCntPairsMax = 1, kCntTilesFwd = 2, kCntTilesBwd = 3
 // feedback state: launches so far (its parity picks the buffer the next
 // gradient kernel writes), signature of the batch geometry the last
 // feedback belongs to (0: none), number of work items of the current order
-// and (words 4-5, 64-bit) the summed per-tile cost of the coming order
-enum : int { kFbParity = 0, kFbSignature = 1, kFbItems = 2, kFbTotal = 4, kFbWords = 8 };
+// and (words 4-5, 64-bit) the summed per-tile cost of the coming order;
+// kFbUse: whether the current order came from the feedback (1) or not (0)
+enum : int { kFbParity = 0, kFbSignature = 1, kFbItems = 2, kFbUse = 3, kFbTotal = 4, kFbWords = 8 };
+// cost classes of the tile order: per class a count and a cursor
+constexpr int kOrderClasses = 256;
 // A work item of the persistent render kernels: a tile, or part `part` of
 // `1 << lp` parts of a tile (the part owns the tile's pixel rows whose slot
 // q of the thread has q mod (1 << lp) == part).  A whole tile is its id.
@@ -166,6 +169,7 @@ struct gsc_workspace {
     // every gradient launch, and a scratch of per-tile costs: 5 x max_tiles
     uint32_t* fb;
     uint32_t* fb_state;     // kFbWords: launch parity, geometry of the feedback, item count
+    uint32_t* order_cls;    // 2 x kOrderClasses: work items per cost class, then each class's cursor
     float4* g2d;       // 3 x NG: 2D gradients
     float* red;        // reduction scratch for losses
     size_t red_floats;

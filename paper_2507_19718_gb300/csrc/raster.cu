@@ -1192,7 +1192,35 @@ static int bits_for(uint32_t n) {
 // whatever the atomics give, since it only decides which CTA renders a tile,
 // never a result.
 constexpr int kOrderThreads = 1024;
-constexpr int kOrderClasses = 256;
+
+// Cost class of a tile or bin (0: the most costly), with the hardware log2:
+// a class only decides which CTA renders a tile, never a result.
+__device__ __forceinline__ uint32_t order_class(float c) {
+    const float l = __log2f(c + 1.0f) * 8.0f;
+    return (uint32_t)(kOrderClasses - 1) - (uint32_t)fminf(l, (float)(kOrderClasses - 1));
+}
+// Parts a tile of feedback cost c is split into.  A one-warp CTA splits a
+// tile above half the mean load of a CTA into up to 4 parts.  A larger CTA
+// walks a tile faster alone, and every part redoes the list filter and the
+// gradient reductions, so it splits only the tiles that would outlast the
+// mean load (above 0.75 of it), in 2 parts: once the cache has trained, a
+// few such tiles set the length of the launch (measured at 2 and 4 pixels
+// per thread).  `total`: the summed cost of all tiles, `grid`: the CTAs.
+struct SplitRule {
+    float split_at;
+    uint32_t max_parts;
+    __device__ SplitRule(const RasterDev& rc, unsigned long long total, int grid) {
+        const bool one_warp = rc.tile_w * rc.tile_h / rc.ppt <= 32;
+        max_parts = (uint32_t)min(one_warp ? 4 : 2, rc.ppt);
+        split_at = (one_warp ? 0.5f : 0.75f) * (float)total / (float)max(grid, 1);
+    }
+    __device__ uint32_t parts(uint32_t c) const { return (max_parts > 1 && (float)c > split_at) ? max_parts : 1u; }
+};
+// cost of one part of a tile of cost c split in p: a part redoes the
+// per-entry work, (p + 1) / 2p of it
+__device__ __forceinline__ float part_cost(uint32_t c, uint32_t p) {
+    return (float)c * (p == 1u ? 1.0f : (p == 2u ? 0.75f : 0.625f));
+}
 
 __device__ __forceinline__ int view_of_bin(const BatchDev& b, uint32_t bin) {
     int v = 0;
@@ -1260,6 +1288,48 @@ __global__ void __launch_bounds__(kCostThreads) k_tile_cost(const __grid_constan
     }
 }
 
+// Per tile its parts and cost class from the feedback cost (k_tile_cost),
+// stored in place of the cost as class | parts << 8, and the work items per
+// class summed into order_cls[0 .. kOrderClasses) (a histogram per CTA
+// first).  Many CTAs, so that no single SM walks every tile.
+__global__ void __launch_bounds__(kCostThreads) k_tile_class(const __grid_constant__ BatchDev b, RasterDev rc,
+                                                             uint32_t* __restrict__ fb, uint32_t fb_stride,
+                                                             const uint32_t* __restrict__ fb_state, int grid,
+                                                             uint32_t* __restrict__ order_cls) {
+    __shared__ uint32_t h[kOrderClasses];
+    for (int k = threadIdx.x; k < kOrderClasses; k += kCostThreads) h[k] = 0;
+    __syncthreads();
+    const SplitRule rule(rc, *reinterpret_cast<const unsigned long long*>(fb_state + kFbTotal), grid);
+    uint32_t* cost = fb + 4 * (size_t)fb_stride;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < b.total_tiles; t += gridDim.x * blockDim.x) {
+        const uint32_t c = cost[t], p = rule.parts(c), k = order_class(part_cost(c, p));
+        cost[t] = k | (p << 8);
+        atomicAdd(&h[k], p);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kOrderClasses; k += kCostThreads)
+        if (h[k]) atomicAdd(&order_cls[k], h[k]);
+}
+
+// Work items of the feedback order: every tile takes its parts' slots in
+// its class from the class cursors (k_tile_order) and writes its items.  The
+// order within a class is whatever the atomics give.
+__global__ void __launch_bounds__(kCostThreads) k_tile_scatter(const __grid_constant__ BatchDev b,
+                                                               const uint32_t* __restrict__ fb, uint32_t fb_stride,
+                                                               const uint32_t* __restrict__ fb_state,
+                                                               uint32_t* __restrict__ order_cls,
+                                                               uint32_t* __restrict__ order) {
+    if (fb_state[kFbUse] == 0u) return;  // the order kernel took the plain order
+    const uint32_t* kp = fb + 4 * (size_t)fb_stride;
+    uint32_t* cursor = order_cls + kOrderClasses;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < b.total_tiles; t += gridDim.x * blockDim.x) {
+        const uint32_t v = kp[t], k = v & 0xffu, p = v >> 8;
+        const uint32_t st = atomicAdd(&cursor[k], p);
+        const uint32_t lp = p == 4 ? 2u : (p == 2 ? 1u : 0u);
+        for (uint32_t q = 0; q < p; ++q) order[st + q] = make_item(t, q, lp);
+    }
+}
+
 // One CTA.  With `totals` (the digit counts of a one-pass pair sort, where
 // the digit is the whole bin id) it first writes every bin's range as the
 // exclusive scan of the counts.  Then the work items, longest first:
@@ -1270,18 +1340,19 @@ __global__ void __launch_bounds__(kCostThreads) k_tile_cost(const __grid_constan
 // order.
 //
 // kOrderFeedback with feedback from the last gradient launch of the same
-// geometry: the items are ordered by the tile costs k_tile_cost wrote.  With one-warp
-// CTAs a tile whose cost exceeds half of the mean work of one of the
-// launch's `grid` persistent CTAs is split into min(4, pixels per thread)
-// parts, so that no single CTA holds the launch back.  The order and the split decide which CTA renders which
-// pixels, never a result.  In feedback mode it also advances the launch
-// parity and resets the cost sum.
+// geometry: the items are ordered by the tile costs k_tile_cost wrote and
+// split by SplitRule; k_tile_class has counted the items per class, this
+// kernel scans the counts into class cursors, and k_tile_scatter writes the
+// items.  The order and the split decide which CTA renders which pixels,
+// never a result.  In feedback mode it also advances the launch parity and
+// resets the cost sum.
 __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_constant__ BatchDev b,
                                                               const uint32_t* __restrict__ totals,
                                                               uint2* __restrict__ ranges, RasterDev rc,
                                                               uint32_t* __restrict__ order, int mode, int grid,
                                                               uint32_t* __restrict__ fb, uint32_t fb_stride,
-                                                              uint32_t* __restrict__ fb_state) {
+                                                              uint32_t* __restrict__ fb_state,
+                                                              uint32_t* __restrict__ order_cls) {
     __shared__ uint32_t cls[kOrderClasses];
     __shared__ uint32_t wsum[kOrderThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1315,47 +1386,18 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_const
         use_fb = fb_state[kFbSignature] == sig && grid > 0;
     }
     __syncthreads();  // also makes the ranges written above visible to the CTA
-    const uint32_t* cost = fb + 4 * (size_t)fb_stride;
-    // A one-warp CTA splits a tile above half the mean load of a CTA into up
-    // to 4 parts.  A larger CTA walks a tile faster alone, and every part
-    // redoes the list filter and the gradient reductions, so it splits only
-    // the tiles that would outlast the mean load (above 0.75 of it), in 2
-    // parts: once the cache has trained, a few such tiles set the length of
-    // the launch (measured at 2 and 4 pixels per thread).
-    const bool one_warp = rc.tile_w * rc.tile_h / rc.ppt <= 32;
-    const uint32_t max_parts = (uint32_t)min(one_warp ? 4 : 2, rc.ppt);
-    // one CTA classifies every tile, so the per-tile arithmetic is kept to
-    // a few instructions: the hardware log2 (a class only decides which CTA
-    // renders a tile, never a result)
-    auto klass_of = [](float c) -> uint32_t {
-        const float l = __log2f(c + 1.0f) * 8.0f;
-        return (uint32_t)(kOrderClasses - 1) - (uint32_t)fminf(l, (float)(kOrderClasses - 1));
-    };
+    auto klass_of = [](float c) -> uint32_t { return order_class(c); };
     if (use_fb) {
-        const unsigned long long total = *reinterpret_cast<const unsigned long long*>(fb_state + kFbTotal);
-        const float split_at = (one_warp ? 0.5f : 0.75f) * (float)total / (float)grid;
-        auto parts_of = [&](uint32_t c) -> uint32_t {
-            return (max_parts > 1 && (float)c > split_at) ? max_parts : 1u;
-        };
-        auto item_cost = [](uint32_t c, uint32_t p) -> float {  // a part redoes the per-entry work: (p + 1) / 2p
-            return (float)c * (p == 1u ? 1.0f : (p == 2u ? 0.75f : 0.625f));
-        };
-        for (uint32_t t = threadIdx.x; t < nt; t += kOrderThreads) {
-            const uint32_t c = cost[t], p = parts_of(c);
-            atomicAdd(&cls[klass_of(item_cost(c, p))], p);
-        }
-        __syncthreads();
-        uint32_t v = threadIdx.x < kOrderClasses ? cls[threadIdx.x] : 0u;
+        // the classes and their item counts come from k_tile_class; the
+        // cursors go to k_tile_scatter, which writes the items
+        uint32_t v = threadIdx.x < kOrderClasses ? order_cls[threadIdx.x] : 0u;
         uint32_t sc = block_scan(v);
-        if (threadIdx.x < kOrderClasses) cls[threadIdx.x] = sc;
-        if (threadIdx.x == kOrderClasses - 1) fb_state[kFbItems] = sc + v;
-        __syncthreads();
-        for (uint32_t t = threadIdx.x; t < nt; t += kOrderThreads) {
-            const uint32_t c = cost[t], p = parts_of(c);
-            const uint32_t st = atomicAdd(&cls[klass_of(item_cost(c, p))], p);
-            const uint32_t lp = p == 4 ? 2u : (p == 2 ? 1u : 0u);
-            for (uint32_t k = 0; k < p; ++k) order[st + k] = make_item(t, k, lp);
+        if (threadIdx.x < kOrderClasses) {
+            order_cls[kOrderClasses + threadIdx.x] = sc;
+            order_cls[threadIdx.x] = 0u;  // for the next binning
         }
+        if (threadIdx.x == kOrderClasses - 1) fb_state[kFbItems] = sc + v;
+        if (threadIdx.x == 0) fb_state[kFbUse] = 1u;
     } else {
         auto bin_info = [&](uint32_t bin, uint32_t& klass, uint32_t& ntiles) {
             const ViewDev& vw = b.v[view_of_bin(b, bin)];
@@ -1394,6 +1436,10 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_const
             }
         }
         if (threadIdx.x == 0) fb_state[kFbItems] = nt;
+        if (mode == kOrderFeedback) {
+            if (threadIdx.x < kOrderClasses) order_cls[threadIdx.x] = 0u;  // counted by k_tile_class, unused
+            if (threadIdx.x == 0) fb_state[kFbUse] = 0u;
+        }
     }
     if (mode == kOrderFeedback) {
         __syncthreads();  // every read of the state above is done
@@ -1448,19 +1494,24 @@ cudaError_t bin_gaussians(const BatchDev& b, const RasterDev& rc, gsc_workspace*
         // are their exclusive scan (done by k_tile_order); more passes: the
         // ranges come from the boundaries of the sorted keys
         const bool one_pass = radix_passes(bits) == 1 && bins <= (uint32_t)kOrderThreads;
-        PhaseScope ph(kPhRanges, s, (one_pass ? 1 : 2) + (order_mode == kOrderFeedback ? 1 : 0));
+        PhaseScope ph(kPhRanges, s, (one_pass ? 1 : 2) + (order_mode == kOrderFeedback ? 3 : 0));
         if (!one_pass) {
             cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * bins, s);
             k_ranges<<<152 * 8, 256, 0, s>>>(keys, ws->counters, ws->ranges, bins);
         }
         const int grid = order_mode == kOrderFeedback ? bwd_grid_hint(rc, b.total_tiles) : 0;
+        uint32_t nblk = min((b.total_tiles + kCostThreads - 1) / kCostThreads, 152u * 4u);
+        nblk = nblk ? nblk : 1u;
+        const uint32_t fbs = (uint32_t)ws->max_tiles;
         if (order_mode == kOrderFeedback) {
-            const uint32_t nblk = min((b.total_tiles + kCostThreads - 1) / kCostThreads, 152u * 4u);
-            k_tile_cost<<<nblk ? nblk : 1u, kCostThreads, 0, s>>>(b, ws->fb, (uint32_t)ws->max_tiles, ws->fb_state);
+            k_tile_cost<<<nblk, kCostThreads, 0, s>>>(b, ws->fb, fbs, ws->fb_state);
+            k_tile_class<<<nblk, kCostThreads, 0, s>>>(b, rc, ws->fb, fbs, ws->fb_state, grid, ws->order_cls);
         }
         k_tile_order<<<1, kOrderThreads, 0, s>>>(b, one_pass ? radix_totals(ws->hist) : nullptr, ws->ranges, rc,
-                                                 ws->tile_order, order_mode, grid, ws->fb, (uint32_t)ws->max_tiles,
-                                                 ws->fb_state);
+                                                 ws->tile_order, order_mode, grid, ws->fb, fbs, ws->fb_state,
+                                                 ws->order_cls);
+        if (order_mode == kOrderFeedback)
+            k_tile_scatter<<<nblk, kCostThreads, 0, s>>>(b, ws->fb, fbs, ws->fb_state, ws->order_cls, ws->tile_order);
         ws->order = ws->tile_order;
     }
     return cudaGetLastError();
