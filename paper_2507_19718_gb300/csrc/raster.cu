@@ -3,13 +3,20 @@
 // splatting rasterizer at SH degree 0, Sec. 3.6).
 //
 // Forward:  k_project  -> depth radix sort -> scan of bin counts -> k_emit
+//           (a pair per bin of the tile rectangle; a bin the falloff bound
+//           cannot reach gets a key past every bin)
 //           -> stable radix sort of the (bin, Gaussian) pairs by bin
 //           -> bin ranges and tile order (k_tile_order; k_ranges first when
-//           the pair sort took more than one pass) -> k_render (each tile
-//           filters its bin's list)
+//           the pair sort took more than one pass; with feedback from the
+//           last gradient launch k_tile_cost, k_tile_class before and
+//           k_tile_scatter after it) -> k_render (each tile filters its
+//           bin's list)
 // Backward: the same binning (no per-pixel state is kept from the forward),
 //           k_render_bwd (forward re-walk for the final T and the last
 //           composited entry, then back to front), k_project_bwd.
+// Training step: the same binning, k_render_bwd with the HDR loss folded in,
+//           k_project_bwd_step (parameter gradients + AdamW; its first
+//           blocks sum the views' losses).
 //
 // The compositing decisions (alpha >= alpha_min, T (1 - alpha) < T_min) are
 // computed by one inline function with explicitly rounded operations, so the
