@@ -172,13 +172,15 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchDe
     float lthr2 = log2f(rc.alpha_min / op);
     float mx = cam.fx * x.t[0] / x.t[2] + cam.cx;
     float my = cam.fy * x.t[1] / x.t[2] + cam.cy;
-    float half = 0.5f * (x.A + x.C), dd = 0.5f * (x.A - x.C);
-    float lmax = half + sqrtf(dd * dd + x.B * x.B);
-    // alpha >= alpha_min  =>  d^T conic d <= 2 ln(op / alpha_min)  =>  |d|^2 <= that * lmax
-    float r = sqrtf(-2.f * lthr2 * kLn2 * lmax) * 1.001f + 0.02f;
-    if (!isfinite(mx) || !isfinite(my) || !isfinite(r)) return;
-    float xl = ceilf(fmaxf(mx - r - 0.5f, -1.f)), xh = floorf(fminf(mx + r - 0.5f, (float)cam.W));
-    float yl = ceilf(fmaxf(my - r - 0.5f, -1.f)), yh = floorf(fminf(my + r - 0.5f, (float)cam.H));
+    // alpha >= alpha_min  =>  d^T conic d <= k = 2 ln(op / alpha_min): an
+    // ellipse whose bounding box has half-widths sqrt(k Sigma_xx) and
+    // sqrt(k Sigma_yy) (Sigma = A, B, C, the inverse of the conic).  The
+    // margins cover the rounding of the FP32 conic the pixels are tested with.
+    const float k = -2.f * lthr2 * kLn2;
+    const float rx = sqrtf(k * x.A) * 1.005f + 0.05f, ry = sqrtf(k * x.C) * 1.005f + 0.05f;
+    if (!isfinite(mx) || !isfinite(my) || !isfinite(rx) || !isfinite(ry)) return;
+    float xl = ceilf(fmaxf(mx - rx - 0.5f, -1.f)), xh = floorf(fminf(mx + rx - 0.5f, (float)cam.W));
+    float yl = ceilf(fmaxf(my - ry - 0.5f, -1.f)), yh = floorf(fminf(my + ry - 0.5f, (float)cam.H));
     int ilo = max(0, (int)xl), ihi = min(cam.W - 1, (int)xh);
     int jlo = max(0, (int)yl), jhi = min(cam.H - 1, (int)yh);
     if (ilo > ihi || jlo > jhi) return;

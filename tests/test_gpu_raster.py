@@ -161,7 +161,7 @@ def test_full_size_1080p_1M_sampled(gpu, orc):
     params = torch.from_numpy(p).cuda()
     img = gpu.cache_render(params, cam, cfg, ws)
     need = ws.status()
-    assert need > 10_000_000
+    assert need > 5_000_000  # a full-size binning (7.7M pairs with the ellipses' own bounding boxes)
     img = img.cpu().numpy()
     marginal = 0
     for (x0, y0) in [(940, 520), (700, 300), (1300, 800), (0, 0)]:
