@@ -21,10 +21,10 @@
 // The compositing decisions (alpha >= alpha_min, T (1 - alpha) < T_min) are
 // computed by one inline function with explicitly rounded operations, so the
 // forward and the backward take them identically.  A Gaussian is binned into
-// every tile its alpha >= alpha_min support can reach (radius from the
-// largest eigenvalue of its 2D covariance), which makes every pixel's
-// ordered list independent of the tile shape: images are bit-identical for
-// any tile size.
+// every tile its alpha >= alpha_min support can reach (the bounding box of
+// that ellipse, then the exact bound per bin and per tile), which makes
+// every pixel's ordered list independent of the tile shape: images are
+// bit-identical for any tile size.
 #include <math.h>
 
 #include "gsc_internal.cuh"
