@@ -653,6 +653,9 @@ def run_served_bench(args, cfg_tuned):
     # tuned there, on the largest scene
     trials = srv.trainer.tune(max(scenes, key=lambda s: s.n_gaussians))
     best_train = min(trials, key=lambda t: t.ms)
+    # the views' launch configuration per request resolution (small views
+    # want more threads per tile), on the largest scene
+    view_trials = srv.tune_views(max(scenes, key=lambda s: s.n_gaussians))
     warm = serve.poisson_trace(200.0, 0.5, 8, seed=synth.BASE_SEED + 70)
     srv.run_batched(copy.deepcopy(warm))
     srv.run_plain(copy.deepcopy(warm))
@@ -661,7 +664,10 @@ def run_served_bench(args, cfg_tuned):
                        f"{args.serve_seconds:g} s, 90% views (256^2..1080p), 10% TF changes (16 retraining "
                        f"frames at 320x240)", "requests": len(trace),
            "hbm_budget_gb": round(srv.budget / 1e9, 1),
-           "retrain_launch": dict(_launch_cfg(best_train), ms=round(best_train.ms, 3))}
+           "retrain_launch": dict(_launch_cfg(best_train), ms=round(best_train.ms, 3)),
+           "view_launches": {f"{w}x{h}": dict(_launch_cfg(min(tr, key=lambda t: t.ms)),
+                                              ms=round(min(t.ms for t in tr), 3))
+                             for (w, h), tr in view_trials.items()}}
     for mode in ("batched", "plain"):
         reset()
         tr = copy.deepcopy(trace)

@@ -169,6 +169,30 @@ class Server:
             hbm_budget = int(0.8 * free) + self.fixed_bytes   # 80% of what was free after start-up
         self.budget = hbm_budget
         self.stats = {}
+        self.view_cfgs = {}   # (width, height) -> launch configuration of its views (tune_views)
+
+    def tune_views(self, sc: "ResidentScene", resolutions=VIEW_RESOLUTIONS, tiles=((16, 16), (8, 8)),
+                   bins=(0, 128), caps=(96, 256), ppts=(1, 2, 4)):
+        """Pick the fastest launch configuration of a view's batched forward
+        render (its K levels) at each request resolution, on scene sc.  A
+        small view has few tiles for the GPU's SMs, so it wants more threads
+        per tile than a 1080p one.  Results do not depend on it.  Returns
+        {(width, height): trials}."""
+        from . import autotune
+        out = {}
+        for w, h in resolutions:
+            cam = synth.orbit_camera(w, h, 30.0)
+            cands = list(autotune.candidates(tiles, bins, caps, ppts))
+            best, trials = autotune.autotune([L.params for L in sc.levels], cam, self.view_ws[0], cands=cands,
+                                             reps=2, fused=True, backward=False)
+            self.view_cfgs[(w, h)] = best.cfg()
+            out[(w, h)] = trials
+        return out
+
+    def _cfg_for(self, reqs) -> gsc.RasterCfg:
+        """Launch configuration of a batch: the one tuned for its largest view."""
+        r = max(reqs, key=lambda q: q.width * q.height)
+        return self.view_cfgs.get((r.width, r.height), self.cfg)
 
     def _out_bytes(self, r: Request) -> int:
         return 3 * r.width * r.height * 4 * self.K
@@ -251,7 +275,7 @@ class Server:
                         if s in last_train_ev:
                             rs.wait_event(last_train_ev[s])   # see the scene's latest trained cache
                     with torch.cuda.stream(rs):
-                        gsc.render_batch(views, gsc.BATCH_FWD, cfg, self.view_ws[wi])
+                        gsc.render_batch(views, gsc.BATCH_FWD, self._cfg_for(batch), self.view_ws[wi])
                         ev = torch.cuda.Event(enable_timing=True)
                         ev.record(rs)
                     for s in {r.scene for r in batch}:
@@ -321,7 +345,7 @@ class Server:
                 cam = gsc.camera(synth.orbit_camera(r.width, r.height, r.angle))
                 r.images = [torch.empty((3, r.height, r.width), device=self.device) for _ in range(K)]
                 for k, L in enumerate(sc.levels):
-                    gsc.cache_render(L.params, cam, cfg, self.plain_ws, image=r.images[k], stream=s)
+                    gsc.cache_render(L.params, cam, self._cfg_for([r]), self.plain_ws, image=r.images[k], stream=s)
             else:
                 sc.set_tf(r.tf_seed)
                 sc.retrain_left = self.retrain_frames

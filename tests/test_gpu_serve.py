@@ -102,3 +102,30 @@ def test_plain_path_serves_the_same_images(gpu):
     for r in plain:
         for got, ref in zip(r.images, _alone(gpu, scenes[r.scene], r, cfg, ws)):
             assert torch.equal(got, ref)
+
+
+def test_per_resolution_view_launches_serve_the_same_images(gpu):
+    """tune_views picks each request resolution's launch configuration; the
+    batched and the plain paths then render with it, and every image is the
+    same bits as the default configuration alone (results do not depend on
+    tile, bin, staging or pixels per thread)."""
+    import torch
+    from paper_2507_19718_gb300 import serve
+    cfg = gpu.raster_cfg()
+    scenes = _scenes(serve)
+    srv = serve.Server(scenes, cfg, max_views=8, train_res=(48, 40), retrain_frames=2, max_res=(96, 64),
+                       keep_images=True)
+    from paper_2507_19718_gb300 import autotune
+    space = dict(tiles=((16, 16), (8, 8)), bins=(0,), caps=(128, 256), ppts=(1, 2))
+    trials = srv.tune_views(scenes[2], resolutions=RES, **space)
+    n = len(list(autotune.candidates(**space)))
+    assert n >= 3 and set(trials) == set(RES) and all(len(t) == n for t in trials.values())
+    assert set(srv.view_cfgs) == set(RES)
+    trace = [r for r in _trace(serve) if r.kind == "view"][:30]
+    batched = srv.run_batched(copy.deepcopy(trace))
+    plain = srv.run_plain(copy.deepcopy(trace))
+    ws = gpu.Workspace(4000, 1 << 20, 96, 64)
+    for rb, rp in zip(batched, plain):
+        ref = _alone(gpu, scenes[rb.scene], rb, cfg, ws)
+        for got_b, got_p, want in zip(rb.images, rp.images, ref):
+            assert torch.equal(got_b, want) and torch.equal(got_p, want), rb.rid
