@@ -69,12 +69,12 @@ def workload_config(tuned_fwd=None, tuned_bwd=None):
 
 # ------------------------------------------------------------------ helpers
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
-    the sources it was captured from are unchanged (else None)."""
+def ncu_traffic(kernel: str, here: str = ROOT):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary under
+    `here`/profiles, if the sources it was captured from are unchanged (else
+    None)."""
     import hashlib
     import re
-    here = os.path.dirname(os.path.abspath(__file__))
     try:
         txt = open(os.path.join(here, "profiles", f"{kernel}_1080p_1M.md")).read()
     except OSError:
@@ -236,7 +236,9 @@ def phase_algorithmic(phase, c, n_gauss_calls, n_pixels_calls, frames, fine=Fals
     if phase == "depth_sort":
         return "byte", 4 * 20.0 * n_gauss_calls
     if phase == "emit":
-        return "byte", 8.0 * M + 20.0 * n_gauss_calls
+        # per Gaussian its sorted index, pair count, offset, tile rectangle
+        # and the 32 B of its record the bin bound reads; per pair key + value
+        return "byte", 8.0 * M + 52.0 * n_gauss_calls
     if phase == "ranges":
         return "byte", 4.0 * M
     if phase == "project":
