@@ -234,7 +234,9 @@ def phase_algorithmic(phase, c, n_gauss_calls, n_pixels_calls, frames, fine=Fals
     if phase == "tile_sort":
         return "byte", c.get("pair_sort_passes", 2) * 20.0 * M   # 20 B per pair per radix pass
     if phase == "depth_sort":
-        return "byte", 4 * 20.0 * n_gauss_calls
+        # one read of the keys for every pass's digit counts, then per pass
+        # keys and values read and written (4 + 4 x 16 B per Gaussian)
+        return "byte", 68.0 * n_gauss_calls
     if phase == "emit":
         # per Gaussian its sorted index, pair count, offset, tile rectangle
         # and the 32 B of its record the bin bound reads; per pair key + value

@@ -264,6 +264,7 @@ size_t layout(int64_t NG, int64_t NP, int32_t W, int32_t H, int32_t NV, gsc_work
     w->pval0 = (uint32_t*)take(4 * np);
     w->pval1 = (uint32_t*)take(4 * np);
     w->hist = (uint32_t*)take(4 * kHistWords);
+    w->sweep = (uint32_t*)take(4 * onesweep_words(ng));
     w->ranges = (uint2*)take(sizeof(uint2) * (size_t)tiles);
     w->tile_order = (uint32_t*)take(4 * 4 * (size_t)tiles);  // up to 4 parts per tile
     w->fb = (uint32_t*)take(4 * 5 * (size_t)tiles);

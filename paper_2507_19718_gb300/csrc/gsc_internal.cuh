@@ -161,6 +161,7 @@ struct gsc_workspace {
     uint32_t* scan_sums;
     uint32_t *pkey0, *pkey1, *pval0, *pval1;
     uint32_t* hist;    // kHistWords
+    uint32_t* sweep;   // onesweep_words(max_gaussians): scratch of the depth sort
     uint2* ranges;     // [start, end) per bin
     uint32_t* tile_order;   // work items (tiles or parts of tiles) by expected cost, longest first
     const uint32_t* order;  // the order of the last binning
@@ -191,6 +192,14 @@ void scan_gathered(const uint32_t* cnt, const uint32_t* idx, uint32_t n, uint32_
 int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* n_dev,
                      uint32_t n_host, int bits, int blocks, uint32_t* hist, cudaStream_t s);
 int sort_blocks_for(uint64_t n);
+// Stable LSD radix sort of n (key, value) pairs on all 32 key bits, the
+// count known on the host: one launch counts the digits of the four 8-bit
+// passes, then one launch per pass (decoupled look-back instead of a scan
+// pass).  `scratch`: onesweep_words(n) words; a bounded wait that runs out
+// sets GSC_ERR_TIMEOUT in status[kStatusCode].  Returns as radix_sort_pairs.
+size_t onesweep_words(uint64_t n);
+int radix_sort_onesweep(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t n, uint32_t* scratch,
+                        int32_t* status, cudaStream_t s);
 // digit counts of the last pass of radix_sort_pairs (in its histogram buffer)
 inline uint32_t* radix_totals(uint32_t* hist) { return hist + (size_t)kMaxSortBlocks * kMaxDigits; }
 int radix_passes(int bits);

@@ -2,7 +2,7 @@
 // (Sec. 3.1 / 3.5 of GSCache, which renders each level with the 3D Gaussian
 // splatting rasterizer at SH degree 0, Sec. 3.6).
 //
-// Forward:  k_project  -> depth radix sort -> scan of bin counts -> k_emit
+// Forward:  k_project  -> depth radix sort (one sweep) -> scan of bin counts -> k_emit
 //           (a pair per bin of the tile rectangle; a bin the falloff bound
 //           cannot reach gets a key past every bin)
 //           -> stable radix sort of the (bin, Gaussian) pairs by bin
@@ -1474,8 +1474,12 @@ cudaError_t bin_gaussians(const BatchDev& b, const RasterDev& rc, gsc_workspace*
     }
     int w;
     {
-        PhaseScope ph(kPhDepthSort, s, 3 * 4);
-        w = radix_sort_pairs(ws->key0, ws->idx0, ws->key1, ws->idx1, nullptr, n, 32, sort_blocks_for(n), ws->hist, s);
+        // the one-sweep sort's published counts hold 30 bits
+        const bool sweep = n < (1u << 30);
+        PhaseScope ph(kPhDepthSort, s, sweep ? 1 + 4 : 3 * 4);
+        w = sweep ? radix_sort_onesweep(ws->key0, ws->idx0, ws->key1, ws->idx1, n, ws->sweep, ws->status, s)
+                  : radix_sort_pairs(ws->key0, ws->idx0, ws->key1, ws->idx1, nullptr, n, 32, sort_blocks_for(n),
+                                     ws->hist, s);
     }
     const uint32_t* sidx = w ? ws->idx1 : ws->idx0;
     {

@@ -14,6 +14,9 @@
 //           values to their slots.
 // The element count may live on the device (the pair count is only known
 // after the binning scan), so no host round trip is needed.
+//
+// The depth sort, whose count the host knows, takes a one-sweep form of the
+// same passes (below): one launch per pass instead of three.
 #include "gsc_internal.cuh"
 
 namespace gsc {
@@ -332,6 +335,225 @@ int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, con
 }
 
 int radix_passes(int bits) { return (bits + kMaxDigitBits - 1) / kMaxDigitBits; }
+
+// ------------------------------------------------------------------ one sweep
+//
+// The depth sort (a count known on the host, 32-bit keys) in 1 + 4 launches
+// instead of 3 per pass.  k_os_hist counts the digits of all four 8-bit
+// passes in one read of the keys; each pass is then one launch of
+// k_os_pass, whose CTAs take the 2048-key tiles in order from a counter.  A
+// CTA ranks its tile as k_radix_scatter does, publishes per digit the
+// tile's count, and adds the counts of the earlier tiles from the words they
+// published (decoupled look-back, Merrill and Garland 2016): a word holds a
+// flag and either the tile's own count or the count up to and through that
+// tile, and the look-back walks back until it meets the latter.  A key's
+// position is the start of its digit over the whole input, plus the digit's
+// count in the earlier tiles, plus its rank in the tile, as in the
+// three-kernel pass.
+//
+// Progress: a CTA waits only for tiles taken before its own, whose CTAs are
+// already running and publish their count before they wait themselves, so
+// every wait ends.  Each is bounded all the same: one that runs out sets
+// GSC_ERR_TIMEOUT in the workspace status, and no store of the pass leaves
+// the output, whatever the positions.
+//
+// Scratch (words): digit totals [pass][256], tile counters [pass], then per
+// pass one published word per (tile, digit); zeroed before every sort.
+constexpr int kOsPasses = 4;
+constexpr int kOsDigits = 256;
+constexpr size_t kOsHeader = kOsPasses * kOsDigits + 32;
+constexpr uint32_t kOsAgg = 1u << 30;  // flag: the tile's own count
+constexpr uint32_t kOsInc = 2u << 30;  // flag: the count through the tile
+constexpr uint32_t kOsValue = kOsAgg - 1u;
+constexpr uint32_t kOsSpinLimit = 1u << 22;
+constexpr int kOsWindow = 8;             // predecessors' words loaded at once
+constexpr uint32_t kOsHistBlocks = 2 * 152;
+
+size_t onesweep_words(uint64_t n) {
+    const uint64_t tiles = (n + kSortTile - 1) / kSortTile;
+    return kOsHeader + (size_t)kOsPasses * tiles * kOsDigits;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// digit totals of every pass: per-warp shared counters, then one global
+// atomic per (pass, digit) and CTA
+__global__ void __launch_bounds__(kSortThreads) k_os_hist(const uint32_t* __restrict__ keys, uint32_t n,
+                                                          uint32_t* __restrict__ totals) {
+    __shared__ uint32_t h[8][kOsPasses][kOsDigits];
+    const int warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 8 * kOsPasses * kOsDigits; i += kSortThreads) (&h[0][0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
+    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        uint32_t k[kSortIPT];
+#pragma unroll
+        for (int j = 0; j < kSortIPT; ++j) {
+            const uint32_t i = t * kSortTile + j * kSortThreads + threadIdx.x;
+            k[j] = i < n ? keys[i] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kSortIPT; ++j) {
+            if (t * kSortTile + j * kSortThreads + threadIdx.x < n) {
+#pragma unroll
+                for (int p = 0; p < kOsPasses; ++p) atomicAdd(&h[warp][p][(k[j] >> (8 * p)) & 255u], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kOsPasses * kOsDigits; i += kSortThreads) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) s += (&h[w][0][0])[i];
+        if (s) atomicAdd(&totals[i], s);
+    }
+}
+
+// one pass over the 8-bit digit `pass`; one CTA per tile (grid = tiles)
+__global__ void __launch_bounds__(kSortThreads) k_os_pass(const uint32_t* __restrict__ kin,
+                                                          const uint32_t* __restrict__ vin,
+                                                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                          uint32_t n, int pass, uint32_t* __restrict__ scratch,
+                                                          int32_t* __restrict__ status) {
+    __shared__ uint32_t wh[8][kOsDigits];
+    __shared__ uint32_t tstart[kOsDigits];
+    __shared__ uint32_t gbase[kOsDigits];
+    __shared__ uint32_t skey[kSortTile];
+    __shared__ uint32_t sval[kSortTile];
+    __shared__ uint32_t sm[8];
+    __shared__ uint32_t s_tile;
+    const int shift = 8 * pass;
+    const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
+    uint32_t* const word = scratch + kOsHeader + (size_t)pass * tiles * kOsDigits;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&scratch[kOsPasses * kOsDigits + pass], 1u);
+    for (int i = threadIdx.x; i < 8 * kOsDigits; i += kSortThreads) (&wh[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t t = s_tile;  // below tiles: one CTA per tile
+    const uint32_t lo = t * kSortTile, hi = min(lo + (uint32_t)kSortTile, n);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    uint32_t kk[kSortIPT], vv[kSortIPT], rank[kSortIPT];
+    int dd[kSortIPT];
+#pragma unroll
+    for (int j = 0; j < kSortIPT; ++j) {
+        const uint32_t i = lo + warp * (kWarp * kSortIPT) + j * kWarp + lane;
+        const bool valid = i < hi;
+        kk[j] = valid ? kin[i] : 0u;
+        vv[j] = valid ? vin[i] : 0u;
+    }
+    // ranks within the tile, stable (warps in order, lanes in order); the
+    // digit kOsDigits marks an empty slot
+#pragma unroll
+    for (int j = 0; j < kSortIPT; ++j) {
+        const bool valid = lo + warp * (kWarp * kSortIPT) + j * kWarp + lane < hi;
+        const int d = valid ? (int)((kk[j] >> shift) & 255u) : kOsDigits;
+        unsigned peers = kFull;
+#pragma unroll
+        for (int bit = 0; bit <= 8; ++bit) {
+            const bool set = (d >> bit) & 1;
+            const unsigned m = __ballot_sync(kFull, set);
+            peers &= set ? m : ~m;
+        }
+        const uint32_t base = valid ? wh[warp][d] : 0u;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) wh[warp][d] = base + (uint32_t)__popc(peers);
+        __syncwarp();
+        rank[j] = base + (uint32_t)__popc(peers & lt);
+        dd[j] = d;
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;  // one digit per thread
+        uint32_t r = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t c = wh[w][d];
+            wh[w][d] = r;
+            r += c;
+        }
+        uint32_t* const mine = word + (size_t)t * kOsDigits + d;
+        st_relaxed(mine, (t == 0 ? kOsInc : kOsAgg) | r);
+        const uint32_t run[1] = {r}, tot[1] = {scratch[pass * kOsDigits + d]};
+        uint32_t ts[1], gs[1];
+        digit_scan<1>(run, ts, sm);  // the digit's start in the tile's sorted order
+        digit_scan<1>(tot, gs, sm);  // and in the whole output
+        // look-back: the digit's count in the tiles before this one, the
+        // words of kOsWindow predecessors loaded at once
+        uint32_t before = 0;
+        bool ok = true, done = t == 0;
+        for (uint32_t k = t; !done;) {
+            const uint32_t m = k < kOsWindow ? k : kOsWindow;
+            uint32_t v[kOsWindow];
+#pragma unroll
+            for (int i = 0; i < kOsWindow; ++i)
+                v[i] = (uint32_t)i < m ? ld_relaxed(word + (size_t)(k - 1 - i) * kOsDigits + d) : 0u;
+#pragma unroll
+            for (int i = 0; i < kOsWindow; ++i) {
+                if (done || (uint32_t)i >= m) break;
+                const uint32_t* const w = word + (size_t)(k - 1 - i) * kOsDigits + d;
+                for (uint32_t it = 0; (v[i] >> 30) == 0u; v[i] = ld_relaxed(w)) {
+                    if (++it == kOsSpinLimit) {
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                if (!ok) break;
+                before += v[i] & kOsValue;
+                done = (v[i] & ~kOsValue) == kOsInc;
+            }
+            k -= m;
+            done = done || !ok || k == 0;
+        }
+        if (t > 0) st_relaxed(mine, kOsInc | ((before + r) & kOsValue));
+        if (!ok) atomicCAS(&status[kStatusCode], 0, (int32_t)GSC_ERR_TIMEOUT);
+        tstart[d] = ts[0];
+        gbase[d] = gs[0] + before - ts[0];
+    }
+    __syncthreads();
+    // local sort of the tile in shared memory, then the runs of equal
+    // digits (contiguous in the output) with coalesced stores
+#pragma unroll
+    for (int j = 0; j < kSortIPT; ++j) {
+        if (dd[j] < kOsDigits) {
+            const uint32_t lp = tstart[dd[j]] + wh[warp][dd[j]] + rank[j];
+            skey[lp] = kk[j];
+            sval[lp] = vv[j];
+        }
+    }
+    __syncthreads();
+    for (uint32_t e = threadIdx.x; e < hi - lo; e += kSortThreads) {
+        const uint32_t k = skey[e];
+        const uint32_t pos = gbase[(k >> shift) & 255u] + e;
+        if (pos < n) {
+            kout[pos] = k;
+            vout[pos] = sval[e];
+        }
+    }
+}
+
+int radix_sort_onesweep(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t n, uint32_t* scratch,
+                        int32_t* status, cudaStream_t s) {
+    if (n == 0) return 0;
+    const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
+    cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * onesweep_words(n), s);
+    k_os_hist<<<tiles < kOsHistBlocks ? tiles : kOsHistBlocks, kSortThreads, 0, s>>>(k0, n, scratch);
+    int cur = 0;
+    for (int p = 0; p < kOsPasses; ++p) {
+        k_os_pass<<<tiles, kSortThreads, 0, s>>>(cur ? k1 : k0, cur ? v1 : v0, cur ? k0 : k1, cur ? v0 : v1, n, p,
+                                                 scratch, status);
+        cur ^= 1;
+    }
+    return cur;
+}
 
 // ------------------------------------------------------------------ scan
 
