@@ -213,7 +213,10 @@ gsc_status gsc_workspace_create(void* device_buffer, size_t bytes, int64_t max_g
 gsc_status gsc_workspace_destroy(gsc_workspace* ws);
 
 /* Synchronise `stream`, then return the device-side status of the
- * workspace (GSC_OK or GSC_ERR_CAPACITY) and clear it.  *pairs_needed
+ * workspace (GSC_OK; GSC_ERR_CAPACITY: a binning needed more pairs than
+ * the workspace holds; GSC_ERR_TIMEOUT: a bounded wait of the depth sort
+ * between its CTAs ran out, which the sort's ordering rules out unless the
+ * device misbehaves) and clear it.  *pairs_needed
  * (optional) receives the largest pair count any render since the last
  * call asked for, so that a caller can size a new workspace. */
 gsc_status gsc_workspace_status(gsc_workspace* ws, gsc_stream_t stream, int64_t* pairs_needed);
